@@ -1,0 +1,203 @@
+/*
+ * vgr.h -- C ABI of the GB300 frame path of a city-scale Gaussian-splatting
+ * renderer: temporal-aware LoD cut update, projection, tile binning with
+ * preemptive alpha filtering, sort and front-to-back alpha blending
+ * (arXiv 2506.02774, "Voyager", Sec. 3.1 pipeline, Sec. 4.1, Sec. 4.2).
+ *
+ * Conventions for every function below:
+ *  - Returns vgr_status; VGR_OK (0) on success.  Never aborts or exits.
+ *    vgr_last_error() gives a thread-local message for the last failure.
+ *  - Host arrays passed in are owned by the caller and only read during the
+ *    call (they are copied to the device).  Device buffers are owned by the
+ *    library; pointers handed out are borrowed and stay valid until the next
+ *    call on the same object or its destruction.
+ *  - A view is not thread-safe; distinct views may be used from distinct
+ *    threads.  All device work of a view is ordered on its stream.
+ *  - Requires a CUDA device of compute capability 10.3 (GB300); the library
+ *    contains sm_103a code only.
+ */
+#ifndef VGR_H
+#define VGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VGR_OK = 0,
+    VGR_E_INVALID = 1,     /* bad argument or malformed hierarchy */
+    VGR_E_NOMEM = 2,       /* device or host allocation failed */
+    VGR_E_CUDA = 3,        /* a CUDA call failed (message has the CUDA error) */
+    VGR_E_TIMEOUT = 4,     /* a bounded device wait or loop ran out */
+    VGR_E_NONMONOTONE = 5, /* a child expands while its parent does not */
+    VGR_E_OVERFLOW = 6     /* a buffer could not be grown to the needed size */
+} vgr_status;
+
+/* Storage precision of per-Gaussian attributes on the device. */
+enum {
+    VGR_STORE_FP32 = 0, /* SH and covariance in FP32 */
+    VGR_STORE_HALF = 1  /* SH in FP16, covariance in BF16; expanded to FP32 in registers */
+};
+
+/* Rasterization filter. */
+enum {
+    VGR_FILTER_PREEMPTIVE = 0, /* Sec. 4.2: log-domain alpha test, Gaussian- and tile-level filters */
+    VGR_FILTER_CANONICAL = 1   /* 3-sigma square footprint, alpha = min(.99, theta e^rho) then test */
+};
+
+/* Exponential in the blend. */
+enum {
+    VGR_EXP_EXACT = 0, /* hardware exp2 */
+    VGR_EXP_LUT = 1    /* Eq. 5: nearest entry of an m-interval table over rho in [-5.55, 0] */
+};
+
+typedef struct vgr_hierarchy vgr_hierarchy;
+typedef struct vgr_view vgr_view;
+
+/*
+ * LoD tree (paper Sec. 3.1 "LoD Tree"): one Gaussian per node, nodes in
+ * breadth-first order, node 0 the root (parent 0xFFFFFFFF), children of a
+ * node contiguous at first_child .. first_child + n_child - 1 with ids larger
+ * than the parent, n_child <= 8 (0 for a leaf).  Arrays have n_nodes entries
+ * (times the stated width):
+ *   mean     3 floats, world position (also the node centre of the LoD test)
+ *   cov6     6 floats, covariance xx xy xz yy yz zz
+ *   opacity  1 float in [0, 1]
+ *   sh       3 (deg+1)^2 floats, coefficient-major, RGB innermost
+ *   radius2  1 float, squared node radius R^2 of the granularity test; the
+ *            radii must nest (R_parent >= R_child + |mean_parent - mean_child|)
+ *            for the cut to be well defined under the test below.
+ */
+typedef struct {
+    uint32_t n_nodes;
+    uint32_t sh_degree; /* 0..3 */
+    const uint32_t* parent;
+    const uint32_t* first_child;
+    const uint8_t* n_child;
+    const float* mean;
+    const float* cov6;
+    const float* opacity;
+    const float* sh;
+    const float* radius2;
+    int32_t storage; /* VGR_STORE_* */
+} vgr_scene_desc;
+
+/*
+ * Pinhole camera.  p_cam = R (p - pos) with R the world->camera rotation
+ * (row-major) and pos the camera centre; camera axes x right, y down,
+ * z forward.  A point projects to (fx x/z + cx, fy y/z + cy) in pixels;
+ * pixel (i, j) covers [i, i+1) x [j, j+1).  Points with z <= z_near are culled.
+ */
+typedef struct {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy;
+    uint32_t width, height;
+    float z_near;
+} vgr_camera;
+
+typedef struct {
+    void* stream;            /* cudaStream_t to run on; NULL: the view creates its own */
+    uint32_t filter;         /* VGR_FILTER_* */
+    uint32_t exp_mode;       /* VGR_EXP_* */
+    uint32_t lut_size;       /* m of Eq. 5 when exp_mode == VGR_EXP_LUT (1..256; default 32) */
+    uint32_t temporal;       /* 1: temporal cut update between frames (default); 0: always from scratch */
+    uint32_t timing;         /* 1: record per-stage device times into vgr_frame_stats */
+    uint32_t use_graph;      /* 1: replay steady-state frames as CUDA graphs (default) */
+    uint64_t cut_capacity;   /* initial capacities; 0 = automatic.  Grown on demand. */
+    uint64_t pair_capacity;
+    uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
+} vgr_view_opts;
+
+enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT,
+       VGR_STAGE_EMIT, VGR_STAGE_TILE_SORT, VGR_STAGE_RANGES, VGR_STAGE_BLEND, VGR_N_STAGES };
+
+typedef struct {
+    uint32_t cut_count;       /* |C| */
+    uint32_t visible_count;   /* |V|: cut Gaussians with at least one kept tile */
+    uint64_t pair_count;      /* P: kept (Gaussian, tile) pairs */
+    uint64_t candidate_pairs; /* P0: pairs examined by the tile-level filter */
+    uint64_t nodes_evaluated; /* granularity tests made by the LoD step */
+    uint32_t lod_from_scratch;/* 1 if the cut was found top-down this frame */
+    uint32_t replays;         /* frame replays (buffer growth or LoD fallback) */
+    float stage_ms[VGR_N_STAGES]; /* device time per stage (timing = 1), else 0 */
+    float frame_ms;           /* device time of the frame (timing = 1), else 0 */
+} vgr_frame_stats;
+
+typedef struct {
+    const float* image;       /* device, height x width x 3 FP32 RGB, background 0 */
+    const uint32_t* cut;      /* device, cut_count node ids in ascending order */
+    uint32_t cut_count;
+    uint32_t width, height;
+    vgr_frame_stats stats;
+} vgr_frame;
+
+/* Device pointers of the intermediate buffers of the last frame (testing). */
+typedef struct {
+    uint32_t n_cut, n_visible;
+    uint64_t n_pairs;
+    uint32_t tiles_x, tiles_y;
+    const uint32_t* cut;          /* [n_cut] ascending node ids */
+    const uint32_t* vis_node;     /* [n_visible] node id, in cut order */
+    const uint32_t* vis_depth;    /* [n_visible] FP32 depth key bits */
+    const uint32_t* vis_ntile;    /* [n_visible] kept tiles */
+    const uint32_t* vis_rect;     /* [2 n_visible] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
+    const float* vis_recA;        /* [4 n_visible] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
+    const float* vis_recB;        /* [4 n_visible] C thr theta r, thr = ln alpha* - ln theta */
+    const float* vis_recC;        /* [2 n_visible] g b */
+    const uint32_t* depth_order;  /* [n_visible] visible index by depth rank */
+    const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
+    const uint32_t* pair_rank;    /* [n_pairs] depth rank of the Gaussian */
+    const uint32_t* tile_range;   /* [2 tiles] start, end into the pair list */
+} vgr_debug_buffers;
+
+void vgr_default_view_opts(vgr_view_opts* opts);
+
+/*
+ * Upload a LoD tree.  Validates the shape (BFS order, contiguous children,
+ * n_child <= 8, radius nesting within a 1e-6 relative slack) and returns
+ * VGR_E_INVALID otherwise.  Precomputes ln(opacity) on the device.
+ */
+vgr_status vgr_load_hierarchy(const vgr_scene_desc* desc, vgr_hierarchy** out);
+vgr_status vgr_free_hierarchy(vgr_hierarchy* h);
+/* Device bytes held by the hierarchy. */
+vgr_status vgr_hierarchy_info(const vgr_hierarchy* h, uint64_t* device_bytes, uint32_t* max_depth);
+
+/* A view keeps one client's state: previous cut, sort buffers, image. */
+vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view** out);
+vgr_status vgr_destroy_view(vgr_view* v);
+/* Forget the previous cut: the next frame finds its cut top-down. */
+vgr_status vgr_reset_view(vgr_view* v);
+vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes);
+
+/*
+ * Render one frame with granularity threshold tau (pixels).  The cut is the
+ * set of nodes whose every ancestor expands and which do not expand, where
+ * with f = max(fx, fy), t = fl(tau / f), k = fl(t t) and single-rounded FP32
+ * arithmetic:  d2 = (dx dx + dy dy) + dz dz,  (dx, dy, dz) = pos - mean[n],
+ * expand(n) = n_child[n] > 0 and fl(d2 k) < radius2[n]   (Sec. 3.1).
+ * Between frames with equal tau and f the cut is updated from the previous
+ * one (Sec. 4.1, Algorithm 1); the result equals the top-down cut.
+ * Requires 0 <= tau <= f, width, height in [1, 16384], z_near > 0.
+ * Waits for the frame to finish before returning (status checks).
+ */
+vgr_status vgr_render_frame(vgr_view* v, const vgr_camera* cam, float tau, vgr_frame* out);
+
+/*
+ * As vgr_render_frame, then copies the image into host memory host_rgb
+ * (height x width x 3 floats, caller-owned; pinned memory is fastest).
+ */
+vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb,
+                                 vgr_frame* out);
+
+vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* out);
+
+const char* vgr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VGR_H */

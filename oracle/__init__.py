@@ -91,7 +91,7 @@ def _load():
             lib.orc_rho_max_rect.argtypes = [P] + [ctypes.c_double] * 6
             lib.orc_rho_max_rect.restype = ctypes.c_double
             lib.orc_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_float,
-                                       P, ctypes.c_double, ctypes.c_int]
+                                       P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
             lib.orc_render.restype = ctypes.POINTER(_Frame)
             lib.orc_frame_free.argtypes = [ctypes.POINTER(_Frame)]
             lib.orc_frame_free.restype = None
@@ -187,13 +187,15 @@ def _arr(ptr, dtype, n):
     return np.frombuffer(buf, dtype=dt, count=n).copy()
 
 
-def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 1e-4,
+def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-3, t_flag: float = 0.05,
            exhaustive: bool = False) -> dict:
     """Render one frame; returns the cut, per-cut projection, pairs and image.
 
     ``tile_mask`` (bool per tile, row-major) restricts binning and blending
-    to those tiles.  ``band`` is the relative half-width of the ambiguity
-    flag around alpha* = 1/255 and T_min = 1e-4.
+    to those tiles.  A pixel is flagged when some Gaussian's rho lies within
+    ``band`` (nats) of ln alpha* - ln theta while the transmittance is still
+    >= ``t_flag``: there an FP32 renderer may take the other side of the
+    alpha >= alpha* test and move the pixel by up to ~alpha* T max(rgb).
     """
     lib = _load()
     ref = _SceneRef(sc)
@@ -204,7 +206,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 1e-
     if tile_mask is not None:
         mask = np.ascontiguousarray(np.asarray(tile_mask, bool).reshape(TW * TH).astype(np.uint8))
     fp = lib.orc_render(ctypes.byref(ref.s), ctypes.byref(c), float(np.float32(tau)),
-                        _ptr(mask) if mask is not None else None, float(band), int(bool(exhaustive)))
+                        _ptr(mask) if mask is not None else None, float(band), float(t_flag),
+                        int(bool(exhaustive)))
     if not fp:
         raise MemoryError("oracle render")
     try:

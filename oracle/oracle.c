@@ -390,9 +390,15 @@ static int orc_cmp_key(const void* a, const void* b) {
     return 0;
 }
 
-/* per-pixel front-to-back blend over the list idx[0..n) */
+/* Per-pixel front-to-back blend over the list idx[0..n).  The ambiguity
+ * flag marks pixels where a renderer working in FP32 may legitimately take
+ * the other side of the alpha >= alpha* decision for some Gaussian (rho within
+ * 'band' of ln alpha* - ln theta) while the transmittance is still at least
+ * t_flag, so that the flip could move the pixel by up to about
+ * alpha* T max(rgb).  Flips of the T < 1e-4 test move a pixel by at most
+ * about 1e-4 max(rgb) and are not flagged. */
 static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, double px, double py,
-                            double band, double* out, uint8_t* flag, uint32_t* n_eval,
+                            double band, double t_flag, double* out, uint8_t* flag, uint32_t* n_eval,
                             uint32_t* n_contrib) {
     double T = 1.0, C[3] = {0, 0, 0};
     uint8_t f = 0;
@@ -403,10 +409,9 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
         double rho = orc_rho(g->conic, dx, dy);
         double alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(rho));
         ++ne;
-        if (fabs(alpha - ORC_ALPHA_MIN) <= band * ORC_ALPHA_MIN) f = 1;
+        if (fabs(rho - g->thr) <= band && T >= t_flag) f = 1;
         if (alpha < ORC_ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - ORC_T_MIN) <= band * ORC_T_MIN) f = 1;
         if (Tn < ORC_T_MIN) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * g->rgb[ch];
         T = Tn;
@@ -420,11 +425,11 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
 
 /*
  * Render one frame.  tile_mask (optional, n_tiles bytes) restricts binning
- * and blending to the flagged tiles.  band is the relative half-width of the
- * alpha* / T_min ambiguity flag.  exhaustive != 0 selects mode 7.
+ * and blending to the flagged tiles.  band and t_flag parameterise the
+ * ambiguity flag (see orc_blend_pixel).  exhaustive != 0 selects mode 7.
  */
 orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, const uint8_t* tile_mask,
-                      double band, int exhaustive) {
+                      double band, double t_flag, int exhaustive) {
     orc_frame* F = (orc_frame*)calloc(1, sizeof(orc_frame));
     if (!F) return NULL;
     float f = cam->fx > cam->fy ? cam->fx : cam->fy;
@@ -475,7 +480,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
             int x = (int)(p % W), y = (int)(p / W);
             int t = (y / ORC_TILE) * TW + x / ORC_TILE;
             if (tile_mask && !tile_mask[t]) continue;
-            orc_blend_pixel(F->proj, list, m, x + 0.5, y + 0.5, band, &F->image[3 * p], &F->flags[p],
+            orc_blend_pixel(F->proj, list, m, x + 0.5, y + 0.5, band, t_flag, &F->image[3 * p], &F->flags[p],
                             &F->n_eval[p], &F->n_contrib[p]);
         }
         free(list);
@@ -559,7 +564,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
         for (int y = ty * ORC_TILE; y < (ty + 1) * ORC_TILE && y < H; ++y)
             for (int x = tx * ORC_TILE; x < (tx + 1) * ORC_TILE && x < W; ++x) {
                 size_t p = (size_t)y * W + x;
-                orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5, band, &F->image[3 * p],
+                orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5, band, t_flag, &F->image[3 * p],
                                 &F->flags[p], &F->n_eval[p], &F->n_contrib[p]);
             }
     }

@@ -1,0 +1,205 @@
+"""GB300 frame path of a city-scale Gaussian-splatting renderer (arXiv
+2506.02774): temporal-aware LoD cut update, projection with preemptive
+alpha filtering, tile binning, radix sort and front-to-back blending.
+
+This package is the thin Python binding of the C ABI in ``include/vgr.h``
+(``libvgr.so``, hand-written CUDA for sm_103a).  It only marshals arguments;
+every step of a frame runs in the library's kernels.  PyTorch is used to
+view the library's device buffers as tensors and for streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (EXP_EXACT, EXP_LUT, FILTER_CANONICAL, FILTER_PREEMPTIVE, STAGES, STORE_FP32, STORE_HALF,
+                   VgrError)
+
+__all__ = ["Hierarchy", "View", "FrameResult", "camera_struct", "VgrError", "load_library", "STORE_FP32",
+           "STORE_HALF", "FILTER_PREEMPTIVE", "FILTER_CANONICAL", "EXP_EXACT", "EXP_LUT", "STAGES"]
+
+
+def load_library(build: bool = True):
+    return _abi.load(build)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class _CudaArray:
+    """__cuda_array_interface__ wrapper of a device pointer owned by the library."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_tensor(ptr: int, shape, dtype: str):
+    """A torch view (no copy) of library-owned device memory."""
+    import torch
+    n = int(np.prod(shape)) if len(shape) else 1
+    if n == 0 or not ptr:
+        return torch.empty(tuple(shape), dtype=getattr(torch, dtype), device="cuda")
+    typestr = {"float32": "<f4", "int32": "<i4", "uint8": "|u1"}[dtype if dtype != "uint32" else "int32"]
+    t = torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+    return t
+
+
+def camera_struct(cam: dict) -> _abi.Camera:
+    c = _abi.Camera()
+    R = np.asarray(cam["R"], np.float32).reshape(9)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    p = np.asarray(cam["pos"], np.float32)
+    for i in range(3):
+        c.pos[i] = float(p[i])
+    c.fx, c.fy = float(cam["fx"]), float(cam["fy"])
+    c.cx, c.cy = float(cam["cx"]), float(cam["cy"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.z_near = float(cam.get("z_near", 0.2))
+    return c
+
+
+class Hierarchy:
+    """A LoD tree uploaded to the GPU (``vgr_load_hierarchy``)."""
+
+    def __init__(self, scene: dict, storage: int = STORE_FP32):
+        lib = _abi.load()
+        self._keep = [np.ascontiguousarray(scene[k]) for k in
+                      ("parent", "first_child", "n_child", "mean", "cov6", "opacity", "sh", "radius2")]
+        a = self._keep
+        assert a[0].dtype == np.uint32 and a[1].dtype == np.uint32 and a[2].dtype == np.uint8
+        for x in a[3:]:
+            assert x.dtype == np.float32
+        d = _abi.SceneDesc(int(scene["n_nodes"]), int(scene["sh_degree"]), *[_ptr(x) for x in a], int(storage))
+        h = ctypes.c_void_p()
+        _abi.check(lib.vgr_load_hierarchy(ctypes.byref(d), ctypes.byref(h)))
+        self._keep = None  # the library copied everything
+        self.handle = h
+        self.n_nodes = int(scene["n_nodes"])
+        self.sh_degree = int(scene["sh_degree"])
+        self.storage = storage
+        b, dep = ctypes.c_uint64(), ctypes.c_uint32()
+        _abi.check(lib.vgr_hierarchy_info(h, ctypes.byref(b), ctypes.byref(dep)))
+        self.device_bytes, self.max_depth = int(b.value), int(dep.value)
+
+    def close(self):
+        if self.handle:
+            _abi.check(_abi.load().vgr_free_hierarchy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FrameResult:
+    """Result of one frame: device image/cut views plus statistics."""
+
+    def __init__(self, fr: _abi.Frame):
+        self.raw = fr
+        self.width, self.height = int(fr.width), int(fr.height)
+        self.cut_count = int(fr.cut_count)
+        s = fr.stats
+        self.stats = dict(cut_count=int(s.cut_count), visible_count=int(s.visible_count),
+                          pair_count=int(s.pair_count), candidate_pairs=int(s.candidate_pairs),
+                          nodes_evaluated=int(s.nodes_evaluated), lod_from_scratch=int(s.lod_from_scratch),
+                          replays=int(s.replays), stage_ms={n: float(s.stage_ms[i]) for i, n in enumerate(STAGES)},
+                          frame_ms=float(s.frame_ms))
+
+    def image(self):
+        """H x W x 3 float32 CUDA tensor viewing the view's image buffer."""
+        return device_tensor(self.raw.image, (self.height, self.width, 3), "float32")
+
+    def cut(self):
+        """Ascending node ids (int32 view of the u32 ids) on the device."""
+        return device_tensor(self.raw.cut, (self.cut_count,), "int32")
+
+
+class View:
+    """One client's render state (``vgr_create_view``)."""
+
+    def __init__(self, hier: Hierarchy, *, filter: int = FILTER_PREEMPTIVE, exp_mode: int = EXP_EXACT,
+                 lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
+                 cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, stream=None):
+        lib = _abi.load()
+        o = _abi.ViewOpts()
+        lib.vgr_default_view_opts(ctypes.byref(o))
+        o.filter, o.exp_mode, o.lut_size = filter, exp_mode, lut_size
+        o.temporal, o.timing, o.use_graph = int(temporal), int(timing), int(use_graph)
+        o.cut_capacity, o.pair_capacity = cut_capacity, pair_capacity
+        if lod_budget:
+            o.lod_budget = lod_budget
+        if stream is not None:
+            o.stream = ctypes.c_void_p(int(stream))
+        v = ctypes.c_void_p()
+        _abi.check(lib.vgr_create_view(hier.handle, ctypes.byref(o), ctypes.byref(v)))
+        self.handle = v
+        self.hier = hier
+
+    def render(self, cam: dict, tau: float) -> FrameResult:
+        fr = _abi.Frame()
+        c = camera_struct(cam)
+        _abi.check(_abi.load().vgr_render_frame(self.handle, ctypes.byref(c), float(tau), ctypes.byref(fr)))
+        return FrameResult(fr)
+
+    def render_host(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
+        """Render and copy the image into the float32 H x W x 3 host array ``out``."""
+        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+        assert out.shape == (int(cam["height"]), int(cam["width"]), 3)
+        fr = _abi.Frame()
+        c = camera_struct(cam)
+        _abi.check(_abi.load().vgr_render_frame_host(self.handle, ctypes.byref(c), float(tau),
+                                                     ctypes.c_void_p(out.ctypes.data), ctypes.byref(fr)))
+        return FrameResult(fr)
+
+    def render_host_ptr(self, cam_struct: _abi.Camera, tau: float, host_ptr: int, fr: _abi.Frame) -> int:
+        """Lowest-overhead form of render_host (pre-built structs); returns the status."""
+        return _abi.load().vgr_render_frame_host(self.handle, ctypes.byref(cam_struct), float(tau),
+                                                 ctypes.c_void_p(host_ptr), ctypes.byref(fr))
+
+    def reset(self):
+        _abi.check(_abi.load().vgr_reset_view(self.handle))
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_uint64()
+        _abi.check(_abi.load().vgr_view_device_bytes(self.handle, ctypes.byref(b)))
+        return int(b.value)
+
+    def debug(self) -> dict:
+        """Copies of the last frame's intermediate buffers (numpy)."""
+        d = _abi.DebugBuffers()
+        _abi.check(_abi.load().vgr_view_debug(self.handle, ctypes.byref(d)))
+        nv, nc, npairs = int(d.n_visible), int(d.n_cut), int(d.n_pairs)
+        T = int(d.tiles_x) * int(d.tiles_y)
+
+        def u32(ptr, n):
+            return device_tensor(ptr, (n,), "int32").cpu().numpy().view(np.uint32).copy()
+
+        def f32(ptr, shape):
+            return device_tensor(ptr, shape, "float32").cpu().numpy().copy()
+
+        return dict(n_cut=nc, n_visible=nv, n_pairs=npairs, tiles=(int(d.tiles_x), int(d.tiles_y)),
+                    cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nv), vis_depth=u32(d.vis_depth, nv),
+                    vis_ntile=u32(d.vis_ntile, nv), vis_rect=u32(d.vis_rect, 2 * nv).reshape(nv, 2),
+                    vis_recA=f32(d.vis_recA, (nv, 4)), vis_recB=f32(d.vis_recB, (nv, 4)),
+                    vis_recC=f32(d.vis_recC, (nv, 2)), depth_order=u32(d.depth_order, nv),
+                    pair_tile=u32(d.pair_tile, npairs), pair_rank=u32(d.pair_rank, npairs),
+                    tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
+
+    def close(self):
+        if self.handle:
+            _abi.check(_abi.load().vgr_destroy_view(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

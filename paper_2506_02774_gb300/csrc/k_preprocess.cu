@@ -1,0 +1,356 @@
+// k_preprocess.cu -- culling & projection of the cut (paper Sec. 3.1
+// 'Culling & Projection') with the preemptive alpha filter moved into it
+// (Sec. 4.2, Eq. 4: alpha >= alpha* <=> rho >= ln alpha* - ln theta).
+//
+// One thread per cut node, tiles of 256 cut entries handed out by ticket and
+// compacted in order by a decoupled look-back scan, so visible Gaussians keep
+// ascending node-id order (the depth sort is stable, so equal depths stay
+// ordered by node id).
+//
+// Per node: p = R (mu - C); depth key = FP32 bits of
+// ((R20 dx + R21 dy) + R22 dz) with single-rounded operations; culled when
+// z <= z_near.  Gaussian-level filter: theta < alpha* is dropped.  EWA:
+// Sigma' = M Sigma M^T + 0.3 I with M = J R, J the perspective Jacobian with
+// x/z, y/z clamped to 1.3 (W/2)/fx, 1.3 (H/2)/fy.  Footprint box from
+// r^2 = 2 (ln theta - ln alpha*) (plus the test slack), candidate tiles are
+// those whose pixel-centre rectangle meets the box, and a candidate is kept
+// when the maximum of rho over that rectangle reaches ln alpha* - ln theta
+// (minus a 2e-3 slack that makes the FP32 test a superset of the exact one).
+// Colour from real SH up to degree 3 (+0.5, clamped at 0).
+#include <cuda_fp16.h>
+
+#include "vgr_internal.cuh"
+#include "vgr_launch.h"
+#include "vgr_tiletest.cuh"
+
+namespace vgr {
+
+constexpr int PRE_THREADS = 256;
+constexpr uint32_t COOP_MIN_AREA = 8;  // candidate rectangles above this are tested by the whole warp
+
+// Real spherical harmonics (orthonormal, Condon-Shortley phase) as
+// polynomials of the unit direction; constants are the closed forms
+//  l=0: 1/(2 sqrt(pi))
+//  l=1: sqrt(3/(4 pi))
+//  l=2: sqrt(15/(4 pi)), sqrt(5/(16 pi)), sqrt(15/(16 pi))
+//  l=3: sqrt(35/(32 pi)), sqrt(105/(4 pi)), sqrt(21/(32 pi)), sqrt(7/(16 pi)), sqrt(105/(16 pi))
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = 0.28209479177387814f;
+    if (DEG >= 1) {
+        Y[1] = -0.48860251190291992f * y;
+        Y[2] = 0.48860251190291992f * z;
+        Y[3] = -0.48860251190291992f * x;
+    }
+    if (DEG >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * (x * y);
+        Y[5] = -1.0925484305920792f * (y * z);
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * (x * z);
+        Y[8] = 0.54627421529603959f * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+            Y[10] = 2.8906114426405538f * (x * y) * z;
+            Y[11] = -0.45704579946446572f * y * (4.0f * zz - xx - yy);
+            Y[12] = 0.37317633259011540f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+            Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.4453057213202769f * z * (xx - yy);
+            Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+template <int STORE>
+struct Store;
+
+template <>
+struct Store<VGR_STORE_FP32> {
+    __device__ static __forceinline__ void cov(const SceneDev& sc, uint32_t n, float* S, float& theta, float& lnth) {
+        const float4 a = sc.covA[n], b = sc.covB[n];
+        S[0] = a.x; S[1] = a.y; S[2] = a.z; S[3] = a.w; S[4] = b.x; S[5] = b.y;
+        theta = b.z;
+        lnth = b.w;
+    }
+    template <int K>
+    __device__ static __forceinline__ void sh(const SceneDev& sc, uint32_t n, float* c) {
+        const float4* p = reinterpret_cast<const float4*>(sc.sh) + (size_t)n * (sc.sh_stride / 4);
+        constexpr int NV = (3 * K + 3) / 4;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float4 v = __ldg(p + i);
+            c[4 * i + 0] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+        }
+    }
+};
+
+template <>
+struct Store<VGR_STORE_HALF> {
+    // covariance as 6 BF16 in covA (uint4 storage: xx xy xz yy yz zz, 2 spare),
+    // opacity and ln(opacity) FP32 in covB.xy
+    __device__ static __forceinline__ void cov(const SceneDev& sc, uint32_t n, float* S, float& theta, float& lnth) {
+        const uint4 a = reinterpret_cast<const uint4*>(sc.covA)[n];
+        const float4 b = sc.covB[n];
+        const uint32_t w[3] = {a.x, a.y, a.z};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            S[2 * i] = __uint_as_float(w[i] << 16);
+            S[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+        theta = b.x;
+        lnth = b.y;
+    }
+    template <int K>
+    __device__ static __forceinline__ void sh(const SceneDev& sc, uint32_t n, float* c) {
+        const uint4* p = reinterpret_cast<const uint4*>(sc.sh) + (size_t)n * (sc.sh_stride / 8);
+        constexpr int NV = (3 * K + 7) / 8;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const uint4 v = __ldg(p + i);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const __half2 h = *reinterpret_cast<const __half2*>(&w[j]);
+                const float2 f = __half22float2(h);
+                c[8 * i + 2 * j] = f.x;
+                c[8 * i + 2 * j + 1] = f.y;
+            }
+        }
+    }
+};
+
+template <int DEG, int STORE>
+__global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const uint32_t* __restrict__ cut,
+                                                            const uint32_t* __restrict__ n_cut_p, uint32_t cap_cut,
+                                                            const FrameParams* __restrict__ fp, VisBuffers vis,
+                                                            uint32_t cap_vis,
+                                                            unsigned long long* __restrict__ status,
+                                                            Counters* __restrict__ ctr) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ uint32_t s_scan[9];
+    __shared__ uint32_t s_tile, s_prefix;
+    const uint32_t n_cut = min(*n_cut_p, cap_cut);
+    const uint32_t ntiles = (n_cut + PRE_THREADS - 1) / PRE_THREADS;
+    const uint32_t lane = lane_id();
+
+    const float R0 = fp->R[0], R1 = fp->R[1], R2 = fp->R[2], R3 = fp->R[3], R4 = fp->R[4], R5 = fp->R[5];
+    const float R6 = fp->R[6], R7 = fp->R[7], R8 = fp->R[8];
+    const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
+    const float fx = fp->fx, fy = fp->fy, cx = fp->cx, cy = fp->cy, z_near = fp->z_near;
+    const float limx = fp->limx, limy = fp->limy, Wf = fp->width_f, Hf = fp->height_f;
+    const int TW = (int)fp->tiles_x, TH = (int)fp->tiles_y;
+    const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
+    const uint32_t epoch = fp->epoch;
+    unsigned long long cand = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_PRE], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t i = tile * PRE_THREADS + threadIdx.x;
+
+        bool v = i < n_cut;
+        uint32_t node = 0, zbits = 0;
+        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, rx = 0.f, ry = 0.f, thr = 0.f, theta = 0.f;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
+        if (v) {
+            node = cut[i];
+            const float4 m = sc.cr[node];
+            dx = __fsub_rn(m.x, Cx);
+            dy = __fsub_rn(m.y, Cy);
+            dz = __fsub_rn(m.z, Cz);
+            const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
+            zbits = __float_as_uint(z);
+            v = z > z_near;
+            float S[6], lnth = 0.f;
+            if (v) {
+                Store<STORE>::cov(sc, node, S, theta, lnth);
+                if (!canonical && !(theta >= ALPHA_MIN)) v = false;  // Gaussian-level filter
+            }
+            if (v) {
+                const float x = fmaf(R0, dx, fmaf(R1, dy, R2 * dz));
+                const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
+                const float iz = 1.0f / z;
+                const float xz = x * iz, yz = y * iz;
+                u = fmaf(fx, xz, cx);
+                vv = fmaf(fy, yz, cy);
+                const float tx = fminf(limx, fmaxf(-limx, xz));
+                const float ty = fminf(limy, fmaxf(-limy, yz));
+                const float fxz = fx * iz, fyz = fy * iz;
+                // M = J R: rows M0 = fx/z (R0 - tx R2row), M1 = fy/z (R1row - ty R2row)
+                const float m00 = fxz * fmaf(-tx, R6, R0), m01 = fxz * fmaf(-tx, R7, R1), m02 = fxz * fmaf(-tx, R8, R2);
+                const float m10 = fyz * fmaf(-ty, R6, R3), m11 = fyz * fmaf(-ty, R7, R4), m12 = fyz * fmaf(-ty, R8, R5);
+                // Sigma M0^T, Sigma M1^T (Sigma = [[S0 S1 S2] [S1 S3 S4] [S2 S4 S5]])
+                const float a0 = fmaf(S[0], m00, fmaf(S[1], m01, S[2] * m02));
+                const float a1 = fmaf(S[1], m00, fmaf(S[3], m01, S[4] * m02));
+                const float a2 = fmaf(S[2], m00, fmaf(S[4], m01, S[5] * m02));
+                const float b0 = fmaf(S[0], m10, fmaf(S[1], m11, S[2] * m12));
+                const float b1 = fmaf(S[1], m10, fmaf(S[3], m11, S[4] * m12));
+                const float b2 = fmaf(S[2], m10, fmaf(S[4], m11, S[5] * m12));
+                const float s00 = fmaf(m00, a0, fmaf(m01, a1, m02 * a2)) + DILATE;
+                const float s01 = fmaf(m10, a0, fmaf(m11, a1, m12 * a2));
+                const float s11 = fmaf(m10, b0, fmaf(m11, b1, m12 * b2)) + DILATE;
+                // det = s00 s11 - s01^2 with the product error recovered (Kahan)
+                const float w = s01 * s01;
+                const float e = fmaf(-s01, s01, w);
+                const float det = fmaf(s00, s11, -w) + e;
+                if (!(det > 0.f)) {
+                    v = false;
+                } else {
+                    const float idet = 1.0f / det;
+                    ca = s11 * idet;
+                    cb = -s01 * idet;
+                    cc = s00 * idet;
+                    rx = __fdiv_rn(-cb, ca);
+                    ry = __fdiv_rn(-cb, cc);
+                    thr = LN_ALPHA_MIN - lnth;
+                    float bx, by;
+                    if (!canonical) {
+                        const float r2 = fmaxf(0.f, 2.0f * (lnth - LN_ALPHA_MIN) + 2.0f * TILE_EPS);
+                        bx = sqrtf(r2 * s00) * 1.0001f + 1e-3f;
+                        by = sqrtf(r2 * s11) * 1.0001f + 1e-3f;
+                    } else {
+                        // 3-sigma radius of the larger eigenvalue (3DGS-style square footprint)
+                        const float mid = 0.5f * (s00 + s11);
+                        const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+                        bx = by = ceilf(3.0f * sqrtf(lam));
+                    }
+                    tx0 = max(0, (int)ceilf((u - bx - (TILE - 0.5f)) * (1.0f / TILE)));
+                    tx1 = min(TW - 1, (int)floorf((u + bx - 0.5f) * (1.0f / TILE)));
+                    ty0 = max(0, (int)ceilf((vv - by - (TILE - 0.5f)) * (1.0f / TILE)));
+                    ty1 = min(TH - 1, (int)floorf((vv + by - 0.5f) * (1.0f / TILE)));
+                    if (!(u - bx < Wf + TILE) || !(u + bx > -TILE) || !(vv - by < Hf + TILE) || !(vv + by > -TILE)) {
+                        tx1 = -1;  // far outside (also guards the float->int conversions)
+                    }
+                    if (tx0 > tx1 || ty0 > ty1) v = false;
+                }
+            }
+        }
+        // kept tiles: per thread for small rectangles, warp-cooperative for large ones
+        const uint32_t wdt = v ? (uint32_t)(tx1 - tx0 + 1) : 0u;
+        const uint32_t area = v ? wdt * (uint32_t)(ty1 - ty0 + 1) : 0u;
+        cand += area;
+        const float thre = thr - TILE_EPS;
+        uint32_t nt = 0;
+        const bool coop = !canonical && area > COOP_MIN_AREA;
+        if (v && !coop) {
+            if (canonical) {
+                nt = area;
+            } else {
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx)
+                        nt += tile_keep(u, vv, ca, cb, cc, rx, ry, thre, tx, ty, Wf, Hf);
+            }
+        }
+        uint32_t mask = __ballot_sync(0xFFFFFFFFu, coop);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const float su = __shfl_sync(0xFFFFFFFFu, u, src), sv = __shfl_sync(0xFFFFFFFFu, vv, src);
+            const float sa = __shfl_sync(0xFFFFFFFFu, ca, src), sb = __shfl_sync(0xFFFFFFFFu, cb, src);
+            const float sc_ = __shfl_sync(0xFFFFFFFFu, cc, src), srx = __shfl_sync(0xFFFFFFFFu, rx, src);
+            const float sry = __shfl_sync(0xFFFFFFFFu, ry, src), sth = __shfl_sync(0xFFFFFFFFu, thre, src);
+            const int stx0 = __shfl_sync(0xFFFFFFFFu, tx0, src), sty0 = __shfl_sync(0xFFFFFFFFu, ty0, src);
+            const uint32_t sw = __shfl_sync(0xFFFFFFFFu, wdt, src), sarea = __shfl_sync(0xFFFFFFFFu, area, src);
+            uint32_t c = 0;
+            for (uint32_t j = lane; j < sarea; j += 32u)
+                c += tile_keep(su, sv, sa, sb, sc_, srx, sry, sth, stx0 + (int)(j % sw), sty0 + (int)(j / sw), Wf, Hf);
+            c = __reduce_add_sync(0xFFFFFFFFu, c);
+            if (lane == (uint32_t)src) nt = c;
+        }
+        if (nt == 0) v = false;
+
+        float r = 0.f, g = 0.f, bl = 0.f;
+        if (v) {
+            float shc[((3 * K + 7) / 8) * 8];
+            Store<STORE>::template sh<K>(sc, node, shc);
+            float Y[K];
+            const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            sh_basis<DEG>(dx * inv, dy * inv, dz * inv, Y);
+            r = 0.5f; g = 0.5f; bl = 0.5f;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                r = fmaf(shc[3 * kk + 0], Y[kk], r);
+                g = fmaf(shc[3 * kk + 1], Y[kk], g);
+                bl = fmaf(shc[3 * kk + 2], Y[kk], bl);
+            }
+            r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); bl = fmaxf(bl, 0.f);
+        }
+
+        uint32_t total;
+        const uint32_t rank = block_excl_scan<PRE_THREADS / 32>(v ? 1u : 0u, s_scan, &total);
+        if (threadIdx.x == 0) s_prefix = lookback(status, 1, tile, total, epoch, &ctr->flags);
+        __syncthreads();
+        if (v) {
+            const uint32_t o = s_prefix + rank;
+            if (o < cap_vis) {
+                vis.node[o] = node;
+                vis.depth[o] = zbits;
+                vis.ntile[o] = nt;
+                vis.rect[o] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+                vis.recA[o] = make_float4(u, vv, -0.5f * ca, -cb);
+                vis.recB[o] = make_float4(-0.5f * cc, thr, theta, r);
+                vis.recC[o] = make_float2(g, bl);
+            }
+        }
+        if (tile == ntiles - 1 && threadIdx.x == 0) {
+            const uint32_t nv = s_prefix + total;
+            ctr->n_vis = nv;
+            if (nv > cap_vis) atomicOr(&ctr->flags, F_OVF_VIS);
+        }
+        __syncthreads();
+    }
+    unsigned long long wc = cand;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wc += __shfl_down_sync(0xFFFFFFFFu, wc, o);
+    if (lane == 0 && wc) atomicAdd(&ctr->n_cand, wc);
+}
+
+// ln(opacity) next to the opacity (Eq. 4 needs ln theta per Gaussian)
+__global__ void k_prepare(float4* covB, uint32_t n, int half) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 b = covB[i];
+        if (half) b.y = logf(b.x);
+        else b.w = logf(b.z);
+        covB[i] = b;
+    }
+}
+
+void prepare_scene(float4* covB, uint32_t n, cudaStream_t s) {
+    k_prepare<<<1024, 256, 0, s>>>(covB, n, 0);
+}
+void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
+    k_prepare<<<1024, 256, 0, s>>>(covB, n, 1);
+}
+
+template <int DEG, int STORE>
+static void launch_pre_t(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
+                         const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
+                         Counters* ctr, int grid, cudaStream_t s) {
+    k_preprocess<DEG, STORE><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
+}
+
+void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
+                       const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
+                       Counters* ctr, int grid, cudaStream_t s) {
+    const bool half = sc.storage == VGR_STORE_HALF;
+#define VGR_PRE_CASE(D)                                                                        \
+    case D:                                                                                    \
+        if (half) launch_pre_t<D, VGR_STORE_HALF>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr, grid, s); \
+        else launch_pre_t<D, VGR_STORE_FP32>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr, grid, s);      \
+        break;
+    switch (sc.sh_degree) {
+        VGR_PRE_CASE(0)
+        VGR_PRE_CASE(1)
+        VGR_PRE_CASE(2)
+        VGR_PRE_CASE(3)
+        default: break;
+    }
+#undef VGR_PRE_CASE
+}
+
+uint32_t preprocess_tile() { return PRE_THREADS; }
+
+}  // namespace vgr

@@ -1,0 +1,796 @@
+// vgr_capi.cu -- the C ABI (include/vgr.h): hierarchy upload and validation,
+// per-view buffers, and the per-frame launch sequence
+//   LoD (temporal update or top-down levels) -> cut compaction ->
+//   preprocess -> depth sort -> emission -> tile sort -> ranges -> blend
+// all enqueued on the view's stream.  Counts stay on the device (every
+// kernel reads its element count from device memory), so a frame needs no
+// host round trip until its end, where a 48-byte status block is read back:
+// buffer overflows are handled by growing the buffer and replaying the
+// frame, a temporal update that ran past its budget by replaying the frame
+// with the top-down cut.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vgr.h"
+#include "vgr_internal.cuh"
+#include "vgr_launch.h"
+
+using namespace vgr;
+
+namespace {
+
+thread_local std::string g_err;
+
+vgr_status fail(vgr_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define VGR_CK(call)                                                                                        \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess) {                                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? VGR_E_NOMEM : VGR_E_CUDA, "%s failed: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                                 \
+        }                                                                                                   \
+    } while (0)
+
+template <typename T>
+vgr_status dalloc(T** p, size_t count, uint64_t* acct) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    VGR_CK(cudaMalloc((void**)p, count * sizeof(T)));
+    VGR_CK(cudaMemset(*p, 0, count * sizeof(T)));
+    if (acct) *acct += count * sizeof(T);
+    return VGR_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+}  // namespace
+
+struct vgr_hierarchy {
+    SceneDev dev{};
+    float4* cr = nullptr;
+    uint32_t* parent = nullptr;
+    uint32_t* child = nullptr;
+    float4* covA = nullptr;
+    float4* covB = nullptr;
+    void* sh = nullptr;
+    uint32_t n_nodes = 0, max_depth = 0;
+    uint64_t bytes = 0;
+    int device = 0;
+    int num_sms = 0;
+};
+
+struct vgr_view {
+    vgr_hierarchy* h = nullptr;
+    vgr_view_opts opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int grid_wide = 0, grid_scan = 0;
+    // capacities
+    uint32_t cap_cut = 0, cap_vis = 0;
+    uint64_t cap_pairs = 0;
+    uint32_t cap_pixels = 0, cap_tiles = 0;
+    // device buffers
+    uint32_t* cut[2] = {nullptr, nullptr};
+    uint32_t* bitmap = nullptr;
+    uint32_t n_words = 0;
+    uint32_t* frontier[2] = {nullptr, nullptr};
+    VisBuffers vis{};
+    uint32_t* sortK[2] = {nullptr, nullptr};
+    uint32_t* sortV[2] = {nullptr, nullptr};
+    float4* srecA = nullptr;
+    float4* srecB = nullptr;
+    float2* srecC = nullptr;
+    uint32_t* pairK[2] = {nullptr, nullptr};
+    uint32_t* pairV[2] = {nullptr, nullptr};
+    uint2* ranges = nullptr;
+    float* image = nullptr;
+    float* lut = nullptr;
+    unsigned long long* status = nullptr;
+    size_t st_compact = 0, st_pre = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
+           st_tile_stride = 0, st_words = 0;
+    Counters* ctr = nullptr;
+    ViewState* vstate = nullptr;
+    FrameParams* fp_dev = nullptr;
+    // pinned host mirrors
+    FrameParams* fp_host = nullptr;
+    unsigned char* ctr_host = nullptr;
+    ViewState* vstate_host = nullptr;
+    cudaEvent_t ev[VGR_N_STAGES + 1] = {};
+    // temporal state
+    bool has_prev = false;
+    int parity = 0;  // buffer index holding the previous cut
+    float prev_tau = -1.f, prev_f = -1.f;
+    uint32_t epoch = 0;
+    // last frame
+    uint32_t last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
+    int last_tile_buf = 0;
+    uint32_t last_n_cut = 0, last_n_vis = 0;
+    uint64_t last_n_pairs = 0;
+    uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
+};
+
+extern "C" {
+
+const char* vgr_last_error(void) { return g_err.c_str(); }
+
+void vgr_default_view_opts(vgr_view_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->filter = VGR_FILTER_PREEMPTIVE;
+    o->exp_mode = VGR_EXP_EXACT;
+    o->lut_size = 32;
+    o->temporal = 1;
+    o->timing = 0;
+    o->use_graph = 0;
+    o->lod_budget = 4096;
+}
+
+// ------------------------------------------------------------- hierarchy
+vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
+    if (!d || !out) return fail(VGR_E_INVALID, "null argument");
+    *out = nullptr;
+    const uint32_t N = d->n_nodes;
+    if (N == 0 || N > CHILD_MASK) return fail(VGR_E_INVALID, "n_nodes must be in [1, 2^28)");
+    if (d->sh_degree > 3) return fail(VGR_E_INVALID, "sh_degree must be <= 3");
+    if (d->storage != VGR_STORE_FP32 && d->storage != VGR_STORE_HALF) return fail(VGR_E_INVALID, "bad storage");
+    if (!d->parent || !d->first_child || !d->n_child || !d->mean || !d->cov6 || !d->opacity || !d->sh ||
+        !d->radius2)
+        return fail(VGR_E_INVALID, "null array in scene description");
+    // shape: BFS order, contiguous child blocks, parent links
+    if (d->parent[0] != NONE) return fail(VGR_E_INVALID, "node 0 must be the root (parent 0xFFFFFFFF)");
+    std::vector<uint8_t> depth(N, 0);
+    uint64_t expect = 1;
+    uint32_t maxd = 0;
+    for (uint32_t n = 0; n < N; ++n) {
+        const uint32_t nc = d->n_child[n];
+        if (nc > 8) return fail(VGR_E_INVALID, "node %u has %u > 8 children", n, nc);
+        if (nc == 0) continue;
+        if (d->first_child[n] != expect)
+            return fail(VGR_E_INVALID, "children of node %u are not the next BFS block (first_child %u, expected %llu)",
+                        n, d->first_child[n], (unsigned long long)expect);
+        if (expect + nc > N) return fail(VGR_E_INVALID, "children of node %u run past n_nodes", n);
+        for (uint32_t c = 0; c < nc; ++c) {
+            const uint32_t ch = (uint32_t)expect + c;
+            if (d->parent[ch] != n) return fail(VGR_E_INVALID, "parent[%u] != %u", ch, n);
+            const uint32_t dd = depth[n] + 1u;
+            if (dd >= MAX_TREE_DEPTH - 2) return fail(VGR_E_INVALID, "tree deeper than %d", MAX_TREE_DEPTH - 3);
+            depth[ch] = (uint8_t)dd;
+            maxd = std::max(maxd, dd);
+        }
+        expect += nc;
+    }
+    if (expect != N) return fail(VGR_E_INVALID, "not every node is reachable from the root (%llu of %u)",
+                                 (unsigned long long)expect, N);
+    for (uint32_t n = 0; n < N; ++n) {
+        const float* m = d->mean + 3 * (size_t)n;
+        if (!std::isfinite(m[0]) || !std::isfinite(m[1]) || !std::isfinite(m[2]))
+            return fail(VGR_E_INVALID, "mean of node %u is not finite", n);
+        const float op = d->opacity[n];
+        if (!(op >= 0.f && op <= 1.f)) return fail(VGR_E_INVALID, "opacity of node %u outside [0, 1]", n);
+        const float r2 = d->radius2[n];
+        if (!(r2 >= 0.f) || !std::isfinite(r2)) return fail(VGR_E_INVALID, "radius2 of node %u invalid", n);
+        for (int k = 0; k < 6; ++k)
+            if (!std::isfinite(d->cov6[6 * (size_t)n + k])) return fail(VGR_E_INVALID, "cov of node %u not finite", n);
+        if (n > 0) {
+            const uint32_t p = d->parent[n];
+            const float* mp = d->mean + 3 * (size_t)p;
+            const double dx = (double)m[0] - mp[0], dy = (double)m[1] - mp[1], dz = (double)m[2] - mp[2];
+            const double need = std::sqrt((double)r2) + std::sqrt(dx * dx + dy * dy + dz * dz);
+            if (std::sqrt((double)d->radius2[p]) < need * (1.0 - 1e-6))
+                return fail(VGR_E_INVALID, "radius of node %u does not contain child %u (nesting violated)", p, n);
+        }
+    }
+
+    int dev = 0;
+    VGR_CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    VGR_CK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major * 10 + prop.minor < 100)
+        return fail(VGR_E_CUDA, "device %s (sm_%d%d) is not a Blackwell GPU", prop.name, prop.major, prop.minor);
+
+    vgr_hierarchy* h = new vgr_hierarchy();
+    h->n_nodes = N;
+    h->max_depth = maxd;
+    h->device = dev;
+    h->num_sms = prop.multiProcessorCount;
+    const uint32_t K3 = 3u * (d->sh_degree + 1) * (d->sh_degree + 1);
+    const bool half = d->storage == VGR_STORE_HALF;
+    const uint32_t stride = half ? (K3 + 7u) / 8u * 8u : (K3 + 3u) / 4u * 4u;
+    vgr_status st = VGR_OK;
+    auto cleanup = [&]() { dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
+                           if (h->sh) cudaFree(h->sh); delete h; };
+#define VGR_TRY(x)                 \
+    do {                           \
+        st = (x);                  \
+        if (st != VGR_OK) {        \
+            cleanup();             \
+            return st;             \
+        }                          \
+    } while (0)
+    VGR_TRY(dalloc(&h->cr, N, &h->bytes));
+    VGR_TRY(dalloc(&h->parent, N, &h->bytes));
+    VGR_TRY(dalloc(&h->child, N, &h->bytes));
+    VGR_TRY(dalloc(&h->covA, N, &h->bytes));
+    VGR_TRY(dalloc(&h->covB, N, &h->bytes));
+    {
+        const size_t shb = (size_t)N * stride * (half ? 2 : 4);
+        cudaError_t e = cudaMalloc(&h->sh, shb);
+        if (e != cudaSuccess) { cleanup(); return fail(VGR_E_NOMEM, "cudaMalloc sh (%zu bytes): %s", shb, cudaGetErrorString(e)); }
+        h->bytes += shb;
+    }
+    // staging in chunks through a pinned buffer
+    const uint32_t CH = 1u << 20;
+    void* pin = nullptr;
+    const size_t pin_bytes = (size_t)CH * std::max<size_t>(64, (size_t)K3 * 4);
+    if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) { cleanup(); return fail(VGR_E_NOMEM, "pinned staging"); }
+    float* tmp_dev = nullptr;
+    if (half) {
+        if (cudaMalloc(&tmp_dev, (size_t)CH * std::max<uint32_t>(K3, 6) * 4) != cudaSuccess) {
+            cudaFreeHost(pin); cleanup(); return fail(VGR_E_NOMEM, "conversion buffer");
+        }
+    }
+    cudaError_t ce = cudaSuccess;
+    for (uint32_t b = 0; b < N && ce == cudaSuccess; b += CH) {
+        const uint32_t cnt = std::min(CH, N - b);
+        float4* f4 = (float4*)pin;
+        for (uint32_t i = 0; i < cnt; ++i) {
+            const uint32_t n = b + i;
+            const float* m = d->mean + 3 * (size_t)n;
+            f4[i] = make_float4(m[0], m[1], m[2], d->n_child[n] ? d->radius2[n] : 0.f);
+        }
+        ce = cudaMemcpy(h->cr + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
+        uint32_t* u = (uint32_t*)pin;
+        for (uint32_t i = 0; i < cnt; ++i) {
+            const uint32_t n = b + i;
+            u[i] = d->n_child[n] ? (d->first_child[n] | ((uint32_t)d->n_child[n] << CHILD_SHIFT)) : 0u;
+        }
+        if (ce == cudaSuccess) ce = cudaMemcpy(h->child + b, u, cnt * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(h->parent + b, d->parent + b, cnt * 4, cudaMemcpyHostToDevice);
+        if (!half) {
+            for (uint32_t i = 0; i < cnt; ++i) {
+                const float* c = d->cov6 + 6 * (size_t)(b + i);
+                f4[i] = make_float4(c[0], c[1], c[2], c[3]);
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpy(h->covA + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
+            for (uint32_t i = 0; i < cnt; ++i) {
+                const float* c = d->cov6 + 6 * (size_t)(b + i);
+                f4[i] = make_float4(c[4], c[5], d->opacity[b + i], 0.f);
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpy(h->covB + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
+            float* fs = (float*)pin;
+            for (uint32_t i = 0; i < cnt; ++i) {
+                const float* s = d->sh + (size_t)(b + i) * K3;
+                float* o = fs + (size_t)i * stride;
+                memcpy(o, s, K3 * 4);
+                for (uint32_t j = K3; j < stride; ++j) o[j] = 0.f;
+            }
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy((float*)h->sh + (size_t)b * stride, fs, (size_t)cnt * stride * 4, cudaMemcpyHostToDevice);
+        } else {
+            if (ce == cudaSuccess) ce = cudaMemcpy(tmp_dev, d->cov6 + 6 * (size_t)b, (size_t)cnt * 24, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess) { convert_cov_bf16(tmp_dev, cnt, h->covA + b, 0); ce = cudaDeviceSynchronize(); }
+            for (uint32_t i = 0; i < cnt; ++i) f4[i] = make_float4(d->opacity[b + i], 0.f, 0.f, 0.f);
+            if (ce == cudaSuccess) ce = cudaMemcpy(h->covB + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy(tmp_dev, d->sh + (size_t)b * K3, (size_t)cnt * K3 * 4, cudaMemcpyHostToDevice);
+            if (ce == cudaSuccess) {
+                convert_sh_half(tmp_dev, cnt, K3, (char*)h->sh + (size_t)b * stride * 2, stride, 0);
+                ce = cudaDeviceSynchronize();
+            }
+        }
+    }
+    cudaFreeHost(pin);
+    if (tmp_dev) cudaFree(tmp_dev);
+    if (ce != cudaSuccess) {
+        cleanup();
+        return fail(VGR_E_CUDA, "hierarchy upload: %s", cudaGetErrorString(ce));
+    }
+    if (half) prepare_scene_half(h->covB, N, 0);
+    else prepare_scene(h->covB, N, 0);
+    ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) { cleanup(); return fail(VGR_E_CUDA, "prepare: %s", cudaGetErrorString(ce)); }
+#undef VGR_TRY
+    h->dev.cr = h->cr;
+    h->dev.parent = h->parent;
+    h->dev.child = h->child;
+    h->dev.covA = h->covA;
+    h->dev.covB = h->covB;
+    h->dev.sh = h->sh;
+    h->dev.n_nodes = N;
+    h->dev.sh_degree = d->sh_degree;
+    h->dev.sh_stride = stride;
+    h->dev.storage = (uint32_t)d->storage;
+    *out = h;
+    return VGR_OK;
+}
+
+vgr_status vgr_free_hierarchy(vgr_hierarchy* h) {
+    if (!h) return fail(VGR_E_INVALID, "null hierarchy");
+    cudaSetDevice(h->device);
+    dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
+    if (h->sh) cudaFree(h->sh);
+    delete h;
+    return VGR_OK;
+}
+
+vgr_status vgr_hierarchy_info(const vgr_hierarchy* h, uint64_t* bytes, uint32_t* max_depth) {
+    if (!h) return fail(VGR_E_INVALID, "null hierarchy");
+    if (bytes) *bytes = h->bytes;
+    if (max_depth) *max_depth = h->max_depth;
+    return VGR_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ views
+namespace {
+
+void free_vis(vgr_view* v) {
+    dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
+    dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.recC);
+    for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
+    dfree(v->srecA); dfree(v->srecB); dfree(v->srecC);
+    v->vis_bytes = 0;
+}
+
+vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
+    free_vis(v);
+    uint64_t b = 0;
+    vgr_status s;
+    if ((s = dalloc(&v->vis.node, cap, &b)) || (s = dalloc(&v->vis.depth, cap, &b)) ||
+        (s = dalloc(&v->vis.ntile, cap, &b)) || (s = dalloc(&v->vis.rect, cap, &b)) ||
+        (s = dalloc(&v->vis.recA, cap, &b)) || (s = dalloc(&v->vis.recB, cap, &b)) ||
+        (s = dalloc(&v->vis.recC, cap, &b)) || (s = dalloc(&v->sortK[0], cap, &b)) ||
+        (s = dalloc(&v->sortK[1], cap, &b)) || (s = dalloc(&v->sortV[0], cap, &b)) ||
+        (s = dalloc(&v->sortV[1], cap, &b)) || (s = dalloc(&v->srecA, cap, &b)) ||
+        (s = dalloc(&v->srecB, cap, &b)) || (s = dalloc(&v->srecC, cap, &b))) {
+        free_vis(v);
+        return s;
+    }
+    v->cap_vis = cap;
+    v->vis_bytes = b;
+    return VGR_OK;
+}
+
+void free_pairs(vgr_view* v) {
+    for (int i = 0; i < 2; ++i) { dfree(v->pairK[i]); dfree(v->pairV[i]); }
+    v->pair_bytes = 0;
+}
+
+vgr_status alloc_pairs(vgr_view* v, uint64_t cap) {
+    free_pairs(v);
+    uint64_t b = 0;
+    vgr_status s;
+    if ((s = dalloc(&v->pairK[0], cap, &b)) || (s = dalloc(&v->pairK[1], cap, &b)) ||
+        (s = dalloc(&v->pairV[0], cap, &b)) || (s = dalloc(&v->pairV[1], cap, &b))) {
+        free_pairs(v);
+        return s;
+    }
+    v->cap_pairs = cap;
+    v->pair_bytes = b;
+    return VGR_OK;
+}
+
+void free_cut(vgr_view* v) {
+    dfree(v->cut[0]); dfree(v->cut[1]);
+    v->cut_bytes = 0;
+}
+
+vgr_status alloc_cut(vgr_view* v, uint32_t cap) {
+    free_cut(v);
+    uint64_t b = 0;
+    vgr_status s;
+    if ((s = dalloc(&v->cut[0], cap, &b)) || (s = dalloc(&v->cut[1], cap, &b))) {
+        free_cut(v);
+        return s;
+    }
+    v->cap_cut = cap;
+    v->cut_bytes = b;
+    return VGR_OK;
+}
+
+// look-back word regions; sized from the current capacities
+vgr_status alloc_status(vgr_view* v) {
+    dfree(v->status);
+    const uint32_t RT = radix_tile();
+    v->st_compact = 0;
+    v->st_pre = v->st_compact + cut_compact_tiles(v->n_words) + 1;
+    v->st_emit = v->st_pre + ceil_div(v->cap_cut, preprocess_tile()) + 1;
+    v->st_depth = v->st_emit + ceil_div(v->cap_vis, emit_tile()) + 1;
+    v->st_depth_stride = (size_t)(ceil_div(v->cap_vis, RT) + 1) * 256;
+    v->st_tile = v->st_depth + 4 * v->st_depth_stride;
+    v->st_tile_stride = (size_t)(ceil_div(v->cap_pairs, RT) + 1) * 256;
+    v->st_words = v->st_tile + 4 * v->st_tile_stride;
+    uint64_t b = 0;
+    vgr_status s = dalloc(&v->status, v->st_words, &b);
+    v->status_bytes = b;
+    return s;
+}
+
+vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
+    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
+    const uint64_t px = (uint64_t)W * H, tiles = (uint64_t)TW * TH;
+    if (px <= v->cap_pixels && tiles <= v->cap_tiles) return VGR_OK;
+    dfree(v->image);
+    dfree(v->ranges);
+    v->img_bytes = 0;
+    const uint32_t cp = (uint32_t)std::max<uint64_t>(px, v->cap_pixels);
+    const uint32_t ct = (uint32_t)std::max<uint64_t>(tiles, v->cap_tiles);
+    vgr_status s;
+    if ((s = dalloc(&v->image, (size_t)cp * 3, &v->img_bytes)) || (s = dalloc(&v->ranges, ct, &v->img_bytes))) {
+        v->cap_pixels = v->cap_tiles = 0;
+        return s;
+    }
+    v->cap_pixels = cp;
+    v->cap_tiles = ct;
+    return VGR_OK;
+}
+
+void destroy_view(vgr_view* v) {
+    free_vis(v);
+    free_pairs(v);
+    free_cut(v);
+    dfree(v->bitmap); dfree(v->frontier[0]); dfree(v->frontier[1]);
+    dfree(v->ranges); dfree(v->image); dfree(v->lut); dfree(v->status);
+    dfree(v->ctr); dfree(v->vstate); dfree(v->fp_dev);
+    if (v->fp_host) cudaFreeHost(v->fp_host);
+    if (v->ctr_host) cudaFreeHost(v->ctr_host);
+    if (v->vstate_host) cudaFreeHost(v->vstate_host);
+    for (auto& e : v->ev)
+        if (e) cudaEventDestroy(e);
+    if (v->own_stream && v->stream) cudaStreamDestroy(v->stream);
+    delete v;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view** out) {
+    if (!h || !out) return fail(VGR_E_INVALID, "null argument");
+    *out = nullptr;
+    VGR_CK(cudaSetDevice(h->device));
+    vgr_view* v = new vgr_view();
+    v->h = h;
+    if (opts) v->opts = *opts;
+    else vgr_default_view_opts(&v->opts);
+    if (v->opts.filter > VGR_FILTER_CANONICAL || v->opts.exp_mode > VGR_EXP_LUT) {
+        delete v;
+        return fail(VGR_E_INVALID, "bad filter or exp_mode");
+    }
+    if (v->opts.lut_size == 0) v->opts.lut_size = 32;
+    if (v->opts.lut_size > 256) { delete v; return fail(VGR_E_INVALID, "lut_size must be <= 256"); }
+    if (v->opts.lod_budget == 0) v->opts.lod_budget = 4096;
+    const uint32_t N = h->n_nodes;
+    vgr_status s = VGR_OK;
+#define VGR_VTRY(x)                 \
+    do {                            \
+        s = (x);                    \
+        if (s != VGR_OK) {          \
+            destroy_view(v);        \
+            return s;               \
+        }                           \
+    } while (0)
+    if (v->opts.stream) {
+        v->stream = (cudaStream_t)v->opts.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete v; return fail(VGR_E_CUDA, "stream: %s", cudaGetErrorString(e)); }
+        v->own_stream = true;
+    }
+    v->grid_wide = h->num_sms * 8;
+    v->grid_scan = h->num_sms * 4;
+    const uint32_t cap_cut = (uint32_t)std::min<uint64_t>(N, v->opts.cut_capacity ? v->opts.cut_capacity
+                                                                                  : std::max<uint64_t>(1u << 20, N / 4));
+    const uint32_t cap_vis = std::min<uint32_t>(cap_cut, std::max<uint32_t>(1u << 19, cap_cut / 2));
+    const uint64_t cap_pairs = v->opts.pair_capacity ? v->opts.pair_capacity : (uint64_t)4 * cap_vis;
+    VGR_VTRY(alloc_cut(v, cap_cut));
+    VGR_VTRY(alloc_vis(v, cap_vis));
+    VGR_VTRY(alloc_pairs(v, cap_pairs));
+    const uint32_t TW = cut_compact_tile_words();
+    v->n_words = (uint32_t)(((uint64_t)(N + 31) / 32 + TW - 1) / TW * TW);
+    VGR_VTRY(dalloc(&v->bitmap, v->n_words, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->frontier[0], N, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->frontier[1], N, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->ctr, 1, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->vstate, 1, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->fp_dev, 1, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->lut, 260, &v->fixed_bytes));
+    VGR_VTRY(alloc_status(v));
+    if (cudaMallocHost((void**)&v->fp_host, sizeof(FrameParams)) != cudaSuccess ||
+        cudaMallocHost((void**)&v->ctr_host, sizeof(Counters)) != cudaSuccess ||
+        cudaMallocHost((void**)&v->vstate_host, sizeof(ViewState)) != cudaSuccess) {
+        destroy_view(v);
+        return fail(VGR_E_NOMEM, "pinned host buffers");
+    }
+    memset(v->fp_host, 0, sizeof(FrameParams));
+    memset(v->ctr_host, 0, sizeof(Counters));
+    for (auto& e : v->ev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
+    }
+    // Eq. 5 table: entry i = e^(-5.55 i / m), i = 0..m
+    {
+        float host_lut[260] = {0};
+        const uint32_t m = v->opts.lut_size;
+        for (uint32_t i = 0; i <= m; ++i) host_lut[i] = (float)std::exp(-5.55 * (double)i / (double)m);
+        cudaError_t ce = cudaMemcpy(v->lut, host_lut, sizeof(host_lut), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "lut: %s", cudaGetErrorString(ce)); }
+    }
+#undef VGR_VTRY
+    *out = v;
+    return VGR_OK;
+}
+
+vgr_status vgr_destroy_view(vgr_view* v) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    cudaSetDevice(v->h->device);
+    if (v->stream) cudaStreamSynchronize(v->stream);
+    destroy_view(v);
+    return VGR_OK;
+}
+
+vgr_status vgr_reset_view(vgr_view* v) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    v->has_prev = false;
+    return VGR_OK;
+}
+
+vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes) {
+    if (!v || !bytes) return fail(VGR_E_INVALID, "null argument");
+    *bytes = v->vis_bytes + v->pair_bytes + v->img_bytes + v->fixed_bytes + v->status_bytes + v->cut_bytes;
+    return VGR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int tile_passes_for(uint32_t n_tiles) {
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) < n_tiles) ++bits;
+    return std::max(1, (bits + 7) / 8);
+}
+
+// Enqueue one frame.  'scratch' selects the top-down cut.
+void enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
+    const SceneDev& sc = v->h->dev;
+    cudaStream_t s = v->stream;
+    const bool timing = v->opts.timing != 0;
+    auto mark = [&](int i) { if (timing) cudaEventRecord(v->ev[i], s); };
+    const FrameParams& fh = *v->fp_host;
+    const uint32_t n_tiles = fh.tiles_x * fh.tiles_y;
+    cudaMemcpyAsync(v->fp_dev, v->fp_host, sizeof(FrameParams), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(v->ctr, 0, sizeof(Counters), s);
+    cudaMemsetAsync(v->ranges, 0, (size_t)n_tiles * sizeof(uint2), s);
+    const int prev = v->parity, cur = v->parity ^ 1;
+    mark(VGR_STAGE_LOD);
+    if (scratch) {
+        for (uint32_t level = 0; level <= v->h->max_depth; ++level)
+            launch_lod_level((int)level, sc, v->frontier[level & 1], v->frontier[(level + 1) & 1], v->h->n_nodes,
+                             v->fp_dev, v->bitmap, v->ctr, v->grid_wide, s);
+    } else {
+        launch_lod_update(sc, v->cut[prev], &v->vstate->n_cut[prev], v->cap_cut, v->fp_dev, v->bitmap, v->ctr,
+                          v->grid_wide, s);
+    }
+    mark(VGR_STAGE_COMPACT);
+    launch_cut_compact(v->bitmap, v->n_words, v->cut[cur], v->cap_cut, &v->vstate->n_cut[cur],
+                       v->status + v->st_compact, v->ctr, v->fp_dev, v->grid_scan, s);
+    mark(VGR_STAGE_PREPROCESS);
+    launch_preprocess(sc, v->cut[cur], &v->vstate->n_cut[cur], v->cap_cut, v->fp_dev, v->vis, v->cap_vis,
+                      v->status + v->st_pre, v->ctr, v->grid_scan, s);
+    mark(VGR_STAGE_DEPTH_SORT);
+    launch_radix_hist(v->vis.depth, &v->ctr->n_vis, nullptr, v->cap_vis, 4, &v->ctr->depth_hist[0][0],
+                      v->grid_scan, s);
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t* kin = p == 0 ? v->vis.depth : v->sortK[(p + 1) & 1];
+        const uint32_t* vin = p == 0 ? nullptr : v->sortV[(p + 1) & 1];
+        launch_radix_pass(kin, vin, v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_vis, nullptr, v->cap_vis, 8 * p,
+                          v->ctr->depth_hist[p], v->status + v->st_depth + p * v->st_depth_stride,
+                          &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
+    }
+    const uint32_t* order = v->sortV[1];  // after 4 passes
+    mark(VGR_STAGE_EMIT);
+    launch_emit(order, v->cap_vis, v->vis, v->srecA, v->srecB, v->srecC, v->pairK[0], v->pairV[0], v->cap_pairs,
+                tile_passes, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, s);
+    mark(VGR_STAGE_TILE_SORT);
+    for (int p = 0; p < tile_passes; ++p) {
+        launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
+                          &v->ctr->n_pairs, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
+                          v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
+                          v->fp_dev, v->ctr, v->grid_scan, s);
+    }
+    const int fb = tile_passes & 1;
+    v->last_tile_buf = fb;
+    mark(VGR_STAGE_RANGES);
+    launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, v->ranges, v->grid_wide, s);
+    mark(VGR_STAGE_BLEND);
+    launch_blend(n_tiles, v->ranges, v->pairV[fb], v->srecA, v->srecB, v->srecC, v->fp_dev, v->lut, v->image, v->ctr,
+                 v->opts.filter, v->opts.exp_mode, s);
+    mark(VGR_N_STAGES);
+    cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
+}
+
+vgr_status check_camera(const vgr_camera* c, float tau) {
+    if (!c) return fail(VGR_E_INVALID, "null camera");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(c->R[i])) return fail(VGR_E_INVALID, "camera R not finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(c->pos[i])) return fail(VGR_E_INVALID, "camera position not finite");
+    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !std::isfinite(c->fx) || !std::isfinite(c->fy))
+        return fail(VGR_E_INVALID, "focal lengths must be positive");
+    if (!std::isfinite(c->cx) || !std::isfinite(c->cy)) return fail(VGR_E_INVALID, "principal point not finite");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        return fail(VGR_E_INVALID, "image size must be in [1, 16384]");
+    if (!(c->z_near > 0.f) || !std::isfinite(c->z_near)) return fail(VGR_E_INVALID, "z_near must be > 0");
+    const float f = std::max(c->fx, c->fy);
+    if (!(tau >= 0.f) || !(tau <= f)) return fail(VGR_E_INVALID, "tau must be in [0, max(fx, fy)]");
+    return VGR_OK;
+}
+
+vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    vgr_status s = check_camera(cam, tau);
+    if (s != VGR_OK) return s;
+    VGR_CK(cudaSetDevice(v->h->device));
+    const uint32_t W = cam->width, H = cam->height;
+    if ((s = ensure_image(v, W, H)) != VGR_OK) return s;
+    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
+    const int tile_passes = tile_passes_for(TW * TH);
+    volatile float f = std::max(cam->fx, cam->fy);
+    volatile float t = tau / f;
+    volatile float k = t * t;
+    bool scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || f != v->prev_f;
+    uint32_t replays = 0;
+    uint32_t flags = 0;
+    const Counters* ch = reinterpret_cast<const Counters*>(v->ctr_host);
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt);
+        FrameParams& p = *v->fp_host;
+        memcpy(p.R, cam->R, sizeof(p.R));
+        memcpy(p.pos, cam->pos, sizeof(p.pos));
+        p.fx = cam->fx; p.fy = cam->fy; p.cx = cam->cx; p.cy = cam->cy;
+        p.z_near = cam->z_near;
+        p.k = k;
+        p.limx = 1.3f * (0.5f * (float)W / cam->fx);
+        p.limy = 1.3f * (0.5f * (float)H / cam->fy);
+        p.width_f = (float)W; p.height_f = (float)H;
+        p.width = W; p.height = H; p.tiles_x = TW; p.tiles_y = TH;
+        p.epoch = ++v->epoch;
+        if ((p.epoch & 0x3FFFFFFFu) == 0) p.epoch = ++v->epoch;
+        p.filter = v->opts.filter; p.exp_mode = v->opts.exp_mode; p.lut_size = v->opts.lut_size;
+        p.lut_step = 5.55f / (float)v->opts.lut_size;
+        p.lod_budget = v->opts.lod_budget;
+        p.max_depth = v->h->max_depth;
+        enqueue_frame(v, scratch, tile_passes);
+        VGR_CK(cudaGetLastError());
+        VGR_CK(cudaStreamSynchronize(v->stream));
+        flags = ch->flags;
+        const int cur = v->parity ^ 1;
+        const uint32_t n_cut = v->vstate_host->n_cut[cur];
+        if (flags & F_SPIN_TIMEOUT) return fail(VGR_E_TIMEOUT, "a look-back wait timed out");
+        if (flags & F_NONMONOTONE)
+            return fail(VGR_E_NONMONOTONE, "granularity test not monotone: a child expands while its parent does not");
+        if (flags & F_OVF_FRONTIER) return fail(VGR_E_OVERFLOW, "frontier overflow");
+        if ((flags & F_LOD_FALLBACK) && !scratch) { scratch = true; ++replays; continue; }
+        if (flags & F_LOD_FALLBACK) return fail(VGR_E_TIMEOUT, "top-down cut exceeded the tree depth");
+        if (flags & F_OVF_CUT) {
+            const uint32_t nc = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)n_cut + n_cut / 4 + 1024);
+            if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
+            scratch = true;  // the previous cut lived in the old buffers
+            ++replays;
+            continue;
+        }
+        if (flags & F_OVF_VIS) {
+            const uint32_t nv = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)ch->n_vis + ch->n_vis / 4 + 1024);
+            if ((s = alloc_vis(v, nv)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
+            ++replays;
+            continue;
+        }
+        if (flags & F_OVF_PAIRS) {
+            const uint64_t np = ch->n_pairs + ch->n_pairs / 4 + 4096;
+            if (np >= 0xFFFFFFFFull) return fail(VGR_E_OVERFLOW, "more than 2^32 pairs");
+            if ((s = alloc_pairs(v, np)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
+            ++replays;
+            continue;
+        }
+        break;
+    }
+    const int cur = v->parity ^ 1;
+    v->parity = cur;
+    v->has_prev = true;
+    v->prev_tau = tau;
+    v->prev_f = f;
+    v->last_w = W; v->last_h = H; v->last_tw = TW; v->last_th = TH;
+    v->last_n_cut = v->vstate_host->n_cut[cur];
+    v->last_n_vis = ch->n_vis;
+    v->last_n_pairs = ch->n_pairs;
+    if (host_rgb) {
+        VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               v->stream));
+        VGR_CK(cudaStreamSynchronize(v->stream));
+    }
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->image = v->image;
+        out->cut = v->cut[cur];
+        out->cut_count = v->last_n_cut;
+        out->width = W;
+        out->height = H;
+        vgr_frame_stats& st = out->stats;
+        st.cut_count = v->last_n_cut;
+        st.visible_count = ch->n_vis;
+        st.pair_count = ch->n_pairs;
+        st.candidate_pairs = ch->n_cand;
+        st.nodes_evaluated = ch->nodes_eval;
+        st.lod_from_scratch = scratch ? 1u : 0u;
+        st.replays = replays;
+        if (v->opts.timing) {
+            for (int i = 0; i < VGR_N_STAGES; ++i) cudaEventElapsedTime(&st.stage_ms[i], v->ev[i], v->ev[i + 1]);
+            cudaEventElapsedTime(&st.frame_ms, v->ev[0], v->ev[VGR_N_STAGES]);
+        }
+    }
+    return VGR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vgr_status vgr_render_frame(vgr_view* v, const vgr_camera* cam, float tau, vgr_frame* out) {
+    return render_impl(v, cam, tau, nullptr, out);
+}
+
+vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
+    if (!host_rgb) return fail(VGR_E_INVALID, "null host image");
+    return render_impl(v, cam, tau, host_rgb, out);
+}
+
+vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
+    if (!v || !o) return fail(VGR_E_INVALID, "null argument");
+    if (!v->has_prev) return fail(VGR_E_INVALID, "no frame rendered yet");
+    memset(o, 0, sizeof(*o));
+    o->n_cut = v->last_n_cut;
+    o->n_visible = v->last_n_vis;
+    o->n_pairs = v->last_n_pairs;
+    o->tiles_x = v->last_tw;
+    o->tiles_y = v->last_th;
+    o->cut = v->cut[v->parity];
+    o->vis_node = v->vis.node;
+    o->vis_depth = v->vis.depth;
+    o->vis_ntile = v->vis.ntile;
+    o->vis_rect = reinterpret_cast<const uint32_t*>(v->vis.rect);
+    o->vis_recA = reinterpret_cast<const float*>(v->vis.recA);
+    o->vis_recB = reinterpret_cast<const float*>(v->vis.recB);
+    o->vis_recC = reinterpret_cast<const float*>(v->vis.recC);
+    o->depth_order = v->sortV[1];
+    o->pair_tile = v->pairK[v->last_tile_buf];
+    o->pair_rank = v->pairV[v->last_tile_buf];
+    o->tile_range = reinterpret_cast<const uint32_t*>(v->ranges);
+    return VGR_OK;
+}
+
+}  // extern "C"

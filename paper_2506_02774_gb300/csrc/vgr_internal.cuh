@@ -1,0 +1,189 @@
+// vgr_internal.cuh -- device-side structures and helpers shared by the
+// kernels of the frame path (LoD cut, preprocess, sort, emit, blend).
+#pragma once
+
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vgr.h"
+
+namespace vgr {
+
+constexpr int TILE = 16;                      // 16x16-pixel tiles
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr float ALPHA_MIN = 1.0f / 255.0f;    // alpha* (Sec. 3.1 'Rasterization')
+constexpr float LN_ALPHA_MIN = -5.5412635451584260f;  // ln(1/255)
+constexpr float T_MIN = 1e-4f;                // early-termination transmittance
+constexpr float ALPHA_MAX = 0.99f;            // Eq. 3 clamp
+constexpr float DILATE = 0.3f;                // low-pass added to the 2D covariance
+constexpr float TILE_EPS = 2e-3f;             // slack of the FP32 tile-level test (nats)
+constexpr int MAX_TREE_DEPTH = 64;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;     // bounded waits in look-back scans
+constexpr uint32_t CHILD_SHIFT = 28;          // child word: first_child | n_child << 28
+constexpr uint32_t CHILD_MASK = (1u << CHILD_SHIFT) - 1u;
+
+// flags in Counters::flags
+enum : uint32_t {
+    F_LOD_FALLBACK = 1u,   // a thread exceeded its expansion budget: redo the cut top-down
+    F_NONMONOTONE = 2u,    // child expands while the parent does not
+    F_SPIN_TIMEOUT = 4u,   // a look-back wait ran out
+    F_OVF_CUT = 8u,
+    F_OVF_VIS = 16u,
+    F_OVF_PAIRS = 32u,
+    F_OVF_FRONTIER = 64u,
+};
+
+// ticket slots (dynamic tile order for the chained scans)
+enum : int { TK_COMPACT = 0, TK_PRE = 1, TK_EMIT = 2, TK_SORT0 = 3 /* .. TK_SORT0 + 7 */, TK_COUNT = 12 };
+
+// Per-frame parameters, uploaded once per frame (a graph replays them).
+struct FrameParams {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy;
+    float z_near;
+    float k;           // fl(fl(tau/f)^2)
+    float limx, limy;  // 1.3 (W/2)/fx, 1.3 (H/2)/fy
+    float width_f, height_f;
+    uint32_t width, height, tiles_x, tiles_y;
+    uint32_t epoch;    // tags look-back words; new value per launch sequence
+    uint32_t filter, exp_mode, lut_size;
+    float lut_step;    // 5.55 / m
+    uint32_t lod_budget;
+    uint32_t max_depth;
+    uint32_t pad[3];
+};
+
+// Zeroed at the start of every frame.  Scalars first: the host reads back
+// only the head of the struct.
+struct Counters {
+    uint32_t n_vis;
+    uint32_t flags;
+    unsigned long long n_pairs;
+    unsigned long long n_cand;
+    unsigned long long nodes_eval;
+    unsigned long long pix_evals;
+    uint32_t tickets[TK_COUNT];
+    uint32_t frontier_n[MAX_TREE_DEPTH + 2];
+    uint32_t depth_hist[4][256];
+    uint32_t tile_hist[4][256];
+};
+constexpr size_t COUNTERS_HEAD = 48;  // bytes read back per frame
+
+// Persistent per-view values (not cleared per frame).
+struct ViewState {
+    uint32_t n_cut[2];
+};
+
+// Device view of the hierarchy.
+struct SceneDev {
+    const float4* cr;          // mean xyz, w = radius2 (internal) or 0 (leaf)
+    const uint32_t* parent;
+    const uint32_t* child;     // first_child | n_child << 28
+    const float4* covA;        // xx xy xz yy
+    const float4* covB;        // yz zz opacity ln(opacity)
+    const void* sh;            // FP32 or FP16, sh_stride elements per node
+    uint32_t n_nodes;
+    uint32_t sh_degree;
+    uint32_t sh_stride;        // elements per node (multiple of 4 for FP32, 8 for FP16)
+    uint32_t storage;          // VGR_STORE_*
+};
+
+// ------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive warp scan of v over all 32 lanes; *total gets the warp sum.
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t* total) {
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane_id() >= (uint32_t)o) x += y;
+    }
+    *total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    return x - v;
+}
+
+// Block-wide exclusive scan (blockDim.x = 32 * NW).  smem: NW + 1 words.
+template <int NW>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem, uint32_t* total) {
+    uint32_t wt;
+    uint32_t x = warp_excl_scan(v, &wt);
+    const uint32_t w = threadIdx.x >> 5;
+    if (lane_id() == 31) smem[w] = wt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < NW; ++i) { uint32_t c = smem[i]; smem[i] = run; run += c; }
+        smem[NW] = run;
+    }
+    __syncthreads();
+    uint32_t r = x + smem[w];
+    *total = smem[NW];
+    return r;
+}
+
+// ------------------------------------------- decoupled look-back words
+// word = epoch(30) << 34 | flag(2) << 32 | value(32); flag 1 = tile
+// aggregate, 2 = inclusive prefix.  Words of an older epoch read as empty.
+__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, uint32_t flag, uint32_t value) {
+    return ((unsigned long long)(epoch & 0x3FFFFFFFu) << 34) | ((unsigned long long)flag << 32) | value;
+}
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long w) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    a.store(w, cuda::memory_order_relaxed);
+}
+__device__ __forceinline__ unsigned long long lb_load(unsigned long long* p) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*p);
+    return a.load(cuda::memory_order_relaxed);
+}
+
+// Publish this tile's aggregate, walk back to an inclusive prefix, publish
+// the inclusive value; returns the exclusive prefix.  'status' points at
+// this scan's word array with 'stride' words between consecutive tiles.
+// Tiles are handed out in ticket order, so every predecessor is running or
+// done; the wait is still bounded and reports F_SPIN_TIMEOUT.
+__device__ __forceinline__ uint32_t lookback(unsigned long long* status, uint32_t stride, uint32_t tile,
+                                             uint32_t agg, uint32_t epoch, uint32_t* flags) {
+    const uint32_t ep = epoch & 0x3FFFFFFFu;
+    if (tile == 0) {
+        lb_store(status, lb_pack(epoch, 2u, agg));
+        return 0;
+    }
+    lb_store(status + (size_t)tile * stride, lb_pack(epoch, 1u, agg));
+    uint32_t prefix = 0;
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        unsigned long long w = lb_load(status + (size_t)j * stride);
+        uint32_t wep = (uint32_t)(w >> 34), fl = (uint32_t)(w >> 32) & 3u;
+        if (wep != ep || fl == 0u) {
+            if (++spins > SPIN_LIMIT) { atomicOr(flags, F_SPIN_TIMEOUT); break; }
+            __nanosleep(20);
+            continue;
+        }
+        prefix += (uint32_t)w;
+        if (fl == 2u) break;
+        --j;
+    }
+    lb_store(status + (size_t)tile * stride, lb_pack(epoch, 2u, prefix + agg));
+    return prefix;
+}
+
+// The granularity test, single-rounded FP32 (no contraction): expand iff
+// fl(((dx dx + dy dy) + dz dz) k) < radius2; cr.w is 0 for leaves.
+__device__ __forceinline__ bool lod_expand(float4 c, float px, float py, float pz, float k) {
+    float dx = __fsub_rn(px, c.x), dy = __fsub_rn(py, c.y), dz = __fsub_rn(pz, c.z);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return __fmul_rn(d2, k) < c.w;
+}
+
+__device__ __forceinline__ void bitmap_set(uint32_t* bm, uint32_t n) { atomicOr(&bm[n >> 5], 1u << (n & 31u)); }
+
+}  // namespace vgr

@@ -1,0 +1,67 @@
+// vgr_launch.h -- host-side launchers of the frame-path kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vgr {
+
+struct SceneDev;
+struct FrameParams;
+struct Counters;
+
+// k_lod.cu
+void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
+                       const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s);
+void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
+                      const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s);
+void launch_cut_compact(uint32_t* bitmap, uint32_t n_words, uint32_t* cut, uint32_t cap, uint32_t* n_cut_out,
+                        unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
+                        cudaStream_t s);
+uint32_t cut_compact_tiles(uint32_t n_words);
+uint32_t cut_compact_tile_words();
+
+// k_preprocess.cu
+struct VisBuffers {
+    uint32_t* node;
+    uint32_t* depth;
+    uint32_t* ntile;
+    uint2* rect;
+    float4* recA;   // u v A B
+    float4* recB;   // C thr theta r
+    float2* recC;   // g b
+};
+void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
+                       const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
+                       Counters* ctr, int grid, cudaStream_t s);
+uint32_t preprocess_tile();
+void prepare_scene(float4* covB, uint32_t n, cudaStream_t s);
+void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s);
+
+// k_sort.cu
+uint32_t radix_tile();
+void launch_radix_hist(const uint32_t* keys, const uint32_t* n32, const unsigned long long* n64, uint64_t cap,
+                       int passes, uint32_t* hist /*[4][256]*/, int grid, cudaStream_t s);
+void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                       const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
+                       const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
+                       Counters* ctr, int grid, cudaStream_t s);
+
+// k_emit.cu
+void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, float4* srecA, float4* srecB,
+                 float2* srecC, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
+                 unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
+uint32_t emit_tile();
+void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint2* ranges, int grid,
+                   cudaStream_t s);
+
+// k_blend.cu
+void launch_blend(uint32_t n_tiles, const uint2* ranges, const uint32_t* pair_rank, const float4* srecA,
+                  const float4* srecB, const float2* srecC, const FrameParams* fp, const float* lut, float* image,
+                  Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
+
+// k_store.cu
+void convert_sh_half(const float* src, uint32_t n, uint32_t k3, void* dst, uint32_t stride, cudaStream_t s);
+void convert_cov_bf16(const float* src6, uint32_t n, void* dst, cudaStream_t s);
+
+}  // namespace vgr

@@ -1,0 +1,154 @@
+"""Comparison helpers for the GPU-vs-oracle parity tests (not a test module).
+
+Bars (spec tolerances): the cut bit-exact; images within 2e-3 max-abs
+per channel on pixels the oracle does not flag as decision-ambiguous, and
+PSNR >= 55 dB over all pixels.  The pair set must equal the oracle's except
+within the FP32 test slack: every extra GPU pair has an oracle margin
+(rho_max - threshold) in [-(slack + delta), 0) and every missing oracle pair a
+margin below delta.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+
+IMG_TOL = 2e-3
+PSNR_MIN = 55.0
+TILE_SLACK = 2e-3      # the renderer's FP32 tile-test slack (nats)
+MARGIN_DELTA = 2e-3    # FP32-vs-FP64 error allowance on rho_max (nats)
+
+
+def psnr(a: np.ndarray, b: np.ndarray) -> float:
+    mse = float(np.mean((a.astype(np.float64) - b) ** 2))
+    return math.inf if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def image_report(img: np.ndarray, ref: dict, tile_mask=None) -> dict:
+    H, W = ref["image"].shape[:2]
+    sel = np.ones((H, W), bool)
+    if tile_mask is not None:
+        TW = (W + 15) // 16
+        ty, tx = np.mgrid[0:H, 0:W]
+        sel = np.asarray(tile_mask).reshape(-1)[(ty // 16) * TW + tx // 16]
+    ok = sel & (ref["flags"] == 0)
+    diff = np.abs(img.astype(np.float64) - ref["image"])
+    return dict(max_abs=float(diff[ok].max()) if ok.any() else 0.0,
+                psnr=psnr(img[sel], ref["image"][sel]),
+                flagged=int((sel & (ref["flags"] != 0)).sum()), pixels=int(sel.sum()),
+                max_abs_all=float(diff[sel].max()) if sel.any() else 0.0)
+
+
+def check_image(img, ref, tile_mask=None, tol=IMG_TOL, psnr_min=PSNR_MIN):
+    r = image_report(img, ref, tile_mask)
+    assert r["max_abs"] <= tol, r
+    assert r["psnr"] >= psnr_min, r
+    assert r["flagged"] <= max(8, 0.01 * r["pixels"]), r
+    return r
+
+
+def _pairkey(tile, node):
+    return (np.asarray(tile, np.int64) << 32) | np.asarray(node, np.int64)
+
+
+def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
+    """Stage-by-stage parity of one frame.  With tile_mask, pair checks are
+    restricted to the masked tiles (the oracle binned only those)."""
+    cut = ref["cut"]
+    np.testing.assert_array_equal(dbg["cut"], cut)
+    proj = ref["proj"]
+    # per-cut-index best candidate margin
+    best = np.full(len(cut), -np.inf)
+    if len(ref["cand_idx"]):
+        np.maximum.at(best, ref["cand_idx"], ref["cand_margin"])
+    # ---- visible set, in ascending node order
+    gv = dbg["vis_node"]
+    assert np.all(np.diff(gv.astype(np.int64)) > 0), "visible list not in ascending node order"
+    idx = np.searchsorted(cut, gv)
+    assert np.all(cut[np.minimum(idx, len(cut) - 1)] == gv), "visible node not in the cut"
+    if tile_mask is None:
+        ov = cut[proj["visible"] == 1]
+        extra = np.setdiff1d(gv, ov)
+        missing = np.setdiff1d(ov, gv)
+        if len(extra):
+            be = best[np.searchsorted(cut, extra)]
+            assert np.all(be >= -(TILE_SLACK + MARGIN_DELTA)) and np.all(be < 0), be
+        if len(missing):
+            bm = best[np.searchsorted(cut, missing)]
+            assert np.all(bm < MARGIN_DELTA), bm
+    # ---- depth keys: the FP32 formula, bit-exact
+    zk = proj["zkey"][idx].view(np.uint32)
+    np.testing.assert_array_equal(dbg["vis_depth"], zk)
+    # ---- records against the FP64 projection
+    p = proj[idx]
+    A, B, C = dbg["vis_recA"], dbg["vis_recB"], dbg["vis_recC"]
+    scale = np.maximum(1.0, np.abs(p["u"]))
+    assert np.max(np.abs(A[:, 0] - p["u"]) / scale) < 2e-5
+    assert np.max(np.abs(A[:, 1] - p["v"]) / np.maximum(1.0, np.abs(p["v"]))) < 2e-5
+    con = np.stack([-2.0 * A[:, 2], -A[:, 3], -2.0 * B[:, 0]], 1)
+    cref = p["conic"]
+    cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))[:, None]
+    assert np.max(np.abs(con - cref) / cs) < 2e-3
+    rgb = np.stack([B[:, 3], C[:, 0], C[:, 1]], 1)
+    assert np.max(np.abs(rgb - p["rgb"])) < 2e-5
+    np.testing.assert_array_equal(B[:, 2], p["theta"].astype(np.float32))
+    assert np.max(np.abs(B[:, 1] - p["thr"])) < 1e-5
+    # ---- depth order: sorted by (depth key, node id)
+    order = dbg["depth_order"]
+    assert np.array_equal(np.sort(order), np.arange(len(gv)))
+    zs, ns = dbg["vis_depth"][order], gv[order]
+    ok = (zs[1:] > zs[:-1]) | ((zs[1:] == zs[:-1]) & (ns[1:] > ns[:-1]))
+    assert np.all(ok), "depth order not (key, node) ascending"
+    # ---- pairs: sorted by tile, depth rank ascending within a tile
+    pt, pr = dbg["pair_tile"].astype(np.int64), dbg["pair_rank"].astype(np.int64)
+    assert np.all(np.diff(pt) >= 0)
+    same = pt[1:] == pt[:-1]
+    assert np.all(pr[1:][same] > pr[:-1][same])
+    rng = dbg["tile_range"]
+    starts = np.flatnonzero(np.r_[True, pt[1:] != pt[:-1]]) if len(pt) else np.zeros(0, np.int64)
+    for s0 in starts[:: max(1, len(starts) // 200)]:
+        t = pt[s0]
+        assert rng[t, 0] == s0 and np.all(pt[rng[t, 0]:rng[t, 1]] == t)
+    gnode = gv[order[pr]] if len(pr) else np.zeros(0, np.int64)
+    gkeys = _pairkey(pt, gnode)
+    okeys = _pairkey(ref["pair_tile"], cut[ref["pair_idx"]])
+    ckeys = _pairkey(ref["cand_tile"], cut[ref["cand_idx"]])
+    if tile_mask is not None:
+        m = np.asarray(tile_mask).reshape(-1)
+        gkeys = gkeys[m[pt]]
+    extra = np.setdiff1d(gkeys, okeys)
+    missing = np.setdiff1d(okeys, gkeys)
+    if len(extra):
+        pos = np.searchsorted(np.sort(ckeys), extra)
+        cs_ = np.sort(ckeys)
+        assert np.all(cs_[np.minimum(pos, len(cs_) - 1)] == extra), "GPU pair outside the candidate set"
+        marg = dict(zip(ckeys.tolist(), ref["cand_margin"].tolist()))
+        em = np.array([marg[int(k)] for k in extra])
+        assert np.all(em >= -(TILE_SLACK + MARGIN_DELTA)), em.min()
+    if len(missing):
+        marg = dict(zip(ckeys.tolist(), ref["cand_margin"].tolist()))
+        mm = np.array([marg[int(k)] for k in missing])
+        assert np.all(mm < MARGIN_DELTA), mm.max()
+    # ---- per-tile order of the common pairs equals the oracle's
+    common = np.intersect1d(gkeys, okeys)
+    g_common = gkeys[np.isin(gkeys, common)]
+    o_common = okeys[np.isin(okeys, common)]
+    np.testing.assert_array_equal(g_common, o_common)
+    return dict(extra_pairs=int(len(extra)), missing_pairs=int(len(missing)), pairs=int(len(gkeys)))
+
+
+def quantize_scene(sc: dict) -> dict:
+    """The scene as the reduced-precision store holds it: SH rounded to FP16
+    and covariances to BF16 (round to nearest even), back in FP32."""
+    q = dict(sc)
+    q["sh"] = sc["sh"].astype(np.float16).astype(np.float32)
+    b = sc["cov6"].astype(np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b >> 16) & 1) + 0x7FFF
+    q["cov6"] = (((b + r) & 0xFFFF0000) & 0xFFFFFFFF).astype(np.uint32).view(np.float32)
+    return q
+
+
+def oracle_render(sc, cam, tau, **kw):
+    return oracle.render(sc, cam, tau, **kw)
