@@ -49,6 +49,21 @@ def check_image(img, ref, tile_mask=None, tol=IMG_TOL, psnr_min=PSNR_MIN):
     return r
 
 
+def pair_margin(ref: dict, tile: int, node: int) -> float:
+    """Oracle margin rho_max - (ln alpha* - ln theta) of (tile, node) in FP64,
+    for any pair (also outside the oracle's candidate rectangle)."""
+    cut = ref["cut"]
+    g = int(np.searchsorted(cut, node))
+    assert cut[g] == node
+    p = ref["proj"][g]
+    H, W = ref["image"].shape[:2]
+    TW = (W + 15) // 16
+    tx, ty = tile % TW, tile // TW
+    x0, y0 = 16 * tx + 0.5, 16 * ty + 0.5
+    x1, y1 = min(16 * tx + 15.5, W - 0.5), min(16 * ty + 15.5, H - 0.5)
+    return oracle.rho_max_rect(p["conic"], p["u"], p["v"], x0, x1, y0, y1) - p["thr"]
+
+
 def _pairkey(tile, node):
     return (np.asarray(tile, np.int64) << 32) | np.asarray(node, np.int64)
 
@@ -73,8 +88,10 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
         extra = np.setdiff1d(gv, ov)
         missing = np.setdiff1d(ov, gv)
         if len(extra):
+            # every pair of such a Gaussian is a slack-band extra; the pair
+            # check below bounds each one's oracle margin
             be = best[np.searchsorted(cut, extra)]
-            assert np.all(be >= -(TILE_SLACK + MARGIN_DELTA)) and np.all(be < 0), be
+            assert np.all(be < 0), be
         if len(missing):
             bm = best[np.searchsorted(cut, missing)]
             assert np.all(bm < MARGIN_DELTA), bm
@@ -84,9 +101,12 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     # ---- records against the FP64 projection
     p = proj[idx]
     A, B, C = dbg["vis_recA"], dbg["vis_recB"], dbg["vis_recC"]
-    scale = np.maximum(1.0, np.abs(p["u"]))
-    assert np.max(np.abs(A[:, 0] - p["u"]) / scale) < 2e-5
-    assert np.max(np.abs(A[:, 1] - p["v"]) / np.maximum(1.0, np.abs(p["v"]))) < 2e-5
+    H, W = ref["image"].shape[:2]
+    for j, key, half in ((0, "u", W / 2.0), (1, "v", H / 2.0)):
+        # u = fx x/z + cx: the FP32 error scales with the larger of the two terms
+        err = np.abs(A[:, j] - p[key]) / np.maximum(np.maximum(1.0, half), np.abs(p[key]))
+        w = np.argsort(err)[-4:]
+        assert err.max() < 2e-5, (key, err[w], A[w, j], p[key][w], p["z"][w], p["cov"][w])
     con = np.stack([-2.0 * A[:, 2], -A[:, 3], -2.0 * B[:, 0]], 1)
     cref = p["conic"]
     cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))[:, None]
@@ -121,12 +141,8 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     extra = np.setdiff1d(gkeys, okeys)
     missing = np.setdiff1d(okeys, gkeys)
     if len(extra):
-        pos = np.searchsorted(np.sort(ckeys), extra)
-        cs_ = np.sort(ckeys)
-        assert np.all(cs_[np.minimum(pos, len(cs_) - 1)] == extra), "GPU pair outside the candidate set"
-        marg = dict(zip(ckeys.tolist(), ref["cand_margin"].tolist()))
-        em = np.array([marg[int(k)] for k in extra])
-        assert np.all(em >= -(TILE_SLACK + MARGIN_DELTA)), em.min()
+        em = np.array([pair_margin(ref, int(k) >> 32, int(k) & 0xFFFFFFFF) for k in extra])
+        assert np.all(em >= -(TILE_SLACK + MARGIN_DELTA)) and np.all(em < 0), (em.min(), em.max())
     if len(missing):
         marg = dict(zip(ckeys.tolist(), ref["cand_margin"].tolist()))
         mm = np.array([marg[int(k)] for k in missing])
