@@ -1,0 +1,350 @@
+"""Frame-rate bench of the GB300 frame path (one JSON line on stdout).
+
+Default workload: the 18M-leaf synthetic city (about 26.5M LoD nodes, SH
+degree 3, FP32 storage) at 1920x1080, tau = 3 px, frames W .. W+K-1 of its
+600-frame street walk.  A step is one frame: temporal LoD cut update, cut
+compaction, preprocess, depth sort, pair emission, tile sort, ranges and
+blend, plus the end-of-frame status read.
+
+value    frames/s with the scene resident in HBM (device-clock time of the K
+         frames, CUDA events on the view's stream, max over ranks)
+e2e      the same through vgr_render_frame_host: camera from host memory and
+         the 1080p image copied back to pinned host memory every frame
+roofline the dominant kernel against MEASURED_PEAKS.json
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+
+--impl reference times the oracle alone (the reference arm of this project:
+there is no released code of the paper).  Under torchrun each rank renders
+its own view of its own scene replica (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "1080p frames/s on 18M-Gaussian scene (LoD+raster ms); served p50/p99 ms"
+WORKLOADS = {
+    "city": dict(scene="city", label="city-18M-leaves-1080p"),
+    "m1": dict(scene="m1", label="box-1M-leaves-1080p"),
+    "tiny": dict(scene="tiny", label="box-4096-leaves-128px"),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=float(d.get("sm_max_mhz", 2070)))
+    return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=2070.0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
+    """Algorithmic bytes per frame and stage (FP32 store), from the counters."""
+    C, V, P, E = st["cut_count"], st["visible_count"], st["pair_count"], st["nodes_evaluated"]
+    N = int(sc["n_nodes"])
+    K3 = 3 * (int(sc["sh_degree"]) + 1) ** 2
+    shb = 4 * ((K3 + 3) // 4 * 4)
+    return dict(
+        lod=16 * E + 4 * C + 4 * C + N / 8,          # node tests, parent ids, prev cut read, bitmap set
+        compact=N / 8 * 2 + 4 * C,                   # bitmap read + clear, cut ids written
+        preprocess=4 * C + 16 * C + (32 + shb) * V + 40 * V + 24 * V,   # ids, centre/R2, cov+SH of visible, records out
+        depth_sort=4 * 2 * 8 * V + 4 * V,            # 4 passes x (key+value) read+write, histogram read
+        emit=(4 + 12 + 40) * V + 40 * V + 8 * P,     # order, counts/rect, records in and out, pairs
+        tile_sort=tile_passes * 2 * 8 * P,
+        ranges=4 * P + 8 * (W // 16 + 1) * (H // 16 + 1),
+        blend=(4 + 40) * P + 12 * W * H,
+    )
+
+
+def run_ours(args) -> dict:
+    import torch
+
+    import scenegen
+    import paper_2506_02774_gb300 as vgr
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    wl = WORKLOADS[args.config]
+    cfg = scenegen.CONFIGS[wl["scene"]]
+    t0 = time.time()
+    sc = scenegen.make_scene(wl["scene"])
+    t_gen = time.time() - t0
+    t0 = time.time()
+    h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF if args.storage == "half" else vgr.STORE_FP32)
+    t_up = time.time() - t0
+    stream = torch.cuda.Stream()
+    view = vgr.View(h, stream=stream.cuda_stream, timing=False)
+    tau = cfg["tau"]
+    nfr = cfg["frames"]
+    W, H = cfg["width"], cfg["height"]
+    # each rank walks its own street (replicas: no data-path collective)
+    heading, start = 0.0, None
+    if rank:
+        start = list(cfg["start"])
+        start[1] += 40.0 * rank
+    cams = [scenegen.trajectory(wl["scene"], f % nfr, heading, start) for f in range(args.warmup + args.steps)]
+    structs = [vgr.camera_struct(c) for c in cams]
+    # warm-up (frame 0 finds its cut top-down, then temporal updates)
+    for i in range(args.warmup):
+        view.render(cams[i], tau)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K frames, device clock on the view's stream
+    clk = ClockSampler(dev)
+    clk.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    stats = []
+    kernels = 0
+    ev0.record(stream)
+    for i in range(args.warmup, args.warmup + args.steps):
+        t = time.perf_counter()
+        r = view.render(cams[i], tau)
+        lat.append(time.perf_counter() - t)
+        stats.append(r.stats)
+        kernels += r.stats["kernels"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    frames = args.steps * ws
+    value = frames / (ms / 1e3)
+
+    # ---- per-stage device times (a second pass over the same frames with stage events)
+    view_t = vgr.View(h, stream=stream.cuda_stream, timing=True)
+    for i in range(args.warmup):
+        view_t.render(cams[i], tau)
+    stage_ms = np.zeros(len(vgr.STAGES))
+    n_t = 0
+    for i in range(args.warmup, args.warmup + args.steps):
+        r = view_t.render(cams[i], tau)
+        stage_ms += np.array([r.stats["stage_ms"][s] for s in vgr.STAGES])
+        n_t += 1
+    stage_ms /= max(1, n_t)
+    view_t.close()
+
+    # ---- end to end through the host-buffer entry point
+    host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
+    hp = host_img.data_ptr()
+    from paper_2506_02774_gb300 import _abi
+    fr = _abi.Frame()
+    view.reset()
+    for i in range(args.warmup):
+        view.render_host_ptr(structs[i], tau, hp, fr)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        _abi.check(view.render_host_ptr(structs[i], tau, hp, fr))
+    e2e_s = time.perf_counter() - t
+    e2e = dict(value=args.steps / e2e_s, unit="frames/s", h2d_bytes_per_step=int(128 + 4),
+               d2h_bytes_per_step=int(W * H * 3 * 4 + 48 + 8))
+
+    # ---- roofline of the dominant kernel
+    mean = {k: float(np.mean([s[k] for s in stats])) for k in
+            ("cut_count", "visible_count", "pair_count", "nodes_evaluated", "candidate_pairs",
+             "pixel_pair_evals")}
+    n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    tp = max(1, (int(math.ceil(math.log2(max(2, n_tiles)))) + 7) // 8)
+    fb = _frame_bytes(sc, mean, W, H, tp)
+    peaks = _peaks()
+    shares = {s: float(stage_ms[i]) for i, s in enumerate(vgr.STAGES)}
+    top = max(shares, key=shares.get)
+    hbm_stages = {s: fb[s] / (shares[s] * 1e-3) / 1e9 for s in vgr.STAGES if shares[s] > 0}
+    evals = None
+    roof = dict(bound="hbm", stage=top, achieved=round(hbm_stages.get(top, 0.0), 1), peak=peaks["hbm_gbs"],
+                unit="GB/s", frac=round(hbm_stages.get(top, 0.0) / peaks["hbm_gbs"], 4),
+                traffic=None, peak_source=peaks["source"] + " hbm_gbs (MEASURED_PEAKS.json)",
+                algorithmic_bytes=int(fb[top]), kernel_ms=round(shares[top], 4))
+    if top == "blend":
+        roof["note"] = "blend is issue-bound; see stage_gbs and DESIGN.md for its ALU roofline"
+    out = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=ws, steps=args.steps,
+               warmup=args.warmup, ms_per_step=round(ms / args.steps, 4), higher_is_better=True,
+               scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+               config=dict(workload=wl["label"], leaves=int(sc["n_leaves"]), nodes=int(sc["n_nodes"]),
+                           width=W, height=H, tau=tau, storage=args.storage,
+                           frames="%d..%d of the %d-frame walk" % (args.warmup, args.warmup + args.steps - 1, nfr),
+                           l2="inputs larger than L2 (scene %.1f GB on the device)" % (h.device_bytes / 1e9),
+                           parallelism="replicas" if ws > 1 else "single"),
+               e2e=dict(value=round(e2e["value"], 2), unit=e2e["unit"],
+                        h2d_bytes_per_step=e2e["h2d_bytes_per_step"], d2h_bytes_per_step=e2e["d2h_bytes_per_step"]),
+               gpu_launches=int(kernels),
+               roofline=roof, clocks=clocks,
+               p50_ms=round(1e3 * float(np.percentile(lat, 50)), 4), p99_ms=round(1e3 * float(np.percentile(lat, 99)), 4),
+               stage_ms={k: round(v, 4) for k, v in shares.items()},
+               stage_gbs={k: round(v, 1) for k, v in hbm_stages.items()},
+               counts={k: round(v, 1) for k, v in mean.items()},
+               setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
+    view.close()
+    h.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    out["_scene"] = sc if rank == 0 else None
+    out["_cams"] = cams
+    out["_rank"] = rank
+    return out
+
+
+def cpu_baseline(sc, cams, tau, budget_s: float = 20.0) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    whole frames of the same walk until ~budget_s of CPU time."""
+    import oracle
+    n_thr = oracle.num_threads()
+    done, t_total = 0, 0.0
+    for cam in cams:
+        t = time.perf_counter()
+        oracle.render(sc, cam, tau)
+        t_total += time.perf_counter() - t
+        done += 1
+        if t_total >= budget_s:
+            break
+    return dict(value=round(done / t_total, 4), unit="frames/s", cores=n_thr, kind="oracle",
+                sample="%d full frame(s) of the same walk (FP64 oracle, %d OpenMP threads), %.1f s"
+                       % (done, n_thr, t_total))
+
+
+def run_reference(args) -> dict:
+    import oracle
+    import scenegen
+    ws, rank, _ = _dist()
+    wl = WORKLOADS[args.config]
+    cfg = scenegen.CONFIGS[wl["scene"]]
+    if rank != 0:
+        return None
+    sc = scenegen.make_scene(wl["scene"])
+    cams = [scenegen.trajectory(wl["scene"], f % cfg["frames"]) for f in range(args.warmup + args.steps)]
+    n_thr = oracle.num_threads()
+    # each step is a bounded sample: every (K/stride)-th frame keeps the run within minutes
+    per_frame_cap = max(1, int(math.ceil(args.steps / 4)))
+    sample = cams[args.warmup::max(1, args.steps // per_frame_cap)][:per_frame_cap]
+    for cam in cams[:min(1, args.warmup)]:
+        oracle.render(sc, cam, cfg["tau"])
+    t = time.perf_counter()
+    for cam in sample:
+        oracle.render(sc, cam, cfg["tau"])
+    dt = time.perf_counter() - t
+    value = len(sample) / dt
+    desc = "%d of the %d timed frames (every %d-th), FP64 oracle, %d OpenMP threads, %.1f s" % (
+        len(sample), args.steps, max(1, args.steps // per_frame_cap), n_thr, dt)
+    return dict(impl="reference", metric=METRIC, value=round(value, 4), unit="frames/s", n_gpus=ws,
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(1e3 / value, 2), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=wl["label"], leaves=int(sc["n_leaves"]), nodes=int(sc["n_nodes"]),
+                            width=cfg["width"], height=cfg["height"], tau=cfg["tau"]),
+                cpu_baseline=dict(value=round(value, 4), unit="frames/s", cores=n_thr, kind="oracle", sample=desc),
+                e2e=dict(value=round(value, 4), unit="frames/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="city", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "half"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(args)
+    sc, cams, rank = out.pop("_scene"), out.pop("_cams"), out.pop("_rank")
+    if rank == 0:
+        if args.no_cpu_baseline or out["n_gpus"] > 1:
+            out["cpu_baseline"] = None
+        else:
+            tau = 3.0
+            out["cpu_baseline"] = cpu_baseline(sc, cams[args.warmup:], tau, args.cpu_budget)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,8 @@ typedef struct {
     uint64_t nodes_evaluated; /* granularity tests made by the LoD step */
     uint32_t lod_from_scratch;/* 1 if the cut was found top-down this frame */
     uint32_t replays;         /* frame replays (buffer growth or LoD fallback) */
+    uint32_t kernels;         /* kernel launches made for the frame, replays included */
+    uint64_t pixel_pair_evals;/* X: (pixel, Gaussian) evaluations in the blend */
     float stage_ms[VGR_N_STAGES]; /* device time per stage (timing = 1), else 0 */
     float frame_ms;           /* device time of the frame (timing = 1), else 0 */
 } vgr_frame_stats;

@@ -110,7 +110,9 @@ class FrameResult:
         self.stats = dict(cut_count=int(s.cut_count), visible_count=int(s.visible_count),
                           pair_count=int(s.pair_count), candidate_pairs=int(s.candidate_pairs),
                           nodes_evaluated=int(s.nodes_evaluated), lod_from_scratch=int(s.lod_from_scratch),
-                          replays=int(s.replays), stage_ms={n: float(s.stage_ms[i]) for i, n in enumerate(STAGES)},
+                          replays=int(s.replays), kernels=int(s.kernels),
+                          pixel_pair_evals=int(s.pixel_pair_evals),
+                          stage_ms={n: float(s.stage_ms[i]) for i, n in enumerate(STAGES)},
                           frame_ms=float(s.frame_ms))
 
     def image(self):

@@ -38,7 +38,8 @@ class ViewOpts(ctypes.Structure):
 class FrameStats(ctypes.Structure):
     _fields_ = [("cut_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64),
                 ("candidate_pairs", c_u64), ("nodes_evaluated", c_u64), ("lod_from_scratch", c_u32),
-                ("replays", c_u32), ("stage_ms", c_f32 * 8), ("frame_ms", c_f32)]
+                ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64), ("stage_ms", c_f32 * 8),
+                ("frame_ms", c_f32)]
 
 
 class Frame(ctypes.Structure):

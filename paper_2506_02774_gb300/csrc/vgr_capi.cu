@@ -574,8 +574,9 @@ int tile_passes_for(uint32_t n_tiles) {
     return std::max(1, (bits + 7) / 8);
 }
 
-// Enqueue one frame.  'scratch' selects the top-down cut.
-void enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
+// Enqueue one frame.  'scratch' selects the top-down cut.  Returns the
+// number of kernels launched.
+uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     const SceneDev& sc = v->h->dev;
     cudaStream_t s = v->stream;
     const bool timing = v->opts.timing != 0;
@@ -632,6 +633,9 @@ void enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_N_STAGES);
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
+    const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
+    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 5u /*depth hist + 4 passes*/ + 1u /*emit*/ +
+           (uint32_t)tile_passes + 1u /*ranges*/ + 1u /*blend*/;
 }
 
 vgr_status check_camera(const vgr_camera* c, float tau) {
@@ -664,7 +668,7 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
     volatile float t = tau / f;
     volatile float k = t * t;
     bool scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || f != v->prev_f;
-    uint32_t replays = 0;
+    uint32_t replays = 0, kernels = 0;
     uint32_t flags = 0;
     const Counters* ch = reinterpret_cast<const Counters*>(v->ctr_host);
     for (int attempt = 0;; ++attempt) {
@@ -685,7 +689,7 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
         p.lut_step = 5.55f / (float)v->opts.lut_size;
         p.lod_budget = v->opts.lod_budget;
         p.max_depth = v->h->max_depth;
-        enqueue_frame(v, scratch, tile_passes);
+        kernels += enqueue_frame(v, scratch, tile_passes);
         VGR_CK(cudaGetLastError());
         VGR_CK(cudaStreamSynchronize(v->stream));
         flags = ch->flags;
@@ -748,6 +752,8 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
         st.nodes_evaluated = ch->nodes_eval;
         st.lod_from_scratch = scratch ? 1u : 0u;
         st.replays = replays;
+        st.kernels = kernels;
+        st.pixel_pair_evals = ch->pix_evals;
         if (v->opts.timing) {
             for (int i = 0; i < VGR_N_STAGES; ++i) cudaEventElapsedTime(&st.stage_ms[i], v->ev[i], v->ev[i + 1]);
             cudaEventElapsedTime(&st.frame_ms, v->ev[0], v->ev[VGR_N_STAGES]);
