@@ -197,6 +197,25 @@ vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, 
 
 vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* out);
 
+/*
+ * The pair sort of the frame path as a standalone call (Sec. 3.1 "Sorting"):
+ * stable LSD radix sort of n (key, value) pairs of u32 by the low
+ * 8 * ceil(key_bits / 8) bits of the key, 8-bit digits, one pass per digit.
+ * keys_in, vals_in, keys_out, vals_out are device pointers to n elements each;
+ * the inputs are only read, the outputs receive the sorted pairs, and input
+ * and output ranges must not overlap.  Equal keys keep their input order.
+ * Runs on 'stream' (a cudaStream_t, NULL for the default stream) and waits
+ * for it before returning.  Scratch (histograms, look-back words, the
+ * ping-pong buffer of a multi-pass sort) is allocated by the library on
+ * first use per device, grown when a larger n arrives and kept until exit;
+ * calls on one device are serialised.  1 <= key_bits <= 32, n < 2^32 - 1
+ * (n = 0 is a no-op).  Errors: VGR_E_INVALID, VGR_E_NOMEM, VGR_E_CUDA,
+ * VGR_E_TIMEOUT (a bounded look-back wait ran out).
+ */
+vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                          uint32_t* vals_out, uint64_t n, uint32_t key_bits, void* stream);
+
+
 const char* vgr_last_error(void);
 
 #ifdef __cplusplus

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (EXP_EXACT, EXP_LUT, FILTER_CANONICAL, FILTER_PREEMPTIVE, STAGES, STORE_FP32, STORE_HALF,
                    VgrError)
 
-__all__ = ["Hierarchy", "View", "FrameResult", "camera_struct", "VgrError", "load_library", "STORE_FP32",
+__all__ = ["Hierarchy", "View", "FrameResult", "camera_struct", "sort_pairs", "VgrError", "load_library", "STORE_FP32",
            "STORE_HALF", "FILTER_PREEMPTIVE", "FILTER_CANONICAL", "EXP_EXACT", "EXP_LUT", "STAGES"]
 
 
@@ -62,6 +62,19 @@ def camera_struct(cam: dict) -> _abi.Camera:
     c.width, c.height = int(cam["width"]), int(cam["height"])
     c.z_near = float(cam.get("z_near", 0.2))
     return c
+
+
+def sort_pairs(keys, vals, key_bits: int = 32, stream=None):
+    """Stable radix sort of int32 CUDA tensors (u32 bit patterns) via
+    vgr_sort_pairs; returns new (keys, values) tensors."""
+    import torch
+    assert keys.is_cuda and vals.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32
+    assert keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()
+    ko, vo = torch.empty_like(keys), torch.empty_like(vals)
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    _abi.check(_abi.load().vgr_sort_pairs(keys.data_ptr(), vals.data_ptr(), ko.data_ptr(), vo.data_ptr(),
+                                          keys.numel(), int(key_bits), ctypes.c_void_p(s)))
+    return ko, vo
 
 
 class Hierarchy:

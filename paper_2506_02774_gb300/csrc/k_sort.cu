@@ -13,10 +13,10 @@
 
 namespace vgr {
 
-constexpr int RS_THREADS = 256;
+constexpr int RS_THREADS = RADIX_THREADS;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 15;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 3840 keys per tile
+constexpr int RS_ITEMS = RADIX_ITEMS;
+constexpr int RS_TILE = RADIX_TILE;  // 3840 keys per tile
 constexpr int RS_BINS = 256;
 
 uint32_t radix_tile() { return RS_TILE; }

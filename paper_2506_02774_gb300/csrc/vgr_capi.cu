@@ -67,6 +67,8 @@ uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); 
 
 }  // namespace
 
+void vgr::set_last_error(const char* msg) { g_err = msg; }
+
 struct vgr_hierarchy {
     SceneDev dev{};
     float4* cr = nullptr;

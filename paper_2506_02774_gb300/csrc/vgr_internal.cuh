@@ -22,6 +22,9 @@ constexpr int MAX_TREE_DEPTH = 64;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;     // bounded waits in look-back scans
 constexpr uint32_t CHILD_SHIFT = 28;          // child word: first_child | n_child << 28
 constexpr uint32_t CHILD_MASK = (1u << CHILD_SHIFT) - 1u;
+constexpr int RADIX_THREADS = 256;            // one radix-sort tile: 256 threads x 15 keys
+constexpr int RADIX_ITEMS = 15;
+constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;
 
 // flags in Counters::flags
 enum : uint32_t {

@@ -6,6 +6,9 @@
 
 namespace vgr {
 
+// vgr_capi.cu: the thread-local message returned by vgr_last_error()
+void set_last_error(const char* msg);
+
 struct SceneDev;
 struct FrameParams;
 struct Counters;
@@ -59,6 +62,14 @@ void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs
 void launch_blend(uint32_t n_tiles, const uint2* ranges, const uint32_t* pair_rank, const float4* srecA,
                   const float4* srecB, const float2* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
+
+// vgr_sort_api.cu: enqueue a standalone pair sort on caller-provided scratch
+size_t sort_status_words(uint64_t n, int passes);
+int sort_passes(uint32_t key_bits);
+cudaError_t sort_pairs_enqueue(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                               uint32_t* vals_out, uint64_t n, uint32_t key_bits, FrameParams* fp, Counters* ctr,
+                               unsigned long long* status, uint32_t* tmp_keys, uint32_t* tmp_vals, int grid,
+                               cudaStream_t s);
 
 // k_store.cu
 void convert_sh_half(const float* src, uint32_t n, uint32_t k3, void* dst, uint32_t stride, cudaStream_t s);
