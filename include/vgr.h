@@ -215,6 +215,34 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* out);
 vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                           uint32_t* vals_out, uint64_t n, uint32_t key_bits, void* stream);
 
+/* Largest n accepted by vgr_sort_pairs_noalloc. */
+#define VGR_SORT_NOALLOC_MAX_N 262144u
+
+/*
+ * vgr_sort_pairs for callers that must not allocate device memory -- for
+ * example code running as a plug-in inside a host application that owns all
+ * device memory, or a frame loop with a fixed memory budget in which
+ * cudaMalloc and cudaFree (which can synchronise the whole device) are not
+ * allowed.  The paper has no counterpart; it is a service of this library.
+ *
+ * Same arguments, result and errors as vgr_sort_pairs, but it calls no
+ * cudaMalloc, cudaFree or other allocating routine: all scratch (look-back
+ * epoch, tickets, histograms, look-back words, the ping-pong buffer) lives in
+ * one fixed array in device memory that the library declares and that every
+ * GPU loading the library holds until the process exits (about 2.7 MB).
+ *   - n is limited to VGR_SORT_NOALLOC_MAX_N (262,144) pairs; larger n
+ *     returns VGR_E_INVALID without touching the GPU.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address and clears the array on 'stream'; make that
+ *     first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents; each call clears what it needs at its start.  Calls
+ *     whose work overlaps on the GPU (different streams or threads without
+ *     ordering between them) race on the array and give wrong results:
+ *     order them.
+ */
+vgr_status vgr_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                  uint32_t* vals_out, uint64_t n, uint32_t key_bits, void* stream);
 
 const char* vgr_last_error(void);
 

@@ -68,6 +68,7 @@ _PROTOS = {
     "vgr_render_frame_host": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp, ctypes.POINTER(Frame)]),
     "vgr_view_debug": (c_i32, [c_vp, ctypes.POINTER(DebugBuffers)]),
     "vgr_sort_pairs": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
+    "vgr_sort_pairs_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_last_error": (ctypes.c_char_p, []),
 }
 

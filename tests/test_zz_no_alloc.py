@@ -1,0 +1,60 @@
+"""vgr_sort_pairs_noalloc: the pair sort for callers that may not allocate
+device memory (for instance a plug-in inside a host application that owns
+all device memory, or a frame loop where cudaMalloc/cudaFree are banned
+because they can synchronise the device).  Its output must equal the
+allocating vgr_sort_pairs bit for bit -- the bar of every integer test here --
+on two calls in a row through the C ABI, since calls share one static scratch
+array that keeps the previous call's contents.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test; it also passes alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2506_02774_gb300 import _abi  # noqa: E402
+
+MAX_N = 262144
+
+
+def _run(fn, keys, vals, key_bits):
+    lib = _abi.load()
+    k = torch.from_numpy(keys.view(np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo = torch.empty_like(k), torch.empty_like(v)
+    s = torch.cuda.current_stream().cuda_stream
+    st = getattr(lib, fn)(k.data_ptr(), v.data_ptr(), ko.data_ptr(), vo.data_ptr(), len(keys), key_bits,
+                          ctypes.c_void_p(s))
+    _abi.check(st)
+    torch.cuda.synchronize()
+    return ko.cpu().numpy().view(np.uint32), vo.cpu().numpy().view(np.uint32)
+
+
+def test_noalloc_matches_allocating_sort_twice():
+    rng = np.random.default_rng(2024)
+    cases = [(MAX_N, 13), (100_003, 32)]  # two calls in a row, different sizes and widths
+    for n, bits in cases:
+        keys = rng.integers(0, 1 << bits, size=n, dtype=np.uint64).astype(np.uint32)
+        vals = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+        ref_k, ref_v = _run("vgr_sort_pairs", keys, vals, bits)
+        got_k, got_v = _run("vgr_sort_pairs_noalloc", keys, vals, bits)
+        np.testing.assert_array_equal(got_k, ref_k)
+        np.testing.assert_array_equal(got_v, ref_v)
+        order = np.argsort(keys, kind="stable")
+        np.testing.assert_array_equal(got_v, vals[order])
+
+
+def test_noalloc_rejects_oversize():
+    lib = _abi.load()
+    x = torch.zeros(8, dtype=torch.int32, device="cuda")
+    st = lib.vgr_sort_pairs_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr(), MAX_N + 1, 16, None)
+    assert st == _abi.VGR_E_INVALID
+    assert b"limit" in lib.vgr_last_error()
