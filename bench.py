@@ -113,15 +113,17 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
     N = int(sc["n_nodes"])
     K3 = 3 * (int(sc["sh_degree"]) + 1) ** 2
     shb = 4 * ((K3 + 3) // 4 * 4)
+    P0 = st.get("candidate_pairs", P)
     return dict(
         lod=16 * E + 4 * C + 4 * C + N / 8,          # node tests, parent ids, prev cut read, bitmap set
         compact=N / 8 * 2 + 4 * C,                   # bitmap read + clear, cut ids written
-        preprocess=4 * C + 16 * C + (32 + shb) * V + 40 * V + 24 * V,   # ids, centre/R2, cov+SH of visible, records out
+        preprocess=4 * C + 16 * C + 32 * V + 52 * V,  # ids, centre/R2 of the cut, covariance of visible, records out
         depth_sort=4 * 2 * 8 * V + 4 * V,            # 4 passes x (key+value) read+write, histogram read
-        emit=(4 + 12 + 40) * V + 40 * V + 8 * P,     # order, counts/rect, records in and out, pairs
-        tile_sort=tile_passes * 2 * 8 * P,
+        color=(4 + 4 + 16 + shb) * V + 16 * V,       # order, node, centre, SH; rgb out
+        emit=(4 + 4 + 8 + 32) * V + 32 * V + 8 * P0,  # order, count, rect, records in and out, slots
+        tile_sort=tile_passes * 2 * 8 * P0,
         ranges=4 * P + 8 * (W // 16 + 1) * (H // 16 + 1),
-        blend=(4 + 40) * P + 12 * W * H,
+        blend=(4 + 48) * P + 12 * W * H,
     )
 
 

@@ -112,14 +112,14 @@ typedef struct {
     uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
 } vgr_view_opts;
 
-enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT,
+enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT, VGR_STAGE_COLOR,
        VGR_STAGE_EMIT, VGR_STAGE_TILE_SORT, VGR_STAGE_RANGES, VGR_STAGE_BLEND, VGR_N_STAGES };
 
 typedef struct {
     uint32_t cut_count;       /* |C| */
-    uint32_t visible_count;   /* |V|: cut Gaussians with at least one kept tile */
-    uint64_t pair_count;      /* P: kept (Gaussian, tile) pairs */
-    uint64_t candidate_pairs; /* P0: pairs examined by the tile-level filter */
+    uint32_t visible_count;   /* |V|: cut Gaussians with at least one candidate tile */
+    uint64_t pair_count;      /* P: (Gaussian, tile) pairs kept by the tile-level filter */
+    uint64_t candidate_pairs; /* P0: candidate pairs examined by the tile-level filter */
     uint64_t nodes_evaluated; /* granularity tests made by the LoD step */
     uint32_t lod_from_scratch;/* 1 if the cut was found top-down this frame */
     uint32_t replays;         /* frame replays (buffer growth or LoD fallback) */
@@ -145,11 +145,11 @@ typedef struct {
     const uint32_t* cut;          /* [n_cut] ascending node ids */
     const uint32_t* vis_node;     /* [n_visible] node id, in cut order */
     const uint32_t* vis_depth;    /* [n_visible] FP32 depth key bits */
-    const uint32_t* vis_ntile;    /* [n_visible] kept tiles */
+    const uint32_t* vis_ntile;    /* [n_visible] candidate tiles (area of vis_rect) */
     const uint32_t* vis_rect;     /* [2 n_visible] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
     const float* vis_recA;        /* [4 n_visible] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
-    const float* vis_recB;        /* [4 n_visible] C thr theta r, thr = ln alpha* - ln theta */
-    const float* vis_recC;        /* [2 n_visible] g b */
+    const float* vis_recB;        /* [4 n_visible] C thr theta h, thr = ln alpha* - ln theta, h = box half-height */
+    const float* rank_rgb;        /* [4 n_visible] r g b 0 in depth-rank order */
     const uint32_t* depth_order;  /* [n_visible] visible index by depth rank */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
     const uint32_t* pair_rank;    /* [n_pairs] depth rank of the Gaussian */

@@ -204,7 +204,7 @@ class View:
                     cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nv), vis_depth=u32(d.vis_depth, nv),
                     vis_ntile=u32(d.vis_ntile, nv), vis_rect=u32(d.vis_rect, 2 * nv).reshape(nv, 2),
                     vis_recA=f32(d.vis_recA, (nv, 4)), vis_recB=f32(d.vis_recB, (nv, 4)),
-                    vis_recC=f32(d.vis_recC, (nv, 2)), depth_order=u32(d.depth_order, nv),
+                    rank_rgb=f32(d.rank_rgb, (nv, 4)), depth_order=u32(d.depth_order, nv),
                     pair_tile=u32(d.pair_tile, npairs), pair_rank=u32(d.pair_rank, npairs),
                     tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
 

@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "VGR_OK", 1: "VGR_E_INVALID", 2: "VGR_E_NOMEM", 3: "VGR_E_CUD
 STORE_FP32, STORE_HALF = 0, 1
 FILTER_PREEMPTIVE, FILTER_CANONICAL = 0, 1
 EXP_EXACT, EXP_LUT = 0, 1
-STAGES = ["lod", "compact", "preprocess", "depth_sort", "emit", "tile_sort", "ranges", "blend"]
+STAGES = ["lod", "compact", "preprocess", "depth_sort", "color", "emit", "tile_sort", "ranges", "blend"]
 
 
 class SceneDesc(ctypes.Structure):
@@ -38,7 +38,7 @@ class ViewOpts(ctypes.Structure):
 class FrameStats(ctypes.Structure):
     _fields_ = [("cut_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64),
                 ("candidate_pairs", c_u64), ("nodes_evaluated", c_u64), ("lod_from_scratch", c_u32),
-                ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64), ("stage_ms", c_f32 * 8),
+                ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64), ("stage_ms", c_f32 * 9),
                 ("frame_ms", c_f32)]
 
 
@@ -51,7 +51,7 @@ class DebugBuffers(ctypes.Structure):
     _fields_ = [("n_cut", c_u32), ("n_visible", c_u32), ("n_pairs", c_u64), ("tiles_x", c_u32),
                 ("tiles_y", c_u32), ("cut", c_vp), ("vis_node", c_vp), ("vis_depth", c_vp),
                 ("vis_ntile", c_vp), ("vis_rect", c_vp), ("vis_recA", c_vp), ("vis_recB", c_vp),
-                ("vis_recC", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_rank", c_vp),
+                ("rank_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_rank", c_vp),
                 ("tile_range", c_vp)]
 
 

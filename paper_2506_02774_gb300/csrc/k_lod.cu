@@ -1,8 +1,9 @@
 // k_lod.cu -- LoD cut finding on the GPU (paper Sec. 3.1 'Cut Finding',
 // Sec. 4.1 'Temporal-Aware LoD Search', Algorithm 1).
 //
-// The cut is written as a bitmap over node ids, then compacted into an
-// ascending id list.  Two producers:
+// The cut is written as a bitmap over node ids (plus a second bitmap of the
+// cut nodes in front of the near plane), then compacted into ascending id
+// lists.  Two producers:
 //  * k_lod_update: the temporal update.  Each node n of the previous cut
 //    tests itself and its parent against the current camera:
 //      parent does not expand  -> collapse: climb to the highest ancestor whose
@@ -25,36 +26,64 @@
 
 namespace vgr {
 
+// A cut node joins the cut bitmap, and the in-front bitmap when its FP32
+// depth key is beyond the near plane (the same key and test as preprocess).
+struct CutOut {
+    uint32_t* cut_bm;
+    uint32_t* front_bm;
+    float R6, R7, R8, Cx, Cy, Cz, z_near;
+    __device__ __forceinline__ void add(uint32_t n, float4 c) const {
+        bitmap_set(cut_bm, n);
+        if (depth_key(c, R6, R7, R8, Cx, Cy, Cz) > z_near) bitmap_set(front_bm, n);
+    }
+};
+
+__device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, uint32_t* cut_bm, uint32_t* front_bm) {
+    CutOut o;
+    o.cut_bm = cut_bm;
+    o.front_bm = front_bm;
+    o.R6 = fp->R[6]; o.R7 = fp->R[7]; o.R8 = fp->R[8];
+    o.Cx = fp->pos[0]; o.Cy = fp->pos[1]; o.Cz = fp->pos[2];
+    o.z_near = fp->z_near;
+    return o;
+}
+
 __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__ prev_cut,
                                                     const uint32_t* __restrict__ n_prev_p, uint32_t cap_prev,
-                                                    SceneDev sc,
-                                                    const FrameParams* __restrict__ fp, uint32_t* __restrict__ bitmap,
+                                                    SceneDev sc, const FrameParams* __restrict__ fp,
+                                                    uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
                                                     Counters* __restrict__ ctr) {
     const uint32_t n_prev = min(*n_prev_p, cap_prev);
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const uint32_t budget = fp->lod_budget, max_depth = fp->max_depth;
+    const CutOut out = make_cut_out(fp, bitmap, front);
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_prev; i += stride) {
         const uint32_t n = prev_cut[i];
-        const bool en = lod_expand(sc.cr[n], px, py, pz, k);
+        const float4 cn = sc.cr[n];
+        const bool en = lod_expand(cn, px, py, pz, k);
         const uint32_t p = sc.parent[n];
         bool ep = true;
+        float4 cp = cn;
         ++evals;
-        if (p != NONE) { ep = lod_expand(sc.cr[p], px, py, pz, k); ++evals; }
+        if (p != NONE) { cp = sc.cr[p]; ep = lod_expand(cp, px, py, pz, k); ++evals; }
         if (!ep) {
             if (en) flags |= F_NONMONOTONE;
             // collapse: climb while the parent of a does not expand
             uint32_t a = p;
+            float4 ca = cp;
             for (uint32_t steps = 0;; ++steps) {
                 const uint32_t pa = sc.parent[a];
                 if (pa == NONE) break;
                 ++evals;
-                if (lod_expand(sc.cr[pa], px, py, pz, k)) break;
+                const float4 cpa = sc.cr[pa];
+                if (lod_expand(cpa, px, py, pz, k)) break;
                 a = pa;
+                ca = cpa;
                 if (steps > max_depth) { flags |= F_LOD_FALLBACK; break; }
             }
-            bitmap_set(bitmap, a);
+            out.add(a, ca);
         } else if (en) {
             // expand: depth-first over n's subtree, children ranges on a stack
             uint32_t nxt[MAX_TREE_DEPTH], end[MAX_TREE_DEPTH];
@@ -67,19 +96,20 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
                 if (nxt[sp - 1] == end[sp - 1]) { --sp; continue; }
                 const uint32_t m = nxt[sp - 1]++;
                 if (++local > budget) { flags |= F_LOD_FALLBACK; break; }
-                if (lod_expand(sc.cr[m], px, py, pz, k)) {
+                const float4 cm = sc.cr[m];
+                if (lod_expand(cm, px, py, pz, k)) {
                     if (sp == MAX_TREE_DEPTH) { flags |= F_LOD_FALLBACK; break; }
-                    const uint32_t cm = sc.child[m];
-                    nxt[sp] = cm & CHILD_MASK;
-                    end[sp] = nxt[sp] + (cm >> CHILD_SHIFT);
+                    const uint32_t chm = sc.child[m];
+                    nxt[sp] = chm & CHILD_MASK;
+                    end[sp] = nxt[sp] + (chm >> CHILD_SHIFT);
                     ++sp;
                 } else {
-                    bitmap_set(bitmap, m);
+                    out.add(m, cm);
                 }
             }
             evals += local;
         } else {
-            bitmap_set(bitmap, n);
+            out.add(n, cn);
         }
     }
     // one atomic per warp for the statistics
@@ -95,10 +125,12 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
 __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __restrict__ fin,
                                                    uint32_t* __restrict__ fout, uint32_t cap, SceneDev sc,
                                                    const FrameParams* __restrict__ fp,
-                                                   uint32_t* __restrict__ bitmap, Counters* __restrict__ ctr) {
+                                                   uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
+                                                   Counters* __restrict__ ctr) {
     const uint32_t n_in = level == 0 ? 1u : min(ctr->frontier_n[level], cap);
     uint32_t* n_out = &ctr->frontier_n[level + 1];
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
+    const CutOut out = make_cut_out(fp, bitmap, front);
     const uint32_t lane = lane_id();
     const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -108,13 +140,14 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
         uint32_t cnt = 0, first = 0;
         if (i < n_in) {
             const uint32_t n = level == 0 ? 0u : fin[i];
+            const float4 cn = sc.cr[n];
             ++evals;
-            if (lod_expand(sc.cr[n], px, py, pz, k)) {
+            if (lod_expand(cn, px, py, pz, k)) {
                 const uint32_t c = sc.child[n];
                 first = c & CHILD_MASK;
                 cnt = c >> CHILD_SHIFT;
             } else {
-                bitmap_set(bitmap, n);
+                out.add(n, cn);
             }
         }
         uint32_t total;
@@ -132,50 +165,79 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
     if (lane == 0 && wsum) atomicAdd(&ctr->nodes_eval, (unsigned long long)wsum);
 }
 
-// Bitmap -> ascending id list, clearing the bitmap for the next frame.
-// Tiles of 256 threads x 4 words, ordered by a decoupled look-back scan.
+// Bitmaps -> ascending id lists (the cut, and its in-front part), clearing
+// both bitmaps for the next frame.  Tiles of 256 threads x 4 words; two
+// decoupled look-back chains (warp 0: cut, warp 1: in-front) give each tile
+// its output offsets; each warp then writes its 128 words' ids in order, one
+// word per step with a ballot, so every store instruction is coalesced.
 constexpr int CC_WORDS = 4;
 constexpr int CC_TILE_WORDS = 256 * CC_WORDS;
 
-__global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitmap, uint32_t n_words,
-                                                     uint32_t* __restrict__ cut, uint32_t cap,
+__device__ __forceinline__ void cc_write(const uint32_t (&w)[4], uint32_t wbase, uint32_t off, uint32_t* out,
+                                         uint32_t cap) {
+    const uint32_t lane = lane_id();
+    uint32_t nz = __ballot_sync(0xFFFFFFFFu, (w[0] | w[1] | w[2] | w[3]) != 0u);
+    while (nz) {
+        const int src = __ffs(nz) - 1;
+        nz &= nz - 1u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t word = __shfl_sync(0xFFFFFFFFu, w[j], src);
+            if (word == 0u) continue;
+            const bool bit = (word >> lane) & 1u;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+            if (bit) {
+                const uint32_t pos = off + __popc(m & lanemask_lt());
+                if (pos < cap) out[pos] = (wbase + (uint32_t)src * 4u + (uint32_t)j) * 32u + lane;
+            }
+            off += __popc(m);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
+                                                     uint32_t n_words, uint32_t* __restrict__ cut,
+                                                     uint32_t* __restrict__ front_list, uint32_t cap,
                                                      uint32_t* __restrict__ n_cut_out,
                                                      unsigned long long* __restrict__ status,
+                                                     unsigned long long* __restrict__ status_front,
                                                      Counters* __restrict__ ctr,
                                                      const FrameParams* __restrict__ fp) {
     __shared__ uint32_t s_scan[9];
-    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_tile, s_prefix[2];
     const uint32_t ntiles = (n_words + CC_TILE_WORDS - 1) / CC_TILE_WORDS;
     const uint32_t epoch = fp->epoch;
+    const uint32_t warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_COMPACT], 1u);
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) break;
         const uint32_t w0 = tile * CC_TILE_WORDS + threadIdx.x * CC_WORDS;
-        // the bitmap is padded to a whole number of tiles
-        uint4 w = *reinterpret_cast<const uint4*>(bitmap + w0);
-        const uint32_t cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
-        uint32_t total;
-        const uint32_t excl = block_excl_scan<8>(cnt, s_scan, &total);
-        if (threadIdx.x == 0) s_prefix = lookback(status, 1, tile, total, epoch, &ctr->flags);
-        __syncthreads();
-        uint32_t off = s_prefix + excl;
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            uint32_t x = ws[j];
-            while (x) {
-                const uint32_t b = __ffs(x) - 1u;
-                if (off < cap) cut[off] = (w0 + j) * 32u + b;
-                ++off;
-                x &= x - 1u;
-            }
+        // the bitmaps are padded to a whole number of tiles
+        const uint4 a = *reinterpret_cast<const uint4*>(bitmap + w0);
+        const uint4 b = *reinterpret_cast<const uint4*>(front + w0);
+        const uint32_t ca = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w);
+        const uint32_t cb = __popc(b.x) + __popc(b.y) + __popc(b.z) + __popc(b.w);
+        uint32_t total;  // both counts in one scan: at most 32768 each per tile
+        const uint32_t excl = block_excl_scan<8>(ca | (cb << 16), s_scan, &total);
+        if (warp < 2) {
+            const uint32_t agg = warp == 0 ? (total & 0xFFFFu) : (total >> 16);
+            const uint32_t pre = lookback_warp(warp == 0 ? status : status_front, 1, tile, agg, epoch, &ctr->flags);
+            if (lane_id() == 0) s_prefix[warp] = pre;
         }
-        if (cnt) *reinterpret_cast<uint4*>(bitmap + w0) = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        const uint32_t wbase = tile * CC_TILE_WORDS + warp * 32u * CC_WORDS;
+        const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
+        const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, excl, 0);
+        cc_write(wa, wbase, s_prefix[0] + (e0 & 0xFFFFu), cut, cap);
+        cc_write(wb, wbase, s_prefix[1] + (e0 >> 16), front_list, cap);
+        if (ca) *reinterpret_cast<uint4*>(bitmap + w0) = make_uint4(0u, 0u, 0u, 0u);
+        if (cb) *reinterpret_cast<uint4*>(front + w0) = make_uint4(0u, 0u, 0u, 0u);
         if (tile == ntiles - 1 && threadIdx.x == 0) {
-            const uint32_t n = s_prefix + total;
+            const uint32_t n = s_prefix[0] + (total & 0xFFFFu);
             *n_cut_out = n;
+            ctr->n_front = s_prefix[1] + (total >> 16);
             if (n > cap) atomicOr(&ctr->flags, F_OVF_CUT);
         }
         __syncthreads();
@@ -184,19 +246,23 @@ __global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitm
 
 // ------------------------------------------------------------ launchers
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
-                       const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s) {
-    k_lod_update<<<grid, 256, 0, s>>>(prev_cut, n_prev, cap_prev, sc, fp, bitmap, ctr);
+                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
+                       cudaStream_t s) {
+    k_lod_update<<<grid, 256, 0, s>>>(prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
 }
 
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
-                      const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s) {
-    k_lod_level<<<grid, 256, 0, s>>>(level, fin, fout, cap, sc, fp, bitmap, ctr);
+                      const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
+                      cudaStream_t s) {
+    k_lod_level<<<grid, 256, 0, s>>>(level, fin, fout, cap, sc, fp, bitmap, front, ctr);
 }
 
-void launch_cut_compact(uint32_t* bitmap, uint32_t n_words, uint32_t* cut, uint32_t cap, uint32_t* n_cut_out,
-                        unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
+void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,
+                        uint32_t cap, uint32_t* n_cut_out, unsigned long long* status,
+                        unsigned long long* status_front, Counters* ctr, const FrameParams* fp, int grid,
                         cudaStream_t s) {
-    k_cut_compact<<<grid, 256, 0, s>>>(bitmap, n_words, cut, cap, n_cut_out, status, ctr, fp);
+    k_cut_compact<<<grid, 256, 0, s>>>(bitmap, front, n_words, cut, front_list, cap, n_cut_out, status,
+                                       status_front, ctr, fp);
 }
 
 uint32_t cut_compact_tiles(uint32_t n_words) { return (n_words + CC_TILE_WORDS - 1) / CC_TILE_WORDS; }

@@ -2,31 +2,31 @@
 // 'Culling & Projection') with the preemptive alpha filter moved into it
 // (Sec. 4.2, Eq. 4: alpha >= alpha* <=> rho >= ln alpha* - ln theta).
 //
-// One thread per cut node, tiles of 256 cut entries handed out by ticket and
-// compacted in order by a decoupled look-back scan, so visible Gaussians keep
-// ascending node-id order (the depth sort is stable, so equal depths stay
-// ordered by node id).
+// One thread per cut node in front of the near plane (the LoD stage lists
+// them), tiles of 256 entries handed out by ticket and compacted in order by a
+// decoupled look-back scan, so visible Gaussians keep ascending node-id order
+// (the depth sort is stable, so equal depths stay ordered by node id).
 //
 // Per node: p = R (mu - C); depth key = FP32 bits of
 // ((R20 dx + R21 dy) + R22 dz) with single-rounded operations; culled when
 // z <= z_near.  Gaussian-level filter: theta < alpha* is dropped.  EWA:
 // Sigma' = M Sigma M^T + 0.3 I with M = J R, J the perspective Jacobian with
 // x/z, y/z clamped to 1.3 (W/2)/fx, 1.3 (H/2)/fy.  Footprint box from
-// r^2 = 2 (ln theta - ln alpha*) (plus the test slack), candidate tiles are
-// those whose pixel-centre rectangle meets the box, and a candidate is kept
-// when the maximum of rho over that rectangle reaches ln alpha* - ln theta
-// (minus a 2e-3 slack that makes the FP32 test a superset of the exact one).
-// Colour from real SH up to degree 3 (+0.5, clamped at 0).
+// r^2 = 2 (ln theta - ln alpha*) (plus the 2e-3 test slack); candidate tiles
+// are those whose pixel-centre rectangle meets the box.  A Gaussian is kept
+// when it has at least one candidate tile; the tile-level test (Eq. 4 over
+// each candidate tile) runs in the emission, where the work is balanced over
+// candidate slots.  Colour (real SH up to degree 3, +0.5, clamped at 0) is a
+// separate dense kernel over the visible list, so the 192-byte SH reads run
+// at full occupancy, outside the ordered scan, in ascending node order.
 #include <cuda_fp16.h>
 
 #include "vgr_internal.cuh"
 #include "vgr_launch.h"
-#include "vgr_tiletest.cuh"
 
 namespace vgr {
 
 constexpr int PRE_THREADS = 256;
-constexpr uint32_t COOP_MIN_AREA = 8;  // candidate rectangles above this are tested by the whole warp
 
 // Real spherical harmonics (orthonormal, Condon-Shortley phase) as
 // polynomials of the unit direction; constants are the closed forms
@@ -119,19 +119,17 @@ struct Store<VGR_STORE_HALF> {
     }
 };
 
-template <int DEG, int STORE>
-__global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const uint32_t* __restrict__ cut,
-                                                            const uint32_t* __restrict__ n_cut_p, uint32_t cap_cut,
-                                                            const FrameParams* __restrict__ fp, VisBuffers vis,
-                                                            uint32_t cap_vis,
-                                                            unsigned long long* __restrict__ status,
-                                                            Counters* __restrict__ ctr) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
+template <int STORE>
+__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, const uint32_t* __restrict__ cut,
+                                                               const uint32_t* __restrict__ n_cut_p, uint32_t cap_cut,
+                                                               const FrameParams* __restrict__ fp, VisBuffers vis,
+                                                               uint32_t cap_vis,
+                                                               unsigned long long* __restrict__ status,
+                                                               Counters* __restrict__ ctr) {
     __shared__ uint32_t s_scan[9];
     __shared__ uint32_t s_tile, s_prefix;
     const uint32_t n_cut = min(*n_cut_p, cap_cut);
     const uint32_t ntiles = (n_cut + PRE_THREADS - 1) / PRE_THREADS;
-    const uint32_t lane = lane_id();
 
     const float R0 = fp->R[0], R1 = fp->R[1], R2 = fp->R[2], R3 = fp->R[3], R4 = fp->R[4], R5 = fp->R[5];
     const float R6 = fp->R[6], R7 = fp->R[7], R8 = fp->R[8];
@@ -141,7 +139,6 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
     const int TW = (int)fp->tiles_x, TH = (int)fp->tiles_y;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     const uint32_t epoch = fp->epoch;
-    unsigned long long cand = 0;
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_PRE], 1u);
@@ -152,15 +149,12 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
 
         bool v = i < n_cut;
         uint32_t node = 0, zbits = 0;
-        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, rx = 0.f, ry = 0.f, thr = 0.f, theta = 0.f;
-        float dx = 0.f, dy = 0.f, dz = 0.f;
+        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f;
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
             node = cut[i];
             const float4 m = sc.cr[node];
-            dx = __fsub_rn(m.x, Cx);
-            dy = __fsub_rn(m.y, Cy);
-            dz = __fsub_rn(m.z, Cz);
+            const float dx = __fsub_rn(m.x, Cx), dy = __fsub_rn(m.y, Cy), dz = __fsub_rn(m.z, Cz);
             const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
             zbits = __float_as_uint(z);
             v = z > z_near;
@@ -179,7 +173,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
                 const float tx = fminf(limx, fmaxf(-limx, xz));
                 const float ty = fminf(limy, fmaxf(-limy, yz));
                 const float fxz = fx * iz, fyz = fy * iz;
-                // M = J R: rows M0 = fx/z (R0 - tx R2row), M1 = fy/z (R1row - ty R2row)
+                // M = J R: rows M0 = fx/z (R0row - tx R2row), M1 = fy/z (R1row - ty R2row)
                 const float m00 = fxz * fmaf(-tx, R6, R0), m01 = fxz * fmaf(-tx, R7, R1), m02 = fxz * fmaf(-tx, R8, R2);
                 const float m10 = fyz * fmaf(-ty, R6, R3), m11 = fyz * fmaf(-ty, R7, R4), m12 = fyz * fmaf(-ty, R8, R5);
                 // Sigma M0^T, Sigma M1^T (Sigma = [[S0 S1 S2] [S1 S3 S4] [S2 S4 S5]])
@@ -203,11 +197,10 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
                     ca = s11 * idet;
                     cb = -s01 * idet;
                     cc = s00 * idet;
-                    rx = __fdiv_rn(-cb, ca);
-                    ry = __fdiv_rn(-cb, cc);
                     thr = LN_ALPHA_MIN - lnth;
                     float bx, by;
                     if (!canonical) {
+                        // opacity-aware box of {rho >= thr - slack}
                         const float r2 = fmaxf(0.f, 2.0f * (lnth - LN_ALPHA_MIN) + 2.0f * TILE_EPS);
                         bx = sqrtf(r2 * s00) * 1.0001f + 1e-3f;
                         by = sqrtf(r2 * s11) * 1.0001f + 1e-3f;
@@ -225,74 +218,29 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
                         tx1 = -1;  // far outside (also guards the float->int conversions)
                     }
                     if (tx0 > tx1 || ty0 > ty1) v = false;
+                    half_h = by;
                 }
             }
         }
-        // kept tiles: per thread for small rectangles, warp-cooperative for large ones
-        const uint32_t wdt = v ? (uint32_t)(tx1 - tx0 + 1) : 0u;
-        const uint32_t area = v ? wdt * (uint32_t)(ty1 - ty0 + 1) : 0u;
-        cand += area;
-        const float thre = thr - TILE_EPS;
-        uint32_t nt = 0;
-        const bool coop = !canonical && area > COOP_MIN_AREA;
-        if (v && !coop) {
-            if (canonical) {
-                nt = area;
-            } else {
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx)
-                        nt += tile_keep(u, vv, ca, cb, cc, rx, ry, thre, tx, ty, Wf, Hf);
-            }
-        }
-        uint32_t mask = __ballot_sync(0xFFFFFFFFu, coop);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            const float su = __shfl_sync(0xFFFFFFFFu, u, src), sv = __shfl_sync(0xFFFFFFFFu, vv, src);
-            const float sa = __shfl_sync(0xFFFFFFFFu, ca, src), sb = __shfl_sync(0xFFFFFFFFu, cb, src);
-            const float sc_ = __shfl_sync(0xFFFFFFFFu, cc, src), srx = __shfl_sync(0xFFFFFFFFu, rx, src);
-            const float sry = __shfl_sync(0xFFFFFFFFu, ry, src), sth = __shfl_sync(0xFFFFFFFFu, thre, src);
-            const int stx0 = __shfl_sync(0xFFFFFFFFu, tx0, src), sty0 = __shfl_sync(0xFFFFFFFFu, ty0, src);
-            const uint32_t sw = __shfl_sync(0xFFFFFFFFu, wdt, src), sarea = __shfl_sync(0xFFFFFFFFu, area, src);
-            uint32_t c = 0;
-            for (uint32_t j = lane; j < sarea; j += 32u)
-                c += tile_keep(su, sv, sa, sb, sc_, srx, sry, sth, stx0 + (int)(j % sw), sty0 + (int)(j / sw), Wf, Hf);
-            c = __reduce_add_sync(0xFFFFFFFFu, c);
-            if (lane == (uint32_t)src) nt = c;
-        }
-        if (nt == 0) v = false;
-
-        float r = 0.f, g = 0.f, bl = 0.f;
-        if (v) {
-            float shc[((3 * K + 7) / 8) * 8];
-            Store<STORE>::template sh<K>(sc, node, shc);
-            float Y[K];
-            const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            sh_basis<DEG>(dx * inv, dy * inv, dz * inv, Y);
-            r = 0.5f; g = 0.5f; bl = 0.5f;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                r = fmaf(shc[3 * kk + 0], Y[kk], r);
-                g = fmaf(shc[3 * kk + 1], Y[kk], g);
-                bl = fmaf(shc[3 * kk + 2], Y[kk], bl);
-            }
-            r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); bl = fmaxf(bl, 0.f);
-        }
+        // candidate tiles; the tile-level test itself runs in the emission
+        const uint32_t area = v ? (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1) : 0u;
 
         uint32_t total;
         const uint32_t rank = block_excl_scan<PRE_THREADS / 32>(v ? 1u : 0u, s_scan, &total);
-        if (threadIdx.x == 0) s_prefix = lookback(status, 1, tile, total, epoch, &ctr->flags);
+        if (threadIdx.x < 32) {
+            const uint32_t pre = lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
+            if (threadIdx.x == 0) s_prefix = pre;
+        }
         __syncthreads();
         if (v) {
             const uint32_t o = s_prefix + rank;
             if (o < cap_vis) {
                 vis.node[o] = node;
                 vis.depth[o] = zbits;
-                vis.ntile[o] = nt;
+                vis.ntile[o] = area;
                 vis.rect[o] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
                 vis.recA[o] = make_float4(u, vv, -0.5f * ca, -cb);
-                vis.recB[o] = make_float4(-0.5f * cc, thr, theta, r);
-                vis.recC[o] = make_float2(g, bl);
+                vis.recB[o] = make_float4(-0.5f * cc, thr, theta, half_h);
             }
         }
         if (tile == ntiles - 1 && threadIdx.x == 0) {
@@ -302,10 +250,36 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
         }
         __syncthreads();
     }
-    unsigned long long wc = cand;
+}
+
+// Colour of the visible Gaussians (dense, no barriers), in visible order,
+// i.e. ascending node id, so consecutive threads read neighbouring SH rows:
+// rgb = sum_lm c_lm Y_lm(d) + 0.5, clamped at 0, d = (mu - C)/|mu - C|.
+template <int DEG, int STORE>
+__global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __restrict__ vis_node, uint32_t cap_vis,
+                                               const FrameParams* __restrict__ fp, const Counters* __restrict__ ctr,
+                                               float4* __restrict__ rgb_out) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const uint32_t n = min(ctr->n_vis, cap_vis);
+    const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t node = vis_node[r];
+        float shc[((3 * K + 7) / 8) * 8];
+        Store<STORE>::template sh<K>(sc, node, shc);
+        const float4 m = sc.cr[node];
+        const float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
+        float Y[K];
+        const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        sh_basis<DEG>(dx * inv, dy * inv, dz * inv, Y);
+        float cr = 0.5f, cg = 0.5f, cbl = 0.5f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wc += __shfl_down_sync(0xFFFFFFFFu, wc, o);
-    if (lane == 0 && wc) atomicAdd(&ctr->n_cand, wc);
+        for (int kk = 0; kk < K; ++kk) {
+            cr = fmaf(shc[3 * kk + 0], Y[kk], cr);
+            cg = fmaf(shc[3 * kk + 1], Y[kk], cg);
+            cbl = fmaf(shc[3 * kk + 2], Y[kk], cbl);
+        }
+        rgb_out[r] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cbl, 0.f), 0.f);
+    }
 }
 
 // ln(opacity) next to the opacity (Eq. 4 needs ln theta per Gaussian)
@@ -325,30 +299,31 @@ void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
     k_prepare<<<1024, 256, 0, s>>>(covB, n, 1);
 }
 
-template <int DEG, int STORE>
-static void launch_pre_t(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
-                         const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
-                         Counters* ctr, int grid, cudaStream_t s) {
-    k_preprocess<DEG, STORE><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
-}
-
 void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
                        const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
                        Counters* ctr, int grid, cudaStream_t s) {
+    if (sc.storage == VGR_STORE_HALF)
+        k_preprocess<VGR_STORE_HALF><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
+    else
+        k_preprocess<VGR_STORE_FP32><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
+}
+
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, uint32_t cap_vis, const FrameParams* fp,
+                  const Counters* ctr, float4* rgb, int grid, cudaStream_t s) {
     const bool half = sc.storage == VGR_STORE_HALF;
-#define VGR_PRE_CASE(D)                                                                        \
-    case D:                                                                                    \
-        if (half) launch_pre_t<D, VGR_STORE_HALF>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr, grid, s); \
-        else launch_pre_t<D, VGR_STORE_FP32>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr, grid, s);      \
+#define VGR_COLOR_CASE(D)                                                                                   \
+    case D:                                                                                                 \
+        if (half) k_color<D, VGR_STORE_HALF><<<grid, 256, 0, s>>>(sc, vis_node, cap_vis, fp, ctr, rgb); \
+        else k_color<D, VGR_STORE_FP32><<<grid, 256, 0, s>>>(sc, vis_node, cap_vis, fp, ctr, rgb);      \
         break;
     switch (sc.sh_degree) {
-        VGR_PRE_CASE(0)
-        VGR_PRE_CASE(1)
-        VGR_PRE_CASE(2)
-        VGR_PRE_CASE(3)
+        VGR_COLOR_CASE(0)
+        VGR_COLOR_CASE(1)
+        VGR_COLOR_CASE(2)
+        VGR_COLOR_CASE(3)
         default: break;
     }
-#undef VGR_PRE_CASE
+#undef VGR_COLOR_CASE
 }
 
 uint32_t preprocess_tile() { return PRE_THREADS; }

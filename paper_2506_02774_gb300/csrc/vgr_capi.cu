@@ -96,6 +96,8 @@ struct vgr_view {
     // device buffers
     uint32_t* cut[2] = {nullptr, nullptr};
     uint32_t* bitmap = nullptr;
+    uint32_t* front_bm = nullptr;     // cut nodes in front of the near plane
+    uint32_t* front_list = nullptr;   // their ids, ascending (cap_cut)
     uint32_t n_words = 0;
     uint32_t* frontier[2] = {nullptr, nullptr};
     VisBuffers vis{};
@@ -103,14 +105,14 @@ struct vgr_view {
     uint32_t* sortV[2] = {nullptr, nullptr};
     float4* srecA = nullptr;
     float4* srecB = nullptr;
-    float2* srecC = nullptr;
+    float4* srecC = nullptr;  // r g b, depth-rank order
     uint32_t* pairK[2] = {nullptr, nullptr};
     uint32_t* pairV[2] = {nullptr, nullptr};
     uint2* ranges = nullptr;
     float* image = nullptr;
     float* lut = nullptr;
     unsigned long long* status = nullptr;
-    size_t st_compact = 0, st_pre = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
+    size_t st_compact = 0, st_front = 0, st_pre = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
            st_tile_stride = 0, st_words = 0;
     Counters* ctr = nullptr;
     ViewState* vstate = nullptr;
@@ -351,7 +353,7 @@ namespace {
 
 void free_vis(vgr_view* v) {
     dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
-    dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.recC);
+    dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
     dfree(v->srecA); dfree(v->srecB); dfree(v->srecC);
     v->vis_bytes = 0;
@@ -364,7 +366,8 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
     if ((s = dalloc(&v->vis.node, cap, &b)) || (s = dalloc(&v->vis.depth, cap, &b)) ||
         (s = dalloc(&v->vis.ntile, cap, &b)) || (s = dalloc(&v->vis.rect, cap, &b)) ||
         (s = dalloc(&v->vis.recA, cap, &b)) || (s = dalloc(&v->vis.recB, cap, &b)) ||
-        (s = dalloc(&v->vis.recC, cap, &b)) || (s = dalloc(&v->sortK[0], cap, &b)) ||
+        (s = dalloc(&v->vis.rgb, cap, &b)) ||
+        (s = dalloc(&v->sortK[0], cap, &b)) ||
         (s = dalloc(&v->sortK[1], cap, &b)) || (s = dalloc(&v->sortV[0], cap, &b)) ||
         (s = dalloc(&v->sortV[1], cap, &b)) || (s = dalloc(&v->srecA, cap, &b)) ||
         (s = dalloc(&v->srecB, cap, &b)) || (s = dalloc(&v->srecC, cap, &b))) {
@@ -396,7 +399,7 @@ vgr_status alloc_pairs(vgr_view* v, uint64_t cap) {
 }
 
 void free_cut(vgr_view* v) {
-    dfree(v->cut[0]); dfree(v->cut[1]);
+    dfree(v->cut[0]); dfree(v->cut[1]); dfree(v->front_list);
     v->cut_bytes = 0;
 }
 
@@ -404,7 +407,8 @@ vgr_status alloc_cut(vgr_view* v, uint32_t cap) {
     free_cut(v);
     uint64_t b = 0;
     vgr_status s;
-    if ((s = dalloc(&v->cut[0], cap, &b)) || (s = dalloc(&v->cut[1], cap, &b))) {
+    if ((s = dalloc(&v->cut[0], cap, &b)) || (s = dalloc(&v->cut[1], cap, &b)) ||
+        (s = dalloc(&v->front_list, cap, &b))) {
         free_cut(v);
         return s;
     }
@@ -418,7 +422,8 @@ vgr_status alloc_status(vgr_view* v) {
     dfree(v->status);
     const uint32_t RT = radix_tile();
     v->st_compact = 0;
-    v->st_pre = v->st_compact + cut_compact_tiles(v->n_words) + 1;
+    v->st_front = v->st_compact + cut_compact_tiles(v->n_words) + 1;
+    v->st_pre = v->st_front + cut_compact_tiles(v->n_words) + 1;
     v->st_emit = v->st_pre + ceil_div(v->cap_cut, preprocess_tile()) + 1;
     v->st_depth = v->st_emit + ceil_div(v->cap_vis, emit_tile()) + 1;
     v->st_depth_stride = (size_t)(ceil_div(v->cap_vis, RT) + 1) * 256;
@@ -454,7 +459,7 @@ void destroy_view(vgr_view* v) {
     free_vis(v);
     free_pairs(v);
     free_cut(v);
-    dfree(v->bitmap); dfree(v->frontier[0]); dfree(v->frontier[1]);
+    dfree(v->bitmap); dfree(v->front_bm); dfree(v->frontier[0]); dfree(v->frontier[1]);
     dfree(v->ranges); dfree(v->image); dfree(v->lut); dfree(v->status);
     dfree(v->ctr); dfree(v->vstate); dfree(v->fp_dev);
     if (v->fp_host) cudaFreeHost(v->fp_host);
@@ -514,6 +519,7 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     const uint32_t TW = cut_compact_tile_words();
     v->n_words = (uint32_t)(((uint64_t)(N + 31) / 32 + TW - 1) / TW * TW);
     VGR_VTRY(dalloc(&v->bitmap, v->n_words, &v->fixed_bytes));
+    VGR_VTRY(dalloc(&v->front_bm, v->n_words, &v->fixed_bytes));
     VGR_VTRY(dalloc(&v->frontier[0], N, &v->fixed_bytes));
     VGR_VTRY(dalloc(&v->frontier[1], N, &v->fixed_bytes));
     VGR_VTRY(dalloc(&v->ctr, 1, &v->fixed_bytes));
@@ -570,9 +576,11 @@ vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes) {
 
 namespace {
 
+// Digit passes of the tile sort: tile ids 0 .. n_tiles-1 plus the sentinel
+// (all ones in the sorted bits) that marks dropped candidate slots.
 int tile_passes_for(uint32_t n_tiles) {
     int bits = 0;
-    while (bits < 32 && ((uint64_t)1 << bits) < n_tiles) ++bits;
+    while (bits < 32 && ((uint64_t)1 << bits) <= n_tiles) ++bits;
     return std::max(1, (bits + 7) / 8);
 }
 
@@ -593,16 +601,17 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     if (scratch) {
         for (uint32_t level = 0; level <= v->h->max_depth; ++level)
             launch_lod_level((int)level, sc, v->frontier[level & 1], v->frontier[(level + 1) & 1], v->h->n_nodes,
-                             v->fp_dev, v->bitmap, v->ctr, v->grid_wide, s);
+                             v->fp_dev, v->bitmap, v->front_bm, v->ctr, v->grid_wide, s);
     } else {
-        launch_lod_update(sc, v->cut[prev], &v->vstate->n_cut[prev], v->cap_cut, v->fp_dev, v->bitmap, v->ctr,
-                          v->grid_wide, s);
+        launch_lod_update(sc, v->cut[prev], &v->vstate->n_cut[prev], v->cap_cut, v->fp_dev, v->bitmap, v->front_bm,
+                          v->ctr, v->grid_wide, s);
     }
     mark(VGR_STAGE_COMPACT);
-    launch_cut_compact(v->bitmap, v->n_words, v->cut[cur], v->cap_cut, &v->vstate->n_cut[cur],
-                       v->status + v->st_compact, v->ctr, v->fp_dev, v->grid_scan, s);
+    launch_cut_compact(v->bitmap, v->front_bm, v->n_words, v->cut[cur], v->front_list, v->cap_cut,
+                       &v->vstate->n_cut[cur], v->status + v->st_compact, v->status + v->st_front, v->ctr, v->fp_dev,
+                       v->grid_scan, s);
     mark(VGR_STAGE_PREPROCESS);
-    launch_preprocess(sc, v->cut[cur], &v->vstate->n_cut[cur], v->cap_cut, v->fp_dev, v->vis, v->cap_vis,
+    launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->cap_vis,
                       v->status + v->st_pre, v->ctr, v->grid_scan, s);
     mark(VGR_STAGE_DEPTH_SORT);
     launch_radix_hist(v->vis.depth, &v->ctr->n_vis, nullptr, v->cap_vis, 4, &v->ctr->depth_hist[0][0],
@@ -615,20 +624,23 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
+    mark(VGR_STAGE_COLOR);
+    launch_color(sc, v->vis.node, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, v->grid_wide, s);
     mark(VGR_STAGE_EMIT);
+    const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->srecA, v->srecB, v->srecC, v->pairK[0], v->pairV[0], v->cap_pairs,
-                tile_passes, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, s);
+                tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, s);
     mark(VGR_STAGE_TILE_SORT);
     for (int p = 0; p < tile_passes; ++p) {
         launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
-                          &v->ctr->n_pairs, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
+                          &v->ctr->n_cand, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
                           v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
                           v->fp_dev, v->ctr, v->grid_scan, s);
     }
     const int fb = tile_passes & 1;
     v->last_tile_buf = fb;
     mark(VGR_STAGE_RANGES);
-    launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, v->ranges, v->grid_wide, s);
+    launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, n_tiles, v->ranges, v->grid_wide, s);
     mark(VGR_STAGE_BLEND);
     launch_blend(n_tiles, v->ranges, v->pairV[fb], v->srecA, v->srecB, v->srecC, v->fp_dev, v->lut, v->image, v->ctr,
                  v->opts.filter, v->opts.exp_mode, s);
@@ -636,8 +648,8 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
-    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 5u /*depth hist + 4 passes*/ + 1u /*emit*/ +
-           (uint32_t)tile_passes + 1u /*ranges*/ + 1u /*blend*/;
+    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 5u /*depth hist + 4 passes*/ + 1u /*color*/ +
+           1u /*emit*/ + (uint32_t)tile_passes + 1u /*ranges*/ + 1u /*blend*/;
 }
 
 vgr_status check_camera(const vgr_camera* c, float tau) {
@@ -717,7 +729,7 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
             continue;
         }
         if (flags & F_OVF_PAIRS) {
-            const uint64_t np = ch->n_pairs + ch->n_pairs / 4 + 4096;
+            const uint64_t np = ch->n_cand + ch->n_cand / 4 + 4096;
             if (np >= 0xFFFFFFFFull) return fail(VGR_E_OVERFLOW, "more than 2^32 pairs");
             if ((s = alloc_pairs(v, np)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
             ++replays;
@@ -793,7 +805,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     o->vis_rect = reinterpret_cast<const uint32_t*>(v->vis.rect);
     o->vis_recA = reinterpret_cast<const float*>(v->vis.recA);
     o->vis_recB = reinterpret_cast<const float*>(v->vis.recB);
-    o->vis_recC = reinterpret_cast<const float*>(v->vis.recC);
+    o->rank_rgb = reinterpret_cast<const float*>(v->srecC);
     o->depth_order = v->sortV[1];
     o->pair_tile = v->pairK[v->last_tile_buf];
     o->pair_rank = v->pairV[v->last_tile_buf];

@@ -63,6 +63,8 @@ struct FrameParams {
 struct Counters {
     uint32_t n_vis;
     uint32_t flags;
+    uint32_t n_front;  // cut nodes in front of the near plane
+    uint32_t pad0;
     unsigned long long n_pairs;
     unsigned long long n_cand;
     unsigned long long nodes_eval;
@@ -72,7 +74,7 @@ struct Counters {
     uint32_t depth_hist[4][256];
     uint32_t tile_hist[4][256];
 };
-constexpr size_t COUNTERS_HEAD = 48;  // bytes read back per frame
+constexpr size_t COUNTERS_HEAD = 48;  // bytes read back per frame (n_vis .. pix_evals)
 
 // Persistent per-view values (not cleared per frame).
 struct ViewState {
@@ -177,6 +179,63 @@ __device__ __forceinline__ uint32_t lookback(unsigned long long* status, uint32_
     }
     lb_store(status + (size_t)tile * stride, lb_pack(epoch, 2u, prefix + agg));
     return prefix;
+}
+
+// Warp-wide variant (all 32 lanes of one warp call it): each step reads 32
+// predecessor words at once, so the prefix is usually found after one L2
+// round trip instead of one per predecessor.  Same words and result as
+// lookback(); every lane returns the exclusive prefix.
+__device__ __forceinline__ uint32_t lookback_warp(unsigned long long* status, uint32_t stride, uint32_t tile,
+                                                  uint32_t agg, uint32_t epoch, uint32_t* flags) {
+    const uint32_t lane = lane_id();
+    const uint32_t ep = epoch & 0x3FFFFFFFu;
+    if (tile == 0) {
+        if (lane == 0) lb_store(status, lb_pack(epoch, 2u, agg));
+        return 0;
+    }
+    if (lane == 0) lb_store(status + (size_t)tile * stride, lb_pack(epoch, 1u, agg));
+    uint32_t prefix = 0;
+    int64_t base = (int64_t)tile - 1;  // window [base - 31, base], lane i reads base - i
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t j = base - (int64_t)lane;
+        uint32_t val = 0, fl = 2u;
+        bool ready = true;
+        if (j >= 0) {
+            const unsigned long long w = lb_load(status + (size_t)j * stride);
+            fl = (uint32_t)(w >> 32) & 3u;
+            ready = ((uint32_t)(w >> 34) == ep) && fl != 0u;
+            val = (uint32_t)w;
+        }
+        const uint32_t incl = __ballot_sync(0xFFFFFFFFu, ready && fl == 2u);
+        const uint32_t rdy = __ballot_sync(0xFFFFFFFFu, ready);
+        if (incl) {
+            const int k = __ffs(incl) - 1;  // nearest inclusive prefix in the window
+            const uint32_t need = k == 31 ? 0xFFFFFFFFu : ((1u << (k + 1)) - 1u);
+            if ((rdy & need) == need) {
+                prefix += __reduce_add_sync(0xFFFFFFFFu, (int)lane <= k ? val : 0u);
+                break;
+            }
+        } else if (rdy == 0xFFFFFFFFu) {  // 32 aggregates: take them and look further back
+            prefix += __reduce_add_sync(0xFFFFFFFFu, val);
+            base -= 32;
+            continue;
+        }
+        if (++spins > SPIN_LIMIT) {
+            if (lane == 0) atomicOr(flags, F_SPIN_TIMEOUT);
+            break;
+        }
+        __nanosleep(20);
+    }
+    if (lane == 0) lb_store(status + (size_t)tile * stride, lb_pack(epoch, 2u, prefix + agg));
+    return prefix;
+}
+
+// FP32 depth key of a node: z = ((R20 dx + R21 dy) + R22 dz), dx = fl(mu_x - C_x),
+// every operation single-rounded.  The near-plane cull and the depth order use it.
+__device__ __forceinline__ float depth_key(float4 m, float R6, float R7, float R8, float Cx, float Cy, float Cz) {
+    const float dx = __fsub_rn(m.x, Cx), dy = __fsub_rn(m.y, Cy), dz = __fsub_rn(m.z, Cz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
 }
 
 // The granularity test, single-rounded FP32 (no contraction): expand iff

@@ -15,11 +15,14 @@ struct Counters;
 
 // k_lod.cu
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
-                       const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s);
+                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
+                       cudaStream_t s);
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
-                      const FrameParams* fp, uint32_t* bitmap, Counters* ctr, int grid, cudaStream_t s);
-void launch_cut_compact(uint32_t* bitmap, uint32_t n_words, uint32_t* cut, uint32_t cap, uint32_t* n_cut_out,
-                        unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
+                      const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
+                      cudaStream_t s);
+void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,
+                        uint32_t cap, uint32_t* n_cut_out, unsigned long long* status,
+                        unsigned long long* status_front, Counters* ctr, const FrameParams* fp, int grid,
                         cudaStream_t s);
 uint32_t cut_compact_tiles(uint32_t n_words);
 uint32_t cut_compact_tile_words();
@@ -30,14 +33,16 @@ struct VisBuffers {
     uint32_t* depth;
     uint32_t* ntile;
     uint2* rect;
-    float4* recA;   // u v A B
-    float4* recB;   // C thr theta r
-    float2* recC;   // g b
+    float4* recA;   // u v A B   (rho = A dx^2 + B dx dy + C dy^2)
+    float4* recB;   // C thr theta half-height of the footprint box
+    float4* rgb;    // r g b 0
 };
 void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
                        const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
                        Counters* ctr, int grid, cudaStream_t s);
 uint32_t preprocess_tile();
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, uint32_t cap_vis, const FrameParams* fp,
+                  const Counters* ctr, float4* rgb, int grid, cudaStream_t s);
 void prepare_scene(float4* covB, uint32_t n, cudaStream_t s);
 void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s);
 
@@ -52,15 +57,15 @@ void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
 
 // k_emit.cu
 void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, float4* srecA, float4* srecB,
-                 float2* srecC, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
+                 float4* srecC, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
                  unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
 uint32_t emit_tile();
-void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint2* ranges, int grid,
-                   cudaStream_t s);
+void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
+                   int grid, cudaStream_t s);
 
 // k_blend.cu
 void launch_blend(uint32_t n_tiles, const uint2* ranges, const uint32_t* pair_rank, const float4* srecA,
-                  const float4* srecB, const float2* srecC, const FrameParams* fp, const float* lut, float* image,
+                  const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
 
 // vgr_sort_api.cu: enqueue a standalone pair sort on caller-provided scratch

@@ -100,7 +100,7 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     np.testing.assert_array_equal(dbg["vis_depth"], zk)
     # ---- records against the FP64 projection
     p = proj[idx]
-    A, B, C = dbg["vis_recA"], dbg["vis_recB"], dbg["vis_recC"]
+    A, B = dbg["vis_recA"], dbg["vis_recB"]
     H, W = ref["image"].shape[:2]
     for j, key, half in ((0, "u", W / 2.0), (1, "v", H / 2.0)):
         # u = fx x/z + cx: the FP32 error scales with the larger of the two terms
@@ -111,7 +111,9 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     cref = p["conic"]
     cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))[:, None]
     assert np.max(np.abs(con - cref) / cs) < 2e-3
-    rgb = np.stack([B[:, 3], C[:, 0], C[:, 1]], 1)
+    rank_of = np.empty(len(gv), np.int64)
+    rank_of[dbg["depth_order"]] = np.arange(len(gv))
+    rgb = dbg["rank_rgb"][rank_of, :3]
     assert np.max(np.abs(rgb - p["rgb"])) < 2e-5
     np.testing.assert_array_equal(B[:, 2], p["theta"].astype(np.float32))
     assert np.max(np.abs(B[:, 1] - p["thr"])) < 1e-5
