@@ -114,12 +114,13 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
     K3 = 3 * (int(sc["sh_degree"]) + 1) ** 2
     shb = 4 * ((K3 + 3) // 4 * 4)
     P0 = st.get("candidate_pairs", P)
+    F = st.get("front_count", V)
     return dict(
-        lod=16 * E + 4 * C + 4 * C + N / 8,          # node tests, parent ids, prev cut read, bitmap set
-        compact=N / 8 * 2 + 4 * C,                   # bitmap read + clear, cut ids written
-        preprocess=4 * C + 16 * C + 32 * V + 52 * V,  # ids, centre/R2 of the cut, covariance of visible, records out
-        depth_sort=4 * 2 * 8 * V + 4 * V,            # 4 passes x (key+value) read+write, histogram read
-        color=(4 + 4 + 16 + shb) * V + 16 * V,       # order, node, centre, SH; rgb out
+        lod=16 * E + 4 * C + 4 * C + 2 * N / 8,      # node tests, parent ids, prev cut read, two bitmaps set
+        compact=2 * (N / 8 * 2) + 4 * C + 4 * F,     # two bitmaps read + cleared, cut and in-front ids written
+        preprocess=(4 + 16 + 32 + 52) * F,           # ids, centre, covariance + opacity, records out
+        depth_sort=4 * 2 * 8 * F + 4 * F,            # 4 passes x (key+value) read+write, histogram read
+        color=4 * F + (4 + 16 + shb) * V + 16 * V,   # culled flags, node, centre, SH; rgb out
         emit=(4 + 4 + 8 + 32) * V + 32 * V + 8 * P0,  # order, count, rect, records in and out, slots
         tile_sort=tile_passes * 2 * 8 * P0,
         ranges=4 * P + 8 * (W // 16 + 1) * (H // 16 + 1),
@@ -144,7 +145,9 @@ def run_ours(args) -> dict:
     wl = WORKLOADS[args.config]
     cfg = scenegen.CONFIGS[wl["scene"]]
     t0 = time.time()
-    sc = scenegen.make_scene(wl["scene"])
+    sc = scenegen.make_scene(wl["scene"], n_leaves=args.leaves or None)
+    if args.leaves:
+        wl = dict(wl, label="%s (%d leaves)" % (wl["label"].replace("18M-leaves-", ""), args.leaves))
     t_gen = time.time() - t0
     t0 = time.time()
     h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF if args.storage == "half" else vgr.STORE_FP32)
@@ -227,7 +230,7 @@ def run_ours(args) -> dict:
 
     # ---- roofline of the dominant kernel
     mean = {k: float(np.mean([s[k] for s in stats])) for k in
-            ("cut_count", "visible_count", "pair_count", "nodes_evaluated", "candidate_pairs",
+            ("cut_count", "front_count", "visible_count", "pair_count", "nodes_evaluated", "candidate_pairs",
              "pixel_pair_evals")}
     n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
     tp = max(1, (int(math.ceil(math.log2(max(2, n_tiles)))) + 7) // 8)
@@ -330,6 +333,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "half"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--leaves", type=int, default=0, help="override the workload's leaf count (smaller profiling cases)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -117,6 +117,7 @@ enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEP
 
 typedef struct {
     uint32_t cut_count;       /* |C| */
+    uint32_t front_count;     /* cut nodes in front of the near plane */
     uint32_t visible_count;   /* |V|: cut Gaussians with at least one candidate tile */
     uint64_t pair_count;      /* P: (Gaussian, tile) pairs kept by the tile-level filter */
     uint64_t candidate_pairs; /* P0: candidate pairs examined by the tile-level filter */
@@ -137,20 +138,25 @@ typedef struct {
     vgr_frame_stats stats;
 } vgr_frame;
 
-/* Device pointers of the intermediate buffers of the last frame (testing). */
+/*
+ * Device pointers of the intermediate buffers of the last frame (testing).
+ * Per-Gaussian arrays are indexed like the in-front list (cut nodes in front
+ * of the near plane, ascending node id); entries culled later have
+ * vis_ntile = 0 and the depth key 0xFFFFFFFF.
+ */
 typedef struct {
-    uint32_t n_cut, n_visible;
+    uint32_t n_cut, n_front, n_visible;
     uint64_t n_pairs;
     uint32_t tiles_x, tiles_y;
     const uint32_t* cut;          /* [n_cut] ascending node ids */
-    const uint32_t* vis_node;     /* [n_visible] node id, in cut order */
-    const uint32_t* vis_depth;    /* [n_visible] FP32 depth key bits */
-    const uint32_t* vis_ntile;    /* [n_visible] candidate tiles (area of vis_rect) */
-    const uint32_t* vis_rect;     /* [2 n_visible] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
-    const float* vis_recA;        /* [4 n_visible] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
-    const float* vis_recB;        /* [4 n_visible] C thr theta h, thr = ln alpha* - ln theta, h = box half-height */
+    const uint32_t* vis_node;     /* [n_front] node id */
+    const uint32_t* vis_depth;    /* [n_front] FP32 depth key bits (0xFFFFFFFF if culled) */
+    const uint32_t* vis_ntile;    /* [n_front] candidate tiles (area of vis_rect), 0 if culled */
+    const uint32_t* vis_rect;     /* [2 n_front] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
+    const float* vis_recA;        /* [4 n_front] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
+    const float* vis_recB;        /* [4 n_front] C thr theta h, thr = ln alpha* - ln theta, h = box half-height */
     const float* rank_rgb;        /* [4 n_visible] r g b 0 in depth-rank order */
-    const uint32_t* depth_order;  /* [n_visible] visible index by depth rank */
+    const uint32_t* depth_order;  /* [n_front] in-front index by depth rank; the first n_visible are visible */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
     const uint32_t* pair_rank;    /* [n_pairs] depth rank of the Gaussian */
     const uint32_t* tile_range;   /* [2 tiles] start, end into the pair list */

@@ -120,7 +120,8 @@ class FrameResult:
         self.width, self.height = int(fr.width), int(fr.height)
         self.cut_count = int(fr.cut_count)
         s = fr.stats
-        self.stats = dict(cut_count=int(s.cut_count), visible_count=int(s.visible_count),
+        self.stats = dict(cut_count=int(s.cut_count), front_count=int(s.front_count),
+                          visible_count=int(s.visible_count),
                           pair_count=int(s.pair_count), candidate_pairs=int(s.candidate_pairs),
                           nodes_evaluated=int(s.nodes_evaluated), lod_from_scratch=int(s.lod_from_scratch),
                           replays=int(s.replays), kernels=int(s.kernels),
@@ -188,10 +189,12 @@ class View:
         return int(b.value)
 
     def debug(self) -> dict:
-        """Copies of the last frame's intermediate buffers (numpy)."""
+        """Copies of the last frame's intermediate buffers (numpy).  The
+        per-Gaussian arrays are returned for the visible Gaussians only, in
+        ascending node order, and depth_order indexes them."""
         d = _abi.DebugBuffers()
         _abi.check(_abi.load().vgr_view_debug(self.handle, ctypes.byref(d)))
-        nv, nc, npairs = int(d.n_visible), int(d.n_cut), int(d.n_pairs)
+        nf, nv, nc, npairs = int(d.n_front), int(d.n_visible), int(d.n_cut), int(d.n_pairs)
         T = int(d.tiles_x) * int(d.tiles_y)
 
         def u32(ptr, n):
@@ -200,11 +203,16 @@ class View:
         def f32(ptr, shape):
             return device_tensor(ptr, shape, "float32").cpu().numpy().copy()
 
-        return dict(n_cut=nc, n_visible=nv, n_pairs=npairs, tiles=(int(d.tiles_x), int(d.tiles_y)),
-                    cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nv), vis_depth=u32(d.vis_depth, nv),
-                    vis_ntile=u32(d.vis_ntile, nv), vis_rect=u32(d.vis_rect, 2 * nv).reshape(nv, 2),
-                    vis_recA=f32(d.vis_recA, (nv, 4)), vis_recB=f32(d.vis_recB, (nv, 4)),
-                    rank_rgb=f32(d.rank_rgb, (nv, 4)), depth_order=u32(d.depth_order, nv),
+        ntile = u32(d.vis_ntile, nf)
+        vis = ntile > 0
+        compact = np.cumsum(vis) - 1
+        order = u32(d.depth_order, nf)[:nv]
+        assert vis[order].all(), "the first n_visible depth ranks must be visible entries"
+        return dict(n_cut=nc, n_front=nf, n_visible=nv, n_pairs=npairs, tiles=(int(d.tiles_x), int(d.tiles_y)),
+                    cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nf)[vis], vis_depth=u32(d.vis_depth, nf)[vis],
+                    vis_ntile=ntile[vis], vis_rect=u32(d.vis_rect, 2 * nf).reshape(nf, 2)[vis],
+                    vis_recA=f32(d.vis_recA, (nf, 4))[vis], vis_recB=f32(d.vis_recB, (nf, 4))[vis],
+                    rank_rgb=f32(d.rank_rgb, (nv, 4)), depth_order=compact[order].astype(np.uint32),
                     pair_tile=u32(d.pair_tile, npairs), pair_rank=u32(d.pair_rank, npairs),
                     tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
 

@@ -36,7 +36,7 @@ class ViewOpts(ctypes.Structure):
 
 
 class FrameStats(ctypes.Structure):
-    _fields_ = [("cut_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64),
+    _fields_ = [("cut_count", c_u32), ("front_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64),
                 ("candidate_pairs", c_u64), ("nodes_evaluated", c_u64), ("lod_from_scratch", c_u32),
                 ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64), ("stage_ms", c_f32 * 9),
                 ("frame_ms", c_f32)]
@@ -48,7 +48,7 @@ class Frame(ctypes.Structure):
 
 
 class DebugBuffers(ctypes.Structure):
-    _fields_ = [("n_cut", c_u32), ("n_visible", c_u32), ("n_pairs", c_u64), ("tiles_x", c_u32),
+    _fields_ = [("n_cut", c_u32), ("n_front", c_u32), ("n_visible", c_u32), ("n_pairs", c_u64), ("tiles_x", c_u32),
                 ("tiles_y", c_u32), ("cut", c_vp), ("vis_node", c_vp), ("vis_depth", c_vp),
                 ("vis_ntile", c_vp), ("vis_rect", c_vp), ("vis_recA", c_vp), ("vis_recB", c_vp),
                 ("rank_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_rank", c_vp),

@@ -26,25 +26,66 @@
 
 namespace vgr {
 
-// A cut node joins the cut bitmap, and the in-front bitmap when its FP32
-// depth key is beyond the near plane (the same key and test as preprocess).
+// A cut node joins the cut bitmap, and the potentially-visible bitmap when
+// its FP32 depth key is beyond the near plane (the same key and test as
+// preprocess) and its footprint can reach the image.  The footprint test is
+// a bound on the one preprocess applies: preprocess's box half-width is
+//   bx = r sqrt(S'00) * 1.0001 + 1e-3,  r^2 = 2 (ln theta - ln alpha*) + 2 slack
+//   <= 3.33 (slack included),  S'00 = m0^T S m0 + 0.3,  m0 = fx/z (R0 - tx R2),
+// and |m0|^2 = (fx/z)^2 (1 + tx^2) <= (fx/z)^2 (1 + limx^2) while
+// m0^T S m0 <= lambda_max(S) |m0|^2 <= L |m0|^2, L the largest absolute row
+// sum of S (Gershgorin, stored per node at load); so with
+//   Bx = 3.34 sqrt(L (fx/z)^2 (1 + limx^2) + 0.3) + 0.01
+// a Gaussian with u + Bx < 0.5 or u - Bx > 16 tiles_x - 0.5 (or likewise in
+// v) has no candidate tile in preprocess and can be left out here.  The
+// canonical mode's 3-sigma box is bounded the same way.
 struct CutOut {
     uint32_t* cut_bm;
     uint32_t* front_bm;
-    float R6, R7, R8, Cx, Cy, Cz, z_near;
+    const float* lmax;
+    float R0, R1, R2, R3, R4, R5, R6, R7, R8, Cx, Cy, Cz, z_near;
+    float fx, fy, cx, cy, kx, ky, umax, vmax;
+    bool canonical;
     __device__ __forceinline__ void add(uint32_t n, float4 c) const {
         bitmap_set(cut_bm, n);
-        if (depth_key(c, R6, R7, R8, Cx, Cy, Cz) > z_near) bitmap_set(front_bm, n);
+        const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
+        const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
+        if (!(z > z_near)) return;
+        const float x = fmaf(R0, dx, fmaf(R1, dy, R2 * dz));
+        const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
+        const float iz = 1.0f / z;
+        const float u = fmaf(fx, x * iz, cx), v = fmaf(fy, y * iz, cy);
+        const float t = lmax[n] * iz * iz;
+        float bx, by;
+        if (!canonical) {
+            bx = 3.34f * sqrtf(fmaf(t, kx, 0.3f)) + 0.01f;
+            by = 3.34f * sqrtf(fmaf(t, ky, 0.3f)) + 0.01f;
+        } else {
+            bx = by = 3.01f * sqrtf(fmaf(t, kx + ky, 0.6f)) + 1.01f;
+        }
+        const float su = 1e-5f * fabsf(u) + 1e-2f, sv = 1e-5f * fabsf(v) + 1e-2f;  // FP32 slack
+        if (u + bx < 0.5f - su || u - bx > umax + su || v + by < 0.5f - sv || v - by > vmax + sv) return;
+        bitmap_set(front_bm, n);
     }
 };
 
-__device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, uint32_t* cut_bm, uint32_t* front_bm) {
+__device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const SceneDev& sc, uint32_t* cut_bm,
+                                               uint32_t* front_bm) {
     CutOut o;
     o.cut_bm = cut_bm;
     o.front_bm = front_bm;
+    o.lmax = sc.lmax;
+    o.R0 = fp->R[0]; o.R1 = fp->R[1]; o.R2 = fp->R[2];
+    o.R3 = fp->R[3]; o.R4 = fp->R[4]; o.R5 = fp->R[5];
     o.R6 = fp->R[6]; o.R7 = fp->R[7]; o.R8 = fp->R[8];
     o.Cx = fp->pos[0]; o.Cy = fp->pos[1]; o.Cz = fp->pos[2];
     o.z_near = fp->z_near;
+    o.fx = fp->fx; o.fy = fp->fy; o.cx = fp->cx; o.cy = fp->cy;
+    o.kx = fp->fx * fp->fx * (1.0f + fp->limx * fp->limx);
+    o.ky = fp->fy * fp->fy * (1.0f + fp->limy * fp->limy);
+    o.umax = (float)(TILE * fp->tiles_x) - 0.5f;
+    o.vmax = (float)(TILE * fp->tiles_y) - 0.5f;
+    o.canonical = fp->filter == VGR_FILTER_CANONICAL;
     return o;
 }
 
@@ -56,7 +97,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     const uint32_t n_prev = min(*n_prev_p, cap_prev);
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const uint32_t budget = fp->lod_budget, max_depth = fp->max_depth;
-    const CutOut out = make_cut_out(fp, bitmap, front);
+    const CutOut out = make_cut_out(fp, sc, bitmap, front);
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_prev; i += stride) {
@@ -130,7 +171,7 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
     const uint32_t n_in = level == 0 ? 1u : min(ctr->frontier_n[level], cap);
     uint32_t* n_out = &ctr->frontier_n[level + 1];
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
-    const CutOut out = make_cut_out(fp, bitmap, front);
+    const CutOut out = make_cut_out(fp, sc, bitmap, front);
     const uint32_t lane = lane_id();
     const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;

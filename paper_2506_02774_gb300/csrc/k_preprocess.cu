@@ -3,9 +3,10 @@
 // (Sec. 4.2, Eq. 4: alpha >= alpha* <=> rho >= ln alpha* - ln theta).
 //
 // One thread per cut node in front of the near plane (the LoD stage lists
-// them), tiles of 256 entries handed out by ticket and compacted in order by a
-// decoupled look-back scan, so visible Gaussians keep ascending node-id order
-// (the depth sort is stable, so equal depths stay ordered by node id).
+// them, in ascending node id), dense and barrier-free: every entry's record
+// is written at its own index, and a culled entry gets the depth key
+// 0xFFFFFFFF.  The stable depth sort then puts the visible Gaussians first,
+// ordered by (depth key, node id), with no compaction pass at all.
 //
 // Per node: p = R (mu - C); depth key = FP32 bits of
 // ((R20 dx + R21 dy) + R22 dz) with single-rounded operations; culled when
@@ -120,17 +121,11 @@ struct Store<VGR_STORE_HALF> {
 };
 
 template <int STORE>
-__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, const uint32_t* __restrict__ cut,
-                                                               const uint32_t* __restrict__ n_cut_p, uint32_t cap_cut,
-                                                               const FrameParams* __restrict__ fp, VisBuffers vis,
-                                                               uint32_t cap_vis,
-                                                               unsigned long long* __restrict__ status,
-                                                               Counters* __restrict__ ctr) {
-    __shared__ uint32_t s_scan[9];
-    __shared__ uint32_t s_tile, s_prefix;
-    const uint32_t n_cut = min(*n_cut_p, cap_cut);
-    const uint32_t ntiles = (n_cut + PRE_THREADS - 1) / PRE_THREADS;
-
+__global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
+                                                            const uint32_t* __restrict__ n_front_p, uint32_t cap,
+                                                            const FrameParams* __restrict__ fp, VisBuffers vis,
+                                                            Counters* __restrict__ ctr) {
+    const uint32_t n_front = min(*n_front_p, cap);
     const float R0 = fp->R[0], R1 = fp->R[1], R2 = fp->R[2], R3 = fp->R[3], R4 = fp->R[4], R5 = fp->R[5];
     const float R6 = fp->R[6], R7 = fp->R[7], R8 = fp->R[8];
     const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
@@ -138,26 +133,21 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
     const float limx = fp->limx, limy = fp->limy, Wf = fp->width_f, Hf = fp->height_f;
     const int TW = (int)fp->tiles_x, TH = (int)fp->tiles_y;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
-    const uint32_t epoch = fp->epoch;
-
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_PRE], 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t i = tile * PRE_THREADS + threadIdx.x;
-
-        bool v = i < n_cut;
-        uint32_t node = 0, zbits = 0;
+    uint32_t n_visible = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // uniform trip count per warp so the visible count can use a ballot
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n_front; base += stride) {
+        const uint32_t i = base + lane_id();
+        bool v = i < n_front;
+        uint32_t node = 0, zbits = 0xFFFFFFFFu;
         float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f;
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
-            node = cut[i];
+            node = front[i];
             const float4 m = sc.cr[node];
             const float dx = __fsub_rn(m.x, Cx), dy = __fsub_rn(m.y, Cy), dz = __fsub_rn(m.z, Cz);
             const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
-            zbits = __float_as_uint(z);
-            v = z > z_near;
+            v = z > z_near;  // always true for the in-front list; kept as the definition
             float S[6], lnth = 0.f;
             if (v) {
                 Store<STORE>::cov(sc, node, S, theta, lnth);
@@ -221,48 +211,34 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
                     half_h = by;
                 }
             }
+            if (v) zbits = __float_as_uint(z);
         }
-        // candidate tiles; the tile-level test itself runs in the emission
-        const uint32_t area = v ? (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1) : 0u;
-
-        uint32_t total;
-        const uint32_t rank = block_excl_scan<PRE_THREADS / 32>(v ? 1u : 0u, s_scan, &total);
-        if (threadIdx.x < 32) {
-            const uint32_t pre = lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
-            if (threadIdx.x == 0) s_prefix = pre;
+        n_visible += __popc(__ballot_sync(0xFFFFFFFFu, v));
+        if (i < n_front) {
+            vis.node[i] = node;
+            vis.depth[i] = zbits;  // culled: all ones, sorted behind every visible key
+            vis.ntile[i] = v ? (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1) : 0u;
+            vis.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+            vis.recA[i] = make_float4(u, vv, -0.5f * ca, -cb);
+            vis.recB[i] = make_float4(-0.5f * cc, thr, theta, half_h);
         }
-        __syncthreads();
-        if (v) {
-            const uint32_t o = s_prefix + rank;
-            if (o < cap_vis) {
-                vis.node[o] = node;
-                vis.depth[o] = zbits;
-                vis.ntile[o] = area;
-                vis.rect[o] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
-                vis.recA[o] = make_float4(u, vv, -0.5f * ca, -cb);
-                vis.recB[o] = make_float4(-0.5f * cc, thr, theta, half_h);
-            }
-        }
-        if (tile == ntiles - 1 && threadIdx.x == 0) {
-            const uint32_t nv = s_prefix + total;
-            ctr->n_vis = nv;
-            if (nv > cap_vis) atomicOr(&ctr->flags, F_OVF_VIS);
-        }
-        __syncthreads();
     }
+    if (lane_id() == 0 && n_visible) atomicAdd(&ctr->n_vis, n_visible);
 }
 
 // Colour of the visible Gaussians (dense, no barriers), in visible order,
 // i.e. ascending node id, so consecutive threads read neighbouring SH rows:
 // rgb = sum_lm c_lm Y_lm(d) + 0.5, clamped at 0, d = (mu - C)/|mu - C|.
 template <int DEG, int STORE>
-__global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __restrict__ vis_node, uint32_t cap_vis,
+__global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __restrict__ vis_node,
+                                               const uint32_t* __restrict__ vis_ntile, uint32_t cap,
                                                const FrameParams* __restrict__ fp, const Counters* __restrict__ ctr,
                                                float4* __restrict__ rgb_out) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const uint32_t n = min(ctr->n_vis, cap_vis);
+    const uint32_t n = min(ctr->n_front, cap);
     const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        if (vis_ntile[r] == 0u) continue;  // culled
         const uint32_t node = vis_node[r];
         float shc[((3 * K + 7) / 8) * 8];
         Store<STORE>::template sh<K>(sc, node, shc);
@@ -299,22 +275,21 @@ void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
     k_prepare<<<1024, 256, 0, s>>>(covB, n, 1);
 }
 
-void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
-                       const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
-                       Counters* ctr, int grid, cudaStream_t s) {
+void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
+                       const FrameParams* fp, VisBuffers vis, Counters* ctr, int grid, cudaStream_t s) {
     if (sc.storage == VGR_STORE_HALF)
-        k_preprocess<VGR_STORE_HALF><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
+        k_preprocess<VGR_STORE_HALF><<<grid, PRE_THREADS, 0, s>>>(sc, front, n_front, cap, fp, vis, ctr);
     else
-        k_preprocess<VGR_STORE_FP32><<<grid, PRE_THREADS, 0, s>>>(sc, cut, n_cut, cap_cut, fp, vis, cap_vis, status, ctr);
+        k_preprocess<VGR_STORE_FP32><<<grid, PRE_THREADS, 0, s>>>(sc, front, n_front, cap, fp, vis, ctr);
 }
 
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, uint32_t cap_vis, const FrameParams* fp,
-                  const Counters* ctr, float4* rgb, int grid, cudaStream_t s) {
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, uint32_t cap,
+                  const FrameParams* fp, const Counters* ctr, float4* rgb, int grid, cudaStream_t s) {
     const bool half = sc.storage == VGR_STORE_HALF;
 #define VGR_COLOR_CASE(D)                                                                                   \
     case D:                                                                                                 \
-        if (half) k_color<D, VGR_STORE_HALF><<<grid, 256, 0, s>>>(sc, vis_node, cap_vis, fp, ctr, rgb); \
-        else k_color<D, VGR_STORE_FP32><<<grid, 256, 0, s>>>(sc, vis_node, cap_vis, fp, ctr, rgb);      \
+        if (half) k_color<D, VGR_STORE_HALF><<<grid, 256, 0, s>>>(sc, vis_node, vis_ntile, cap, fp, ctr, rgb); \
+        else k_color<D, VGR_STORE_FP32><<<grid, 256, 0, s>>>(sc, vis_node, vis_ntile, cap, fp, ctr, rgb);      \
         break;
     switch (sc.sh_degree) {
         VGR_COLOR_CASE(0)

@@ -76,6 +76,7 @@ struct vgr_hierarchy {
     uint32_t* child = nullptr;
     float4* covA = nullptr;
     float4* covB = nullptr;
+    float* lmax = nullptr;
     void* sh = nullptr;
     uint32_t n_nodes = 0, max_depth = 0;
     uint64_t bytes = 0;
@@ -90,7 +91,7 @@ struct vgr_view {
     bool own_stream = false;
     int grid_wide = 0, grid_scan = 0;
     // capacities
-    uint32_t cap_cut = 0, cap_vis = 0;
+    uint32_t cap_cut = 0, cap_vis = 0;  // visible arrays are indexed like the in-front list: cap_vis = cap_cut
     uint64_t cap_pairs = 0;
     uint32_t cap_pixels = 0, cap_tiles = 0;
     // device buffers
@@ -112,7 +113,7 @@ struct vgr_view {
     float* image = nullptr;
     float* lut = nullptr;
     unsigned long long* status = nullptr;
-    size_t st_compact = 0, st_front = 0, st_pre = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
+    size_t st_compact = 0, st_front = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
            st_tile_stride = 0, st_words = 0;
     Counters* ctr = nullptr;
     ViewState* vstate = nullptr;
@@ -130,7 +131,7 @@ struct vgr_view {
     // last frame
     uint32_t last_w = 0, last_h = 0, last_tw = 0, last_th = 0;
     int last_tile_buf = 0;
-    uint32_t last_n_cut = 0, last_n_vis = 0;
+    uint32_t last_n_cut = 0, last_n_vis = 0, last_n_front = 0;
     uint64_t last_n_pairs = 0;
     uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
 };
@@ -223,7 +224,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     const bool half = d->storage == VGR_STORE_HALF;
     const uint32_t stride = half ? (K3 + 7u) / 8u * 8u : (K3 + 3u) / 4u * 4u;
     vgr_status st = VGR_OK;
-    auto cleanup = [&]() { dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
+    auto cleanup = [&]() { dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
                            if (h->sh) cudaFree(h->sh); delete h; };
 #define VGR_TRY(x)                 \
     do {                           \
@@ -238,6 +239,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     VGR_TRY(dalloc(&h->child, N, &h->bytes));
     VGR_TRY(dalloc(&h->covA, N, &h->bytes));
     VGR_TRY(dalloc(&h->covB, N, &h->bytes));
+    VGR_TRY(dalloc(&h->lmax, N, &h->bytes));
     {
         const size_t shb = (size_t)N * stride * (half ? 2 : 4);
         cudaError_t e = cudaMalloc(&h->sh, shb);
@@ -272,6 +274,20 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
         }
         if (ce == cudaSuccess) ce = cudaMemcpy(h->child + b, u, cnt * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(h->parent + b, d->parent + b, cnt * 4, cudaMemcpyHostToDevice);
+        {
+            // largest absolute row sum of the covariance >= its largest eigenvalue;
+            // widened for the rounding of the stored (FP32 or BF16) covariance
+            float* lm = (float*)pin;
+            const double widen = half ? 1.0 + 1.0 / 64.0 : 1.0 + 1e-5;
+            for (uint32_t i = 0; i < cnt; ++i) {
+                const float* c = d->cov6 + 6 * (size_t)(b + i);
+                const double r0 = fabs(c[0]) + fabs(c[1]) + fabs(c[2]);
+                const double r1 = fabs(c[1]) + fabs(c[3]) + fabs(c[4]);
+                const double r2 = fabs(c[2]) + fabs(c[4]) + fabs(c[5]);
+                lm[i] = (float)(std::max(r0, std::max(r1, r2)) * widen);
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpy(h->lmax + b, lm, cnt * 4, cudaMemcpyHostToDevice);
+        }
         if (!half) {
             for (uint32_t i = 0; i < cnt; ++i) {
                 const float* c = d->cov6 + 6 * (size_t)(b + i);
@@ -321,6 +337,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     h->dev.child = h->child;
     h->dev.covA = h->covA;
     h->dev.covB = h->covB;
+    h->dev.lmax = h->lmax;
     h->dev.sh = h->sh;
     h->dev.n_nodes = N;
     h->dev.sh_degree = d->sh_degree;
@@ -333,7 +350,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
 vgr_status vgr_free_hierarchy(vgr_hierarchy* h) {
     if (!h) return fail(VGR_E_INVALID, "null hierarchy");
     cudaSetDevice(h->device);
-    dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
+    dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
     if (h->sh) cudaFree(h->sh);
     delete h;
     return VGR_OK;
@@ -423,8 +440,7 @@ vgr_status alloc_status(vgr_view* v) {
     const uint32_t RT = radix_tile();
     v->st_compact = 0;
     v->st_front = v->st_compact + cut_compact_tiles(v->n_words) + 1;
-    v->st_pre = v->st_front + cut_compact_tiles(v->n_words) + 1;
-    v->st_emit = v->st_pre + ceil_div(v->cap_cut, preprocess_tile()) + 1;
+    v->st_emit = v->st_front + cut_compact_tiles(v->n_words) + 1;
     v->st_depth = v->st_emit + ceil_div(v->cap_vis, emit_tile()) + 1;
     v->st_depth_stride = (size_t)(ceil_div(v->cap_vis, RT) + 1) * 256;
     v->st_tile = v->st_depth + 4 * v->st_depth_stride;
@@ -511,8 +527,8 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     v->grid_scan = h->num_sms * 4;
     const uint32_t cap_cut = (uint32_t)std::min<uint64_t>(N, v->opts.cut_capacity ? v->opts.cut_capacity
                                                                                   : std::max<uint64_t>(1u << 20, N / 4));
-    const uint32_t cap_vis = std::min<uint32_t>(cap_cut, std::max<uint32_t>(1u << 19, cap_cut / 2));
-    const uint64_t cap_pairs = v->opts.pair_capacity ? v->opts.pair_capacity : (uint64_t)4 * cap_vis;
+    const uint32_t cap_vis = cap_cut;
+    const uint64_t cap_pairs = v->opts.pair_capacity ? v->opts.pair_capacity : (uint64_t)2 * cap_vis;
     VGR_VTRY(alloc_cut(v, cap_cut));
     VGR_VTRY(alloc_vis(v, cap_vis));
     VGR_VTRY(alloc_pairs(v, cap_pairs));
@@ -611,21 +627,21 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
                        &v->vstate->n_cut[cur], v->status + v->st_compact, v->status + v->st_front, v->ctr, v->fp_dev,
                        v->grid_scan, s);
     mark(VGR_STAGE_PREPROCESS);
-    launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->cap_vis,
-                      v->status + v->st_pre, v->ctr, v->grid_scan, s);
+    launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, v->grid_wide, s);
     mark(VGR_STAGE_DEPTH_SORT);
-    launch_radix_hist(v->vis.depth, &v->ctr->n_vis, nullptr, v->cap_vis, 4, &v->ctr->depth_hist[0][0],
+    // every in-front entry is sorted; culled ones carry the key 0xFFFFFFFF and land last
+    launch_radix_hist(v->vis.depth, &v->ctr->n_front, nullptr, v->cap_vis, 4, &v->ctr->depth_hist[0][0],
                       v->grid_scan, s);
     for (int p = 0; p < 4; ++p) {
         const uint32_t* kin = p == 0 ? v->vis.depth : v->sortK[(p + 1) & 1];
         const uint32_t* vin = p == 0 ? nullptr : v->sortV[(p + 1) & 1];
-        launch_radix_pass(kin, vin, v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_vis, nullptr, v->cap_vis, 8 * p,
+        launch_radix_pass(kin, vin, v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_front, nullptr, v->cap_vis, 8 * p,
                           v->ctr->depth_hist[p], v->status + v->st_depth + p * v->st_depth_stride,
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
     mark(VGR_STAGE_COLOR);
-    launch_color(sc, v->vis.node, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, v->grid_wide, s);
+    launch_color(sc, v->vis.node, v->vis.ntile, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, v->grid_wide, s);
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->srecA, v->srecB, v->srecC, v->pairK[0], v->pairV[0], v->cap_pairs,
@@ -717,14 +733,9 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
         if (flags & F_LOD_FALLBACK) return fail(VGR_E_TIMEOUT, "top-down cut exceeded the tree depth");
         if (flags & F_OVF_CUT) {
             const uint32_t nc = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)n_cut + n_cut / 4 + 1024);
-            if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
+            if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_vis(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK)
+                return s;
             scratch = true;  // the previous cut lived in the old buffers
-            ++replays;
-            continue;
-        }
-        if (flags & F_OVF_VIS) {
-            const uint32_t nv = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)ch->n_vis + ch->n_vis / 4 + 1024);
-            if ((s = alloc_vis(v, nv)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
             ++replays;
             continue;
         }
@@ -745,6 +756,7 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
     v->last_w = W; v->last_h = H; v->last_tw = TW; v->last_th = TH;
     v->last_n_cut = v->vstate_host->n_cut[cur];
     v->last_n_vis = ch->n_vis;
+    v->last_n_front = ch->n_front;
     v->last_n_pairs = ch->n_pairs;
     if (host_rgb) {
         VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
@@ -760,6 +772,7 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
         out->height = H;
         vgr_frame_stats& st = out->stats;
         st.cut_count = v->last_n_cut;
+        st.front_count = ch->n_front;
         st.visible_count = ch->n_vis;
         st.pair_count = ch->n_pairs;
         st.candidate_pairs = ch->n_cand;
@@ -795,6 +808,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     memset(o, 0, sizeof(*o));
     o->n_cut = v->last_n_cut;
     o->n_visible = v->last_n_vis;
+    o->n_front = v->last_n_front;
     o->n_pairs = v->last_n_pairs;
     o->tiles_x = v->last_tw;
     o->tiles_y = v->last_th;

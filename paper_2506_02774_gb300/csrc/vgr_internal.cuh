@@ -88,6 +88,7 @@ struct SceneDev {
     const uint32_t* child;     // first_child | n_child << 28
     const float4* covA;        // xx xy xz yy
     const float4* covB;        // yz zz opacity ln(opacity)
+    const float* lmax;         // upper bound of the covariance's largest eigenvalue (Gershgorin)
     const void* sh;            // FP32 or FP16, sh_stride elements per node
     uint32_t n_nodes;
     uint32_t sh_degree;

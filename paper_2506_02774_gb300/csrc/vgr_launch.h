@@ -37,12 +37,11 @@ struct VisBuffers {
     float4* recB;   // C thr theta half-height of the footprint box
     float4* rgb;    // r g b 0
 };
-void launch_preprocess(const SceneDev& sc, const uint32_t* cut, const uint32_t* n_cut, uint32_t cap_cut,
-                       const FrameParams* fp, VisBuffers vis, uint32_t cap_vis, unsigned long long* status,
-                       Counters* ctr, int grid, cudaStream_t s);
+void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
+                       const FrameParams* fp, VisBuffers vis, Counters* ctr, int grid, cudaStream_t s);
 uint32_t preprocess_tile();
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, uint32_t cap_vis, const FrameParams* fp,
-                  const Counters* ctr, float4* rgb, int grid, cudaStream_t s);
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, uint32_t cap,
+                  const FrameParams* fp, const Counters* ctr, float4* rgb, int grid, cudaStream_t s);
 void prepare_scene(float4* covB, uint32_t n, cudaStream_t s);
 void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s);
 
