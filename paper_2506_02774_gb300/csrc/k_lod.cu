@@ -61,7 +61,8 @@ struct CutOut {
             bx = 3.34f * sqrtf(fmaf(t, kx, 0.3f)) + 0.01f;
             by = 3.34f * sqrtf(fmaf(t, ky, 0.3f)) + 0.01f;
         } else {
-            bx = by = 3.01f * sqrtf(fmaf(t, kx + ky, 0.6f)) + 1.01f;
+            // canonical: ceil(3 sqrt(lam)), lam <= S'00 + S'11 + 0.32 (its sqrt(max(0.1, .)) floor)
+            bx = by = 3.01f * sqrtf(fmaf(t, kx + ky, 1.0f)) + 1.01f;
         }
         const float su = 1e-5f * fabsf(u) + 1e-2f, sv = 1e-5f * fabsf(v) + 1e-2f;  // FP32 slack
         if (u + bx < 0.5f - su || u - bx > umax + su || v + by < 0.5f - sv || v - by > vmax + sv) return;

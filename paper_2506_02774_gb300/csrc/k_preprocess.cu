@@ -125,6 +125,9 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
                                                             const uint32_t* __restrict__ n_front_p, uint32_t cap,
                                                             const FrameParams* __restrict__ fp, VisBuffers vis,
                                                             Counters* __restrict__ ctr) {
+    __shared__ uint32_t s_hist[4][256];  // digit histograms of the depth keys (the sort's passes)
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+    __syncthreads();
     const uint32_t n_front = min(*n_front_p, cap);
     const float R0 = fp->R[0], R1 = fp->R[1], R2 = fp->R[2], R3 = fp->R[3], R4 = fp->R[4], R5 = fp->R[5];
     const float R6 = fp->R[6], R7 = fp->R[7], R8 = fp->R[8];
@@ -214,6 +217,12 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
             if (v) zbits = __float_as_uint(z);
         }
         n_visible += __popc(__ballot_sync(0xFFFFFFFFu, v));
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t dd = i < n_front ? ((zbits >> (8 * p)) & 255u) : 256u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dd);
+            if (dd < 256u && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[p][dd], (uint32_t)__popc(peers));
+        }
         if (i < n_front) {
             vis.node[i] = node;
             vis.depth[i] = zbits;  // culled: all ones, sorted behind every visible key
@@ -224,6 +233,11 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
         }
     }
     if (lane_id() == 0 && n_visible) atomicAdd(&ctr->n_vis, n_visible);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        const uint32_t c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&ctr->depth_hist[0][0] + i, c);
+    }
 }
 
 // Colour of the visible Gaussians (dense, no barriers), in visible order,

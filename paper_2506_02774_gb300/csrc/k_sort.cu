@@ -53,7 +53,17 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 }
 
 // One digit pass.  n comes from n32 (if non-null) or n64, clamped to cap.
-__global__ void __launch_bounds__(RS_THREADS) k_radix_pass(const uint32_t* __restrict__ keys_in,
+// Per tile of RS_TILE keys (warp w owns a contiguous run of 32 * RS_ITEMS):
+//  1. each warp ranks its keys: peers with the same digit come from
+//     match_any; the run leader's shared atomicAdd on the warp's digit
+//     counter returns the count of earlier keys, shuffled to the peers;
+//  2. the tile's digit counts are published to the look-back words at once,
+//     so later tiles rarely wait for this one;
+//  3. keys and values are placed digit-sorted in shared memory;
+//  4. the look-back over earlier tiles gives each digit its global start;
+//  5. every thread writes consecutive staged elements, so each digit's run
+//     is stored contiguously (coalesced).
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
                                                            uint32_t* __restrict__ vals_out,
@@ -64,9 +74,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_pass(const uint32_t* __res
                                                            uint32_t* __restrict__ ticket,
                                                            const FrameParams* __restrict__ fp,
                                                            Counters* __restrict__ ctr) {
-    __shared__ uint32_t s_wh[RS_WARPS][RS_BINS];  // per-warp counts, then per-warp offsets
-    __shared__ uint32_t s_gbase[RS_BINS];         // global start of each digit
-    __shared__ uint32_t s_off[RS_BINS];           // start of this tile's run of each digit
+    __shared__ uint32_t s_wc[RS_WARPS][RS_BINS];  // per-warp digit counts, then per-warp run offsets
+    __shared__ uint32_t s_gbase[RS_BINS];         // global start of each digit (all tiles)
+    __shared__ uint32_t s_lstart[RS_BINS];        // start of each digit's run in the staged tile
+    __shared__ uint32_t s_gofs[RS_BINS];          // global index minus staged index, per digit
+    __shared__ uint32_t s_key[RS_TILE];
+    __shared__ uint32_t s_val[RS_TILE];
+    __shared__ uint32_t s_scan[RS_WARPS + 1];
     __shared__ uint32_t s_tile;
     uint64_t n64v = n32 ? (uint64_t)*n32 : (uint64_t)*n64;
     if (n64v > cap) n64v = cap;
@@ -74,65 +88,96 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_pass(const uint32_t* __res
     const uint32_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const uint32_t epoch = fp->epoch;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-
-    // exclusive scan of the digit totals (thread t owns digit t)
     {
-        const uint32_t c = hist[threadIdx.x];
         uint32_t total;
-        __shared__ uint32_t s_scan[RS_WARPS + 1];
-        s_gbase[threadIdx.x] = block_excl_scan<RS_WARPS>(c, s_scan, &total);
+        s_gbase[threadIdx.x] = block_excl_scan<RS_WARPS>(hist[threadIdx.x], s_scan, &total);
     }
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-        for (int w = 0; w < RS_WARPS; ++w) s_wh[w][threadIdx.x] = 0u;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) s_wc[w][threadIdx.x] = 0u;
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) break;
-
-        uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
         const uint32_t base = tile * RS_TILE + warp * (32 * RS_ITEMS) + lane;
+        uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
-            const bool valid = idx < n;
-            key[it] = valid ? keys_in[idx] : 0xFFFFFFFFu;
-            val[it] = valid ? (vals_in ? vals_in[idx] : idx) : 0u;
+            key[it] = idx < n ? keys_in[idx] : 0u;
+            val[it] = idx < n ? (vals_in ? vals_in[idx] : idx) : 0u;
         }
+        // 1. ranks within the warp, in (item, lane) = input order
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
-            const bool valid = idx < n;
-            const uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;
+            const uint32_t d = idx < n ? ((key[it] >> shift) & 255u) : 256u;
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-            uint32_t r = 0;
-            if (valid) r = s_wh[warp][d] + __popc(peers & lanemask_lt());
-            __syncwarp();
-            if (valid && lane == (uint32_t)(__ffs(peers) - 1)) s_wh[warp][d] += __popc(peers);
-            __syncwarp();
-            rank[it] = r;
+            const int leader = __ffs(peers) - 1;
+            uint32_t before = 0;
+            if (d < 256u && (int)lane == leader) before = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+            before = __shfl_sync(0xFFFFFFFFu, before, leader);
+            rank[it] = before + __popc(peers & lanemask_lt());
         }
         __syncthreads();
-        // digit t: offsets of each warp's run and the tile total
+        // 2. digit d (thread d): per-warp run offsets, tile total, early publish
+        const uint32_t d = threadIdx.x;
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            const uint32_t c = s_wh[w][threadIdx.x];
-            s_wh[w][threadIdx.x] = run;
+            const uint32_t c = s_wc[w][d];
+            s_wc[w][d] = run;
             run += c;
         }
-        const uint32_t prefix = lookback(status + (size_t)threadIdx.x, RS_BINS, tile, run, epoch, &ctr->flags);
-        s_off[threadIdx.x] = s_gbase[threadIdx.x] + prefix;
+        unsigned long long* my = status + (size_t)tile * RS_BINS + d;
+        if (tile == 0) lb_store(my, lb_pack(epoch, 2u, run));
+        else lb_store(my, lb_pack(epoch, 1u, run));
+        {
+            uint32_t total;
+            s_lstart[d] = block_excl_scan<RS_WARPS>(run, s_scan, &total);
+        }
         __syncthreads();
+        // 3. stage digit-sorted
 #pragma unroll
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
             if (idx < n) {
-                const uint32_t d = (key[it] >> shift) & 255u;
-                const uint32_t pos = s_off[d] + s_wh[warp][d] + rank[it];
-                if (pos < n) {
-                    keys_out[pos] = key[it];
-                    vals_out[pos] = val[it];
+                const uint32_t dd = (key[it] >> shift) & 255u;
+                const uint32_t pos = s_lstart[dd] + s_wc[warp][dd] + rank[it];
+                s_key[pos] = key[it];
+                s_val[pos] = val[it];
+            }
+        }
+        // 4. look-back for digit d over earlier tiles (aggregate already published)
+        uint32_t prefix = 0;
+        if (tile > 0) {
+            const uint32_t ep = epoch & 0x3FFFFFFFu;
+            int64_t j = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const unsigned long long w = lb_load(status + (size_t)j * RS_BINS + d);
+                const uint32_t wep = (uint32_t)(w >> 34), fl = (uint32_t)(w >> 32) & 3u;
+                if (wep != ep || fl == 0u) {
+                    if (++spins > SPIN_LIMIT) { atomicOr(&ctr->flags, F_SPIN_TIMEOUT); break; }
+                    __nanosleep(20);
+                    continue;
                 }
+                prefix += (uint32_t)w;
+                if (fl == 2u) break;
+                --j;
+            }
+            lb_store(my, lb_pack(epoch, 2u, prefix + run));
+        }
+        s_gofs[d] = s_gbase[d] + prefix - s_lstart[d];
+        __syncthreads();
+        // 5. coalesced write of the staged tile
+        const uint32_t tile_n = min((uint32_t)RS_TILE, n - tile * RS_TILE);
+        for (uint32_t j = threadIdx.x; j < tile_n; j += RS_THREADS) {
+            const uint32_t k = s_key[j];
+            const uint32_t pos = s_gofs[(k >> shift) & 255u] + j;
+            if (pos < n) {
+                keys_out[pos] = k;
+                vals_out[pos] = s_val[j];
             }
         }
         __syncthreads();

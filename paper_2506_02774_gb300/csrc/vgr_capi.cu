@@ -629,9 +629,8 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_PREPROCESS);
     launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, v->grid_wide, s);
     mark(VGR_STAGE_DEPTH_SORT);
-    // every in-front entry is sorted; culled ones carry the key 0xFFFFFFFF and land last
-    launch_radix_hist(v->vis.depth, &v->ctr->n_front, nullptr, v->cap_vis, 4, &v->ctr->depth_hist[0][0],
-                      v->grid_scan, s);
+    // every potentially visible entry is sorted; culled ones carry the key
+    // 0xFFFFFFFF and land last (the digit histograms come from preprocess)
     for (int p = 0; p < 4; ++p) {
         const uint32_t* kin = p == 0 ? v->vis.depth : v->sortK[(p + 1) & 1];
         const uint32_t* vin = p == 0 ? nullptr : v->sortV[(p + 1) & 1];
@@ -664,7 +663,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
-    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 5u /*depth hist + 4 passes*/ + 1u /*color*/ +
+    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
            1u /*emit*/ + (uint32_t)tile_passes + 1u /*ranges*/ + 1u /*blend*/;
 }
 
