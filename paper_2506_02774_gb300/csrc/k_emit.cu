@@ -3,7 +3,7 @@
 // pair list.
 //
 // Visible Gaussians are visited in depth order (the output of the depth
-// sort), 256 per CTA tile.  Each one owns as many pair slots as it has
+// sort), 1024 per CTA tile (4 per thread).  Each one owns as many pair slots as it has
 // candidate tiles; a decoupled look-back scan over the candidate counts gives
 // every CTA tile its global slot range.  The CTA then walks its slots with
 // all 256 threads (slot -> Gaussian by binary search over the CTA's
@@ -23,8 +23,10 @@
 namespace vgr {
 
 constexpr int EM_THREADS = 256;
+constexpr int EM_ITEMS = 4;
+constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
 
-uint32_t emit_tile() { return EM_THREADS; }
+uint32_t emit_tile() { return EM_TILE; }
 
 __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
                                                      VisBuffers vis, float4* __restrict__ srecA,
@@ -35,15 +37,15 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
                                                      Counters* __restrict__ ctr, const FrameParams* __restrict__ fp) {
     __shared__ uint32_t s_scan[9];
     __shared__ uint32_t s_tile, s_prefix;
-    __shared__ uint32_t s_off[EM_THREADS + 1];
-    __shared__ float4 s_g[EM_THREADS];      // u v a b
-    __shared__ float4 s_h[EM_THREADS];      // c rx ry thre
-    __shared__ uint32_t s_rect[EM_THREADS]; // x0 | y0 << 16
-    __shared__ uint32_t s_w[EM_THREADS];
+    __shared__ uint32_t s_off[EM_TILE + 1];   // candidate counts, then exclusive slot offsets
+    __shared__ float4 s_g[EM_TILE];           // u v a b
+    __shared__ float4 s_h[EM_TILE];           // c rx ry thre
+    __shared__ uint32_t s_rect[EM_TILE];      // x0 | y0 << 16
+    __shared__ uint16_t s_w[EM_TILE];         // candidate rectangle width
     __shared__ uint32_t s_hist[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     const uint32_t n_vis = min(ctr->n_vis, cap_vis);
-    const uint32_t ntiles = (n_vis + EM_THREADS - 1) / EM_THREADS;
+    const uint32_t ntiles = (n_vis + EM_TILE - 1) / EM_TILE;
     const uint32_t epoch = fp->epoch;
     const uint32_t TW = fp->tiles_x;
     const float Wf = fp->width_f, Hf = fp->height_f;
@@ -56,31 +58,44 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) break;
-        const uint32_t r = tile * EM_THREADS + threadIdx.x;
-        uint32_t area = 0;
-        if (r < n_vis) {
-            const uint32_t vi = order[r];
-            area = vis.ntile[vi];
-            const uint2 rect = vis.rect[vi];
-            const float4 A = vis.recA[vi];
-            const float4 B = vis.recB[vi];
-            srecA[r] = A;
-            srecB[r] = B;
-            srecC[r] = vis.rgb[vi];
-            // the conic is stored pre-scaled (A = -a/2, B = -b, C = -c/2): exact to undo
-            const float ca = -2.0f * A.z, cb = -A.w, cc = -2.0f * B.x;
-            s_g[threadIdx.x] = make_float4(A.x, A.y, ca, cb);
-            s_h[threadIdx.x] = make_float4(cc, __fdiv_rn(-cb, ca), __fdiv_rn(-cb, cc), B.y - TILE_EPS);
-            s_rect[threadIdx.x] = rect.x;
-            s_w[threadIdx.x] = (rect.y & 0xFFFFu) - (rect.x & 0xFFFFu) + 1u;
+        // gather EM_ITEMS Gaussians per thread (independent loads in flight)
+#pragma unroll
+        for (int k = 0; k < EM_ITEMS; ++k) {
+            const uint32_t q = k * EM_THREADS + threadIdx.x;  // position in rank order within the tile
+            const uint32_t r = tile * EM_TILE + q;
+            uint32_t area = 0;
+            if (r < n_vis) {
+                const uint32_t vi = order[r];
+                area = vis.ntile[vi];
+                const uint2 rect = vis.rect[vi];
+                const float4 A = vis.recA[vi];
+                const float4 B = vis.recB[vi];
+                srecA[r] = A;
+                srecB[r] = B;
+                srecC[r] = vis.rgb[vi];
+                // the conic is stored pre-scaled (A = -a/2, B = -b, C = -c/2): exact to undo
+                const float ca = -2.0f * A.z, cb = -A.w, cc = -2.0f * B.x;
+                s_g[q] = make_float4(A.x, A.y, ca, cb);
+                s_h[q] = make_float4(cc, __fdiv_rn(-cb, ca), __fdiv_rn(-cb, cc), B.y - TILE_EPS);
+                s_rect[q] = rect.x;
+                s_w[q] = (uint16_t)((rect.y & 0xFFFFu) - (rect.x & 0xFFFFu) + 1u);
+            }
+            s_off[q] = area;
         }
+        __syncthreads();
+        // exclusive scan of the candidate counts in rank order: thread t owns entries 4t .. 4t+3
+        uint32_t a4[EM_ITEMS];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < EM_ITEMS; ++k) { a4[k] = s_off[EM_ITEMS * threadIdx.x + k]; sum += a4[k]; }
         uint32_t total;
-        const uint32_t excl = block_excl_scan<EM_THREADS / 32>(area, s_scan, &total);
-        s_off[threadIdx.x] = excl;
+        uint32_t run = block_excl_scan<EM_THREADS / 32>(sum, s_scan, &total);
+#pragma unroll
+        for (int k = 0; k < EM_ITEMS; ++k) { s_off[EM_ITEMS * threadIdx.x + k] = run; run += a4[k]; }
         if (threadIdx.x < 32) {
             const uint32_t pre = lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
             if (threadIdx.x == 0) {
-                s_off[EM_THREADS] = total;
+                s_off[EM_TILE] = total;
                 s_prefix = pre;
             }
         }
@@ -88,7 +103,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
         const uint64_t base = s_prefix;
         for (uint32_t j = threadIdx.x; j < total; j += EM_THREADS) {
             // owner of slot j: the last g with s_off[g] <= j
-            uint32_t lo = 0, hi = EM_THREADS;
+            uint32_t lo = 0, hi = EM_TILE;
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (s_off[mid] <= j) lo = mid; else hi = mid;
@@ -108,7 +123,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
             const uint64_t pos = base + j;
             if (pos < cap) {
                 pair_key[pos] = key;
-                pair_val[pos] = tile * EM_THREADS + g;
+                pair_val[pos] = tile * EM_TILE + g;
                 for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
             }
         }
