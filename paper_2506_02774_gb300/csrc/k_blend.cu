@@ -18,7 +18,8 @@
 //   alpha = min(0.99, theta e^rho)         (Eq. 3)
 //   T'    = T (1 - alpha); stop when T' < 1e-4 (this Gaussian excluded)
 //   C    += alpha T rgb; T = T'
-// The CTA leaves once all 256 pixels have stopped.  Modes: canonical (every
+// CTAs take tiles heaviest first (k_tile_order).  The CTA leaves once all
+// 256 pixels have stopped.  Modes: canonical (every
 // pixel of the tile, alpha first, then the alpha* test; for the
 // filtered-vs-unfiltered comparison) and the Eq. 5 lookup table for e^rho.
 #include "vgr_internal.cuh"
@@ -31,7 +32,8 @@ constexpr int BL_WARPS = BL_THREADS / 32;
 constexpr int BL_BATCH = 256;
 
 template <int MODE>
-__global__ void __launch_bounds__(BL_THREADS) k_blend(const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict__ tile_order,
+                                                      const uint2* __restrict__ ranges,
                                                       const uint32_t* __restrict__ pair_rank,
                                                       const float4* __restrict__ srecA,
                                                       const float4* __restrict__ srecB,
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint2* __restrict__ 
     __shared__ uint8_t s_list[BL_WARPS][BL_BATCH];     // per-warp record indices, depth order
     __shared__ float s_lut[260];
     const uint32_t W = fp->width, H = fp->height, TW = fp->tiles_x;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = tile_order[blockIdx.x];  // heaviest tiles first
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t px = (tile % TW) * TILE + (threadIdx.x & (TILE - 1));
     const uint32_t ty0 = (tile / TW) * TILE;
@@ -142,15 +144,16 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint2* __restrict__ 
     if (lane == 0 && wsum) atomicAdd(&ctr->pix_evals, (unsigned long long)wsum);
 }
 
-void launch_blend(uint32_t n_tiles, const uint2* ranges, const uint32_t* pair_rank, const float4* srecA,
+void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_rank,
+                  const float4* srecA,
                   const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s) {
     if (filter == VGR_FILTER_CANONICAL)
-        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
     else if (exp_mode == VGR_EXP_LUT)
-        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
     else
-        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
 }
 
 }  // namespace vgr

@@ -171,4 +171,33 @@ void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs
     k_ranges<<<grid, 256, 0, s>>>(keys, ctr, cap_pairs, n_tiles, ranges);
 }
 
+// Blend order: tiles by descending pair count (buckets of floor(log2(count+1)),
+// heaviest bucket first), so the long tiles start in the first wave and the
+// short ones fill in behind them.  One CTA; the order inside a bucket does
+// not matter (tiles are independent).
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, uint32_t n_tiles,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ uint32_t s_cnt[33], s_start[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&s_cnt[32 - __clz(r.y - r.x + 1u)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 32; b >= 0; --b) { s_start[b] = run; run += s_cnt[b]; }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&s_start[32 - __clz(r.y - r.x + 1u)], 1u)] = t;
+    }
+}
+
+void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {
+    k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order);
+}
+
 }  // namespace vgr

@@ -110,6 +110,7 @@ struct vgr_view {
     uint32_t* pairK[2] = {nullptr, nullptr};
     uint32_t* pairV[2] = {nullptr, nullptr};
     uint2* ranges = nullptr;
+    uint32_t* tile_order = nullptr;  // blend order, heaviest tiles first
     float* image = nullptr;
     float* lut = nullptr;
     unsigned long long* status = nullptr;
@@ -458,11 +459,13 @@ vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
     if (px <= v->cap_pixels && tiles <= v->cap_tiles) return VGR_OK;
     dfree(v->image);
     dfree(v->ranges);
+    dfree(v->tile_order);
     v->img_bytes = 0;
     const uint32_t cp = (uint32_t)std::max<uint64_t>(px, v->cap_pixels);
     const uint32_t ct = (uint32_t)std::max<uint64_t>(tiles, v->cap_tiles);
     vgr_status s;
-    if ((s = dalloc(&v->image, (size_t)cp * 3, &v->img_bytes)) || (s = dalloc(&v->ranges, ct, &v->img_bytes))) {
+    if ((s = dalloc(&v->image, (size_t)cp * 3, &v->img_bytes)) || (s = dalloc(&v->ranges, ct, &v->img_bytes)) ||
+        (s = dalloc(&v->tile_order, ct, &v->img_bytes))) {
         v->cap_pixels = v->cap_tiles = 0;
         return s;
     }
@@ -476,7 +479,7 @@ void destroy_view(vgr_view* v) {
     free_pairs(v);
     free_cut(v);
     dfree(v->bitmap); dfree(v->front_bm); dfree(v->frontier[0]); dfree(v->frontier[1]);
-    dfree(v->ranges); dfree(v->image); dfree(v->lut); dfree(v->status);
+    dfree(v->ranges); dfree(v->tile_order); dfree(v->image); dfree(v->lut); dfree(v->status);
     dfree(v->ctr); dfree(v->vstate); dfree(v->fp_dev);
     if (v->fp_host) cudaFreeHost(v->fp_host);
     if (v->ctr_host) cudaFreeHost(v->ctr_host);
@@ -656,15 +659,16 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     v->last_tile_buf = fb;
     mark(VGR_STAGE_RANGES);
     launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, n_tiles, v->ranges, v->grid_wide, s);
+    launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
     mark(VGR_STAGE_BLEND);
-    launch_blend(n_tiles, v->ranges, v->pairV[fb], v->srecA, v->srecB, v->srecC, v->fp_dev, v->lut, v->image, v->ctr,
+    launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->srecA, v->srecB, v->srecC, v->fp_dev, v->lut, v->image, v->ctr,
                  v->opts.filter, v->opts.exp_mode, s);
     mark(VGR_N_STAGES);
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
     return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
-           1u /*emit*/ + (uint32_t)tile_passes + 1u /*ranges*/ + 1u /*blend*/;
+           1u /*emit*/ + (uint32_t)tile_passes + 2u /*ranges, tile order*/ + 1u /*blend*/;
 }
 
 vgr_status check_camera(const vgr_camera* c, float tau) {

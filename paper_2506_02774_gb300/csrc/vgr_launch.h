@@ -61,9 +61,11 @@ void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, float4
 uint32_t emit_tile();
 void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
                    int grid, cudaStream_t s);
+void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
 
 // k_blend.cu
-void launch_blend(uint32_t n_tiles, const uint2* ranges, const uint32_t* pair_rank, const float4* srecA,
+void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_rank,
+                  const float4* srecA,
                   const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
 
