@@ -41,11 +41,18 @@ def image_report(img: np.ndarray, ref: dict, tile_mask=None) -> dict:
                 max_abs_all=float(diff[sel].max()) if sel.any() else 0.0)
 
 
+FLIP_BOUND = 1e-2  # a flipped alpha* decision moves a pixel by at most ~2 alpha* max(rgb)
+
+
 def check_image(img, ref, tile_mask=None, tol=IMG_TOL, psnr_min=PSNR_MIN):
+    """2e-3 on unflagged pixels; flagged pixels (a near-threshold alpha
+    decision at T >= 0.05) within the bound of one flipped decision; PSNR over
+    all pixels.  The count guard catches a flag rule gone wrong."""
     r = image_report(img, ref, tile_mask)
     assert r["max_abs"] <= tol, r
+    assert r["max_abs_all"] <= FLIP_BOUND, r
     assert r["psnr"] >= psnr_min, r
-    assert r["flagged"] <= max(8, 0.01 * r["pixels"]), r
+    assert r["flagged"] <= max(8, 0.05 * r["pixels"]), r
     return r
 
 
