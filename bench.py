@@ -100,6 +100,25 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+OPS_PER_EVAL = 9      # 2 FADD (dx, dy), 4 FMUL + 2 FFMA (rho), 1 compare (Eq. 4)
+OPS_PER_CONTRIB = 10  # FMUL (exp argument), FMUL (theta e^rho), min, 1 - alpha, T', compare, alpha T, 3 FFMA, + 1 MUFU
+
+
+def _traffic(kernel: str, source: str, algorithmic: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), used only while the kernel's source is the one
+    the counters were taken on (sha256 of csrc/<source>); else None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2506_02774_gb300", "csrc", source)
+    if not os.path.exists(p) or not os.path.exists(src):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    return int(d["dram_bytes_per_launch"])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -153,7 +172,8 @@ def run_ours(args) -> dict:
     h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF if args.storage == "half" else vgr.STORE_FP32)
     t_up = time.time() - t0
     stream = torch.cuda.Stream()
-    view = vgr.View(h, stream=stream.cuda_stream, timing=False)
+    view = vgr.View(h, stream=stream.cuda_stream, timing=False, use_graph=not args.no_graph)
+    view_loop = vgr.View(h, stream=stream.cuda_stream, timing=False, use_graph=False)
     tau = cfg["tau"]
     nfr = cfg["frames"]
     W, H = cfg["width"], cfg["height"]
@@ -164,40 +184,48 @@ def run_ours(args) -> dict:
         start[1] += 40.0 * rank
     cams = [scenegen.trajectory(wl["scene"], f % nfr, heading, start) for f in range(args.warmup + args.steps)]
     structs = [vgr.camera_struct(c) for c in cams]
-    # warm-up (frame 0 finds its cut top-down, then temporal updates)
-    for i in range(args.warmup):
-        view.render(cams[i], tau)
-    torch.cuda.synchronize()
 
-    # ---- timed region: K frames, device clock on the view's stream
+    def timed(v):
+        """Warm-up frames (frame 0 finds its cut top-down, then temporal
+        updates), then K timed frames on the view's stream, max over ranks."""
+        v.reset()
+        for i in range(args.warmup):
+            v.render(cams[i], tau)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat, stats, kernels = [], [], 0
+        ev0.record(stream)
+        for i in range(args.warmup, args.warmup + args.steps):
+            t = time.perf_counter()
+            r = v.render(cams[i], tau)
+            lat.append(time.perf_counter() - t)
+            stats.append(r.stats)
+            kernels += r.stats["kernels"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            tt = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, lat, stats, kernels
+
+    # ---- timed regions: the plain launch loop, then the headline view
+    # (each frame one captured CUDA graph unless --no-graph)
     clk = ClockSampler(dev)
     clk.start()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat = []
-    stats = []
-    kernels = 0
-    ev0.record(stream)
-    for i in range(args.warmup, args.warmup + args.steps):
-        t = time.perf_counter()
-        r = view.render(cams[i], tau)
-        lat.append(time.perf_counter() - t)
-        stats.append(r.stats)
-        kernels += r.stats["kernels"]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    ms_loop, _, _, _ = timed(view_loop)
+    ms, lat, stats, kernels = timed(view)
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    view_loop.close()
     frames = args.steps * ws
     value = frames / (ms / 1e3)
+    value_loop = frames / (ms_loop / 1e3)
 
     # ---- per-stage device times (a second pass over the same frames with stage events)
     view_t = vgr.View(h, stream=stream.cuda_stream, timing=True)
@@ -231,7 +259,7 @@ def run_ours(args) -> dict:
     # ---- roofline of the dominant kernel
     mean = {k: float(np.mean([s[k] for s in stats])) for k in
             ("cut_count", "front_count", "visible_count", "pair_count", "nodes_evaluated", "candidate_pairs",
-             "pixel_pair_evals")}
+             "pixel_pair_evals", "pixel_pair_contribs")}
     n_tiles = ((W + 15) // 16) * ((H + 15) // 16)
     tp = max(1, (int(math.ceil(math.log2(max(2, n_tiles)))) + 7) // 8)
     fb = _frame_bytes(sc, mean, W, H, tp)
@@ -239,13 +267,27 @@ def run_ours(args) -> dict:
     shares = {s: float(stage_ms[i]) for i, s in enumerate(vgr.STAGES)}
     top = max(shares, key=shares.get)
     hbm_stages = {s: fb[s] / (shares[s] * 1e-3) / 1e9 for s in vgr.STAGES if shares[s] > 0}
-    evals = None
-    roof = dict(bound="hbm", stage=top, achieved=round(hbm_stages.get(top, 0.0), 1), peak=peaks["hbm_gbs"],
-                unit="GB/s", frac=round(hbm_stages.get(top, 0.0) / peaks["hbm_gbs"], 4),
-                traffic=None, peak_source=peaks["source"] + " hbm_gbs (MEASURED_PEAKS.json)",
-                algorithmic_bytes=int(fb[top]), kernel_ms=round(shares[top], 4))
     if top == "blend":
-        roof["note"] = "blend is issue-bound; see stage_gbs and DESIGN.md for its ALU roofline"
+        # plain-ALU roofline: FP32 lane-instructions the method needs per
+        # evaluated pixel-pair (dx, dy, rho, Eq. 4 test) and per blended one
+        # (exp argument, alpha, T update, test, weight, 3 colour FMAs),
+        # against SMs x 128 FP32 lanes x clock
+        X, K = mean["pixel_pair_evals"], mean["pixel_pair_contribs"]
+        ops = OPS_PER_EVAL * X + OPS_PER_CONTRIB * K
+        t = shares[top] * 1e-3
+        peak_t = 152 * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof = dict(bound="alu", stage=top, achieved=round(ops / t / 1e12, 3), peak=round(peak_t, 2),
+                    unit="TFLOP/s", frac=round(ops / t / 1e12 / peak_t, 4),
+                    traffic=_traffic("k_blend", "k_blend.cu", fb[top]),
+                    peak_source="152 SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz of %s), one op per FP32 "
+                                "lane-instruction" % (peaks["sm_max_mhz"], peaks["source"]),
+                    ops_per_launch=int(ops), kernel_ms=round(shares[top], 4),
+                    hbm_frac=round(hbm_stages[top] / peaks["hbm_gbs"], 4))
+    else:
+        roof = dict(bound="hbm", stage=top, achieved=round(hbm_stages.get(top, 0.0), 1), peak=peaks["hbm_gbs"],
+                    unit="GB/s", frac=round(hbm_stages.get(top, 0.0) / peaks["hbm_gbs"], 4),
+                    traffic=None, peak_source=peaks["source"] + " hbm_gbs (MEASURED_PEAKS.json)",
+                    algorithmic_bytes=int(fb[top]), kernel_ms=round(shares[top], 4))
     out = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=ws, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms / args.steps, 4), higher_is_better=True,
                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
@@ -257,20 +299,116 @@ def run_ours(args) -> dict:
                e2e=dict(value=round(e2e["value"], 2), unit=e2e["unit"],
                         h2d_bytes_per_step=e2e["h2d_bytes_per_step"], d2h_bytes_per_step=e2e["d2h_bytes_per_step"]),
                gpu_launches=int(kernels),
+               launch_mode="cuda-graph replay per frame" if not args.no_graph else "plain launch loop",
+               value_plain_loop=round(value_loop, 2),
                roofline=roof, clocks=clocks,
-               p50_ms=round(1e3 * float(np.percentile(lat, 50)), 4), p99_ms=round(1e3 * float(np.percentile(lat, 99)), 4),
+               frame_latency_ms=dict(p50=round(1e3 * float(np.percentile(lat, 50)), 4),
+                                     p99=round(1e3 * float(np.percentile(lat, 99)), 4)),
                stage_ms={k: round(v, 4) for k, v in shares.items()},
                stage_gbs={k: round(v, 1) for k, v in hbm_stages.items()},
                counts={k: round(v, 1) for k, v in mean.items()},
                setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
     view.close()
+    if args.config == "city" and not args.leaves and not args.no_served:
+        out["served"] = run_served(sc, h, args.serve_clients, args.serve_rate, args.serve_seconds)
+        out["p50_ms"], out["p99_ms"] = out["served"]["continuous"]["p50_ms"], out["served"]["continuous"]["p99_ms"]
     h.close()
+    if args.config == "city" and not args.leaves and not args.no_batched:
+        out["batched"] = run_batched(sc, args.batch_views, args.batch_steps, 4)
     if ws > 1:
         torch.distributed.destroy_process_group()
     out["_scene"] = sc if rank == 0 else None
     out["_cams"] = cams
     out["_rank"] = rank
     return out
+
+
+def run_batched(sc, n_views: int, steps: int, warmup: int, seed: int = 4) -> dict:
+    """Multi-view batch: n_views views of the city (FP16 SH + BF16 covariance
+    storage), each at frames 300.. of its own street walk at a size drawn
+    uniformly from 360p/720p/1080p/1440p (fx scaled with the width); one
+    vgr_render_batch per step, against the same frames rendered one view
+    after another.  Wall-clock throughput (views/s)."""
+    import torch
+    import scenegen
+    import paper_2506_02774_gb300 as vgr
+    rng = np.random.default_rng(seed)
+    names = ["360p", "720p", "1080p", "1440p"]
+    pick = [names[i] for i in rng.integers(0, 4, n_views)]
+    sizes = [scenegen.RESOLUTIONS[n] for n in pick]
+    tau = scenegen.CONFIGS["city"]["tau"]
+    h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF)
+    views = [vgr.View(h, use_graph=True) for _ in range(n_views)]
+    frames = list(range(300 - warmup, 300 + steps))
+    cams = {fr: [scenegen.street_trajectory("city", 200 + i, fr, *sizes[i]) for i in range(n_views)] for fr in frames}
+    taus = [tau] * n_views
+    out = {}
+    for mode in ("sequential", "batched"):
+        for v in views:
+            v.reset()
+        pix = 0
+        for fr in frames:
+            if fr == 300:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+            if mode == "batched":
+                res = vgr.render_batch(views, cams[fr], taus)
+            else:
+                res = [v.render(c, tau) for v, c in zip(views, cams[fr])]
+            if fr >= 300:
+                pix += sum(r.width * r.height for r in res)
+        dt = time.perf_counter() - t
+        out[mode] = dict(views_per_s=round(n_views * steps / dt, 1), ms_per_step=round(1e3 * dt / steps, 3),
+                         mpix_per_s=round(pix / dt / 1e6, 1))
+    dev_bytes = sum(v.device_bytes() for v in views)
+    for v in views:
+        v.close()
+    h.close()
+    counts = {n: pick.count(n) for n in names}
+    return dict(views=n_views, sizes=counts, frames="300..%d of each view's own street walk" % (300 + steps - 1),
+                storage="fp16 SH + bf16 covariance", views_device_gb=round(dev_bytes / 1e9, 1),
+                speedup=round(out["batched"]["views_per_s"] / out["sequential"]["views_per_s"], 3), **out)
+
+
+def run_served(sc, h, n_clients: int, rate: float, seconds: float, seed: int = 5) -> dict:
+    """Serving: n_clients clients with Poisson arrivals (rate req/s each) for
+    `seconds`, image sizes uniform over 720p/1080p/1440p, each client on its
+    own street walk (one frame step per request), images copied to pinned
+    host memory.  Latency = completion - arrival.  Continuous batching (every
+    client's frame may be in flight) against one frame at a time."""
+    import scenegen
+    import paper_2506_02774_gb300 as vgr
+    rng = np.random.default_rng(seed)
+    names = ["720p", "1080p", "1440p"]
+    pick = [names[i] for i in rng.integers(0, 3, n_clients)]
+    tau = scenegen.CONFIGS["city"]["tau"]
+    warm, trace = [], []
+    for c in range(n_clients):
+        W, H = scenegen.RESOLUTIONS[pick[c]]
+        for k in range(2):
+            warm.append(dict(client=c, arrival_s=0.0, tau=tau, cam=scenegen.street_trajectory("city", 300 + c, k, W, H)))
+        t, k = 0.0, 2
+        while True:
+            t += float(rng.exponential(1.0 / rate))
+            if t > seconds:
+                break
+            trace.append(dict(client=c, arrival_s=t, tau=tau, cam=scenegen.street_trajectory("city", 300 + c, k, W, H)))
+            k += 1
+    trace.sort(key=lambda r: r["arrival_s"])
+    out = {}
+    for mode, inflight in (("continuous", 0), ("one_at_a_time", 1)):
+        sv = vgr.Server(h, n_clients, max_inflight=inflight, host_images=True)
+        sv.serve(warm)
+        r = sv.serve(trace)
+        sv.close()
+        ok = r["status"] == 0
+        lat = 1e3 * (r["finish_s"] - r["arrival_s"])[ok]
+        span = float(r["finish_s"].max() - r["arrival_s"].min())
+        out[mode] = dict(p50_ms=round(float(np.percentile(lat, 50)), 3), p99_ms=round(float(np.percentile(lat, 99)), 3),
+                         mean_ms=round(float(lat.mean()), 3), completed=int(ok.sum()), refused=int((r["status"] == 2).sum()),
+                         frames_per_s=round(float(ok.sum()) / span, 1))
+    return dict(clients=n_clients, rate_per_client=rate, seconds=seconds, requests=len(trace),
+                sizes={n: pick.count(n) for n in names}, host_images=True, **out)
 
 
 def cpu_baseline(sc, cams, tau, budget_s: float = 20.0) -> dict:
@@ -328,6 +466,14 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--no-graph", action="store_true", help="headline view without CUDA graph replay")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batch leg")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
+    ap.add_argument("--batch-views", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-clients", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="city", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="fp32", choices=["fp32", "half"])

@@ -106,7 +106,9 @@ typedef struct {
     uint32_t lut_size;       /* m of Eq. 5 when exp_mode == VGR_EXP_LUT (1..256; default 32) */
     uint32_t temporal;       /* 1: temporal cut update between frames (default); 0: always from scratch */
     uint32_t timing;         /* 1: record per-stage device times into vgr_frame_stats */
-    uint32_t use_graph;      /* 1: replay steady-state frames as CUDA graphs (default) */
+    uint32_t use_graph;      /* 1: replay each frame as one captured CUDA graph (captured on first use per
+                                cut mode and buffer parity; re-captured after a buffer grows or the image
+                                size changes); ignored while timing is set.  Default 0. */
     uint64_t cut_capacity;   /* initial capacities; 0 = automatic.  Grown on demand. */
     uint64_t pair_capacity;
     uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
@@ -126,6 +128,7 @@ typedef struct {
     uint32_t replays;         /* frame replays (buffer growth or LoD fallback) */
     uint32_t kernels;         /* kernel launches made for the frame, replays included */
     uint64_t pixel_pair_evals;/* X: (pixel, Gaussian) evaluations in the blend */
+    uint64_t pixel_pair_contribs; /* of those, the ones blended (alpha >= alpha*, before termination) */
     float stage_ms[VGR_N_STAGES]; /* device time per stage (timing = 1), else 0 */
     float frame_ms;           /* device time of the frame (timing = 1), else 0 */
 } vgr_frame_stats;
@@ -201,7 +204,100 @@ vgr_status vgr_render_frame(vgr_view* v, const vgr_camera* cam, float tau, vgr_f
 vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb,
                                  vgr_frame* out);
 
+/*
+ * Asynchronous form of vgr_render_frame, for keeping several views' frames
+ * on the GPU at once (a view created with stream 0 owns its own stream).
+ * vgr_submit_frame validates the arguments as vgr_render_frame does and
+ * enqueues the frame -- and, when host_rgb is not NULL, the copy of the image
+ * into host_rgb (caller-owned, height x width x 3 floats, valid until
+ * vgr_finish_frame returns) -- without waiting.  vgr_frame_done sets *done to
+ * 1 when the submitted work has finished, 0 otherwise, without waiting.
+ * vgr_finish_frame waits for it, reads the frame's status, replays the frame
+ * when the temporal update fell back or a buffer had to grow (replays wait),
+ * and fills out (may be NULL); the result equals vgr_render_frame's.  Each
+ * successful submit is followed by exactly one finish; until then another
+ * submit, vgr_reset_view and vgr_view_debug return VGR_E_INVALID.
+ */
+vgr_status vgr_submit_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb);
+vgr_status vgr_frame_done(vgr_view* v, int* done);
+vgr_status vgr_finish_frame(vgr_view* v, vgr_frame* out);
+
+/*
+ * One frame on each of n distinct views (own camera, tau and image size
+ * each; the views may share a hierarchy): every frame is submitted, then
+ * every frame is finished in order, so frames of views on different streams
+ * overlap on the GPU.  host_rgb is NULL or n pointers (NULL entries: no host
+ * copy); outs is NULL or n frames.  Returns the first error (VGR_E_INVALID
+ * for a repeated or NULL view, before anything is submitted); every frame
+ * that was submitted is finished.  The paper renders one view at a time;
+ * this call has no counterpart there.
+ */
+vgr_status vgr_render_batch(vgr_view* const* views, const vgr_camera* cams, const float* taus,
+                            float* const* host_rgb, uint32_t n, vgr_frame* outs);
+
 vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* out);
+
+/*
+ * Device bytes a view created with opts (NULL: defaults) on h holds after
+ * its first frame at width x height, before any buffer grows.
+ */
+vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* opts, uint32_t width,
+                                   uint32_t height, uint64_t* bytes);
+
+/*
+ * Frame server with continuous batching (no counterpart in the paper, which
+ * renders one view).  Each client of a server owns a view (own stream),
+ * created when the client's first request is admitted: admission requires
+ * free device memory >= vgr_view_bytes_estimate at the request's image size
+ * + hbm_reserve, otherwise the request completes with VGR_E_NOMEM.  A
+ * client's requests run in arrival order, one frame in flight per client;
+ * frames of different clients run concurrently, at most max_inflight at a
+ * time, and a request starts as soon as its client and a slot are free.
+ */
+typedef struct vgr_server vgr_server;
+
+typedef struct {
+    uint32_t n_clients;      /* clients 0 .. n_clients-1 (1..65536) */
+    uint32_t max_inflight;   /* frames in flight at once; 1 = one frame at a time; 0 = n_clients */
+    uint32_t host_images;    /* 1: every image is copied to the client's pinned host buffer */
+    uint64_t hbm_reserve;    /* free device bytes admission keeps (default 1 GiB) */
+    vgr_view_opts view;      /* options of every client's view; stream and timing are ignored
+                                (default: vgr_default_view_opts with use_graph = 1) */
+} vgr_serve_opts;
+
+typedef struct {
+    uint32_t client;
+    float tau;
+    double arrival_s;        /* seconds after the start of vgr_serve_trace; non-decreasing */
+    vgr_camera cam;
+} vgr_request;
+
+typedef struct {
+    double start_s;          /* submission (after admission) */
+    double finish_s;         /* completion seen by the server: image in device memory, and in the
+                                client's host buffer when host_images is set */
+    vgr_status status;       /* VGR_OK, VGR_E_NOMEM (not admitted) or the frame's error */
+    uint32_t cut_count, visible_count;
+    uint64_t pair_count;
+    uint32_t replays, lod_from_scratch;
+} vgr_request_result;
+
+void vgr_default_serve_opts(vgr_serve_opts* opts);
+/* The server keeps h (which must outlive it) and copies opts. */
+vgr_status vgr_create_server(vgr_hierarchy* h, const vgr_serve_opts* opts, vgr_server** out);
+vgr_status vgr_destroy_server(vgr_server* s);
+/*
+ * Serve n requests (caller-owned, read only) in real time: request i is
+ * released at arrival_s after the call starts; res (n entries) receives each
+ * request's times and counts.  Returns when every request has completed.
+ * Views persist across calls (a first trace can admit and warm up the
+ * clients).  Returns VGR_E_INVALID for a bad client id or decreasing arrival
+ * times (before anything runs), else the first frame error (refusals by
+ * admission are reported per request only).  Not thread-safe per server.
+ */
+vgr_status vgr_serve_trace(vgr_server* s, const vgr_request* reqs, uint32_t n, vgr_request_result* res);
+/* A client's view (NULL before admission) and its pinned host image (NULL without host_images). */
+vgr_status vgr_server_client_view(vgr_server* s, uint32_t client, vgr_view** view, const float** host_rgb);
 
 /*
  * The pair sort of the frame path as a standalone call (Sec. 3.1 "Sorting"):

@@ -17,7 +17,8 @@ from . import _abi
 from ._abi import (EXP_EXACT, EXP_LUT, FILTER_CANONICAL, FILTER_PREEMPTIVE, STAGES, STORE_FP32, STORE_HALF,
                    VgrError)
 
-__all__ = ["Hierarchy", "View", "FrameResult", "camera_struct", "sort_pairs", "VgrError", "load_library", "STORE_FP32",
+__all__ = ["Hierarchy", "View", "FrameResult", "Server", "render_batch", "camera_struct", "sort_pairs", "VgrError",
+           "load_library", "STORE_FP32",
            "STORE_HALF", "FILTER_PREEMPTIVE", "FILTER_CANONICAL", "EXP_EXACT", "EXP_LUT", "STAGES"]
 
 
@@ -126,6 +127,7 @@ class FrameResult:
                           nodes_evaluated=int(s.nodes_evaluated), lod_from_scratch=int(s.lod_from_scratch),
                           replays=int(s.replays), kernels=int(s.kernels),
                           pixel_pair_evals=int(s.pixel_pair_evals),
+                          pixel_pair_contribs=int(s.pixel_pair_contribs),
                           stage_ms={n: float(s.stage_ms[i]) for i, n in enumerate(STAGES)},
                           frame_ms=float(s.frame_ms))
 
@@ -180,6 +182,31 @@ class View:
         return _abi.load().vgr_render_frame_host(self.handle, ctypes.byref(cam_struct), float(tau),
                                                  ctypes.c_void_p(host_ptr), ctypes.byref(fr))
 
+    def submit(self, cam: dict, tau: float, host_out: np.ndarray | None = None):
+        """Enqueue a frame without waiting (``vgr_submit_frame``); ``host_out``
+        (float32 H x W x 3, kept alive until finish) receives the image."""
+        c = camera_struct(cam)
+        ptr = None
+        if host_out is not None:
+            assert host_out.dtype == np.float32 and host_out.flags["C_CONTIGUOUS"]
+            assert host_out.shape == (int(cam["height"]), int(cam["width"]), 3)
+            ptr = ctypes.c_void_p(host_out.ctypes.data)
+        self._pending_host = host_out
+        _abi.check(_abi.load().vgr_submit_frame(self.handle, ctypes.byref(c), float(tau), ptr))
+
+    def done(self) -> bool:
+        d = ctypes.c_int32()
+        _abi.check(_abi.load().vgr_frame_done(self.handle, ctypes.byref(d)))
+        return bool(d.value)
+
+    def finish(self) -> FrameResult:
+        fr = _abi.Frame()
+        try:
+            _abi.check(_abi.load().vgr_finish_frame(self.handle, ctypes.byref(fr)))
+        finally:
+            self._pending_host = None
+        return FrameResult(fr)
+
     def reset(self):
         _abi.check(_abi.load().vgr_reset_view(self.handle))
 
@@ -219,6 +246,92 @@ class View:
     def close(self):
         if self.handle:
             _abi.check(_abi.load().vgr_destroy_view(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def render_batch(views, cams, taus, host_outs=None):
+    """One frame on each of several distinct views (``vgr_render_batch``):
+    all submitted, then all finished.  Returns one FrameResult per view."""
+    n = len(views)
+    assert len(cams) == n and len(taus) == n
+    if n == 0:
+        return []
+    hv = (ctypes.c_void_p * n)(*[v.handle.value for v in views])
+    cs = (_abi.Camera * n)(*[camera_struct(c) for c in cams])
+    ts = (ctypes.c_float * n)(*[float(t) for t in taus])
+    hp = None
+    if host_outs is not None:
+        for a, c in zip(host_outs, cams):
+            if a is not None:
+                assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+                assert a.shape == (int(c["height"]), int(c["width"]), 3)
+        hp = (ctypes.c_void_p * n)(*[(a.ctypes.data if a is not None else None) for a in host_outs])
+    frs = (_abi.Frame * n)()
+    _abi.check(_abi.load().vgr_render_batch(hv, cs, ts, hp, n, frs))
+    return [FrameResult(frs[i]) for i in range(n)]
+
+
+class Server:
+    """Continuous-batching frame server over one hierarchy (``vgr_create_server``)."""
+
+    def __init__(self, hier: Hierarchy, n_clients: int, *, max_inflight: int = 0, host_images: bool = False,
+                 hbm_reserve: int | None = None, use_graph: bool = True, **view_kw):
+        lib = _abi.load()
+        o = _abi.ServeOpts()
+        lib.vgr_default_serve_opts(ctypes.byref(o))
+        o.n_clients, o.max_inflight, o.host_images = int(n_clients), int(max_inflight), int(host_images)
+        if hbm_reserve is not None:
+            o.hbm_reserve = int(hbm_reserve)
+        o.view.use_graph = int(use_graph)
+        for k, val in view_kw.items():
+            setattr(o.view, k, val)
+        s = ctypes.c_void_p()
+        _abi.check(lib.vgr_create_server(hier.handle, ctypes.byref(o), ctypes.byref(s)))
+        self.handle = s
+        self.hier = hier
+        self.n_clients = int(n_clients)
+
+    def serve(self, requests):
+        """Serve a trace in real time.  ``requests``: list of dicts with client,
+        arrival_s, cam, tau (arrival_s non-decreasing).  Returns a numpy record
+        array with start_s, finish_s, status, counts per request."""
+        n = len(requests)
+        rq = (_abi.Request * max(1, n))()
+        for i, r in enumerate(requests):
+            rq[i].client = int(r["client"])
+            rq[i].tau = float(r["tau"])
+            rq[i].arrival_s = float(r["arrival_s"])
+            rq[i].cam = camera_struct(r["cam"])
+        rs = (_abi.RequestResult * max(1, n))()
+        _abi.check(_abi.load().vgr_serve_trace(self.handle, rq, n, rs))
+        out = np.zeros(n, dtype=[("client", "u4"), ("arrival_s", "f8"), ("start_s", "f8"), ("finish_s", "f8"),
+                                 ("status", "i4"), ("cut_count", "u4"), ("visible_count", "u4"),
+                                 ("pair_count", "u8"), ("replays", "u4"), ("lod_from_scratch", "u4")])
+        for i in range(n):
+            x = rs[i]
+            out[i] = (rq[i].client, rq[i].arrival_s, x.start_s, x.finish_s, x.status, x.cut_count, x.visible_count,
+                      x.pair_count, x.replays, x.lod_from_scratch)
+        return out
+
+    def client_host_image(self, client: int, height: int, width: int):
+        """A copy of the client's last image from its pinned host buffer
+        (servers created with host_images=True); None before admission."""
+        v, hp = ctypes.c_void_p(), ctypes.c_void_p()
+        _abi.check(_abi.load().vgr_server_client_view(self.handle, int(client), ctypes.byref(v), ctypes.byref(hp)))
+        if not hp.value:
+            return None
+        n = int(height) * int(width) * 3
+        return np.ctypeslib.as_array((ctypes.c_float * n).from_address(hp.value)).reshape(height, width, 3).copy()
+
+    def close(self):
+        if self.handle:
+            _abi.check(_abi.load().vgr_destroy_server(self.handle))
             self.handle = None
 
     def __del__(self):

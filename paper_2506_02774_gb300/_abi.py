@@ -38,7 +38,8 @@ class ViewOpts(ctypes.Structure):
 class FrameStats(ctypes.Structure):
     _fields_ = [("cut_count", c_u32), ("front_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64),
                 ("candidate_pairs", c_u64), ("nodes_evaluated", c_u64), ("lod_from_scratch", c_u32),
-                ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64), ("stage_ms", c_f32 * 9),
+                ("replays", c_u32), ("kernels", c_u32), ("pixel_pair_evals", c_u64),
+                ("pixel_pair_contribs", c_u64), ("stage_ms", c_f32 * 9),
                 ("frame_ms", c_f32)]
 
 
@@ -53,6 +54,21 @@ class DebugBuffers(ctypes.Structure):
                 ("vis_ntile", c_vp), ("vis_rect", c_vp), ("vis_recA", c_vp), ("vis_recB", c_vp),
                 ("rank_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_rank", c_vp),
                 ("tile_range", c_vp)]
+
+
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("n_clients", c_u32), ("max_inflight", c_u32), ("host_images", c_u32), ("hbm_reserve", c_u64),
+                ("view", ViewOpts)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("client", c_u32), ("tau", c_f32), ("arrival_s", ctypes.c_double), ("cam", Camera)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("start_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("status", c_i32),
+                ("cut_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64), ("replays", c_u32),
+                ("lod_from_scratch", c_u32)]
 
 
 _PROTOS = {
@@ -70,6 +86,17 @@ _PROTOS = {
     "vgr_sort_pairs": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_sort_pairs_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_last_error": (ctypes.c_char_p, []),
+    "vgr_submit_frame": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp]),
+    "vgr_frame_done": (c_i32, [c_vp, ctypes.POINTER(c_i32)]),
+    "vgr_finish_frame": (c_i32, [c_vp, ctypes.POINTER(Frame)]),
+    "vgr_render_batch": (c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(Camera), ctypes.POINTER(c_f32),
+                                 ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(Frame)]),
+    "vgr_view_bytes_estimate": (c_i32, [c_vp, ctypes.POINTER(ViewOpts), c_u32, c_u32, ctypes.POINTER(c_u64)]),
+    "vgr_default_serve_opts": (None, [ctypes.POINTER(ServeOpts)]),
+    "vgr_create_server": (c_i32, [c_vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(c_vp)]),
+    "vgr_destroy_server": (c_i32, [c_vp]),
+    "vgr_serve_trace": (c_i32, [c_vp, ctypes.POINTER(Request), c_u32, ctypes.POINTER(RequestResult)]),
+    "vgr_server_client_view": (c_i32, [c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
 }
 
 _lib = None

@@ -3,25 +3,27 @@
 // Sec. 4.2 (Eq. 4) in front of the exponential.
 //
 // One CTA of 256 threads per tile, one pixel per thread; warp w shades pixel
-// rows 2w and 2w+1.  The tile's pair range is consumed in batches of 256
-// records (48 bytes each, depth-rank order) staged in shared memory.  Each
-// record carries the half-height of its opacity-aware footprint box, outside
-// which rho < ln alpha* - ln theta holds with a margin; from it every warp
-// builds, in depth order, the list of batch records whose box reaches its two
-// rows and walks only that list.  Pixels a warp skips this way would have
-// failed the Eq. 4 test anyway, so the result is the same as walking the
-// whole batch, but tiles crossing the horizon (tens of thousands of small,
-// distant Gaussians over sky pixels that never saturate) cost each warp a
+// rows 2w and 2w+1 and walks the tile's pair range on its own (no CTA-wide
+// barrier): 32 records at a time (48 bytes each, depth-rank order), it keeps
+// those whose opacity-aware footprint box reaches one of its two rows -- the
+// box half-height is part of the record, and outside the box
+// rho < ln alpha* - ln theta holds with a margin, so a skipped record would
+// have failed the Eq. 4 test at every pixel of those rows -- stages them in
+// its own slice of shared memory and walks them in order, two at a time for
+// instruction-level parallelism.  The next 32 records are loaded while the
+// current ones are walked; the eight warps of a tile read the same records,
+// so all but the first read of each record hit L1.  A warp stops when its 32
+// pixels have stopped; tiles crossing the horizon (tens of thousands of
+// small distant Gaussians, each reaching one or two rows) cost each warp a
 // fraction of the pairs.  Per pixel:
 //   rho   = A dx^2 + B dx dy + C dy^2      (A = -a/2, B = -b, C = -c/2)
 //   skip if rho < ln alpha* - ln theta     (Eq. 4: alpha < alpha*, no exp)
 //   alpha = min(0.99, theta e^rho)         (Eq. 3)
 //   T'    = T (1 - alpha); stop when T' < 1e-4 (this Gaussian excluded)
 //   C    += alpha T rgb; T = T'
-// CTAs take tiles heaviest first (k_tile_order).  The CTA leaves once all
-// 256 pixels have stopped.  Modes: canonical (every
-// pixel of the tile, alpha first, then the alpha* test; for the
-// filtered-vs-unfiltered comparison) and the Eq. 5 lookup table for e^rho.
+// CTAs take tiles heaviest first (k_tile_order).  Modes: canonical (every
+// record at every pixel of the tile, alpha first, then the alpha* test; for
+// the filtered-vs-unfiltered comparison) and the Eq. 5 lookup table for e^rho.
 #include "vgr_internal.cuh"
 #include "vgr_launch.h"
 
@@ -29,7 +31,49 @@ namespace vgr {
 
 constexpr int BL_THREADS = TILE * TILE;  // 256, one pixel each
 constexpr int BL_WARPS = BL_THREADS / 32;
-constexpr int BL_BATCH = 256;
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+struct BlendPixel {
+    float fxp, fyp;
+    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
+    bool done;
+    uint32_t evals = 0, contribs = 0;
+};
+
+// One record at one pixel; returns false once the pixel has stopped.
+template <int MODE>
+__device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& A, const float4& B, const float4* __restrict__ sC,
+                                           uint32_t k, float rho, const float* s_lut, uint32_t m, float lut_scale) {
+    ++p.evals;
+    float alpha;
+    if (MODE == 1) {  // canonical: Eq. 3, then the alpha* test
+        alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
+        if (alpha < ALPHA_MIN) return true;
+    } else {
+        if (rho < B.y) return true;  // Eq. 4 before Eq. 3
+        if (MODE == 0) {
+            alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
+        } else {  // Eq. 5: nearest of m intervals over [-5.55, 0]
+            const uint32_t idx = min(m, (uint32_t)__float2int_rn(rho * lut_scale));
+            alpha = fminf(ALPHA_MAX, B.z * s_lut[idx]);
+        }
+    }
+    const float Tn = p.T * (1.f - alpha);
+    if (Tn < T_MIN) { p.done = true; return false; }
+    const float w = alpha * p.T;
+    const float4 C4 = sC[k];
+    p.cr = fmaf(w, C4.x, p.cr);
+    p.cg = fmaf(w, C4.y, p.cg);
+    p.cb = fmaf(w, C4.z, p.cb);
+    p.T = Tn;
+    ++p.contribs;
+    return true;
+}
+
+__device__ __forceinline__ float blend_rho(const BlendPixel& p, const float4& A, const float4& B) {
+    const float dx = A.x - p.fxp, dy = A.y - p.fyp;
+    return fmaf(A.z * dx, dx, fmaf(B.x * dy, dy, A.w * dx * dy));
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict__ tile_order,
@@ -41,107 +85,89 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
                                                       const FrameParams* __restrict__ fp,
                                                       const float* __restrict__ lut, float* __restrict__ image,
                                                       Counters* __restrict__ ctr) {
-    __shared__ float4 sA[BL_BATCH];
-    __shared__ float4 sB[BL_BATCH];
-    __shared__ float4 sC[BL_BATCH];
-    __shared__ uint8_t s_mask[BL_BATCH];               // bit w: the record reaches warp w's rows
-    __shared__ uint8_t s_list[BL_WARPS][BL_BATCH];     // per-warp record indices, depth order
+    __shared__ float4 sA[BL_WARPS][32];
+    __shared__ float4 sB[BL_WARPS][32];
+    __shared__ float4 sC[BL_WARPS][32];
     __shared__ float s_lut[260];
     const uint32_t W = fp->width, H = fp->height, TW = fp->tiles_x;
     const uint32_t tile = tile_order[blockIdx.x];  // heaviest tiles first
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t px = (tile % TW) * TILE + (threadIdx.x & (TILE - 1));
+    const uint32_t px = (tile % TW) * TILE + (lane & (TILE - 1));
     const uint32_t ty0 = (tile / TW) * TILE;
-    const uint32_t py = ty0 + (threadIdx.x / TILE);
+    const uint32_t py = ty0 + 2 * warp + (lane >> 4);
     const bool inside = px < W && py < H;
-    const float fxp = (float)px + 0.5f, fyp = (float)py + 0.5f;
-    const float row0 = (float)ty0 + 0.5f;  // centre of the tile's first pixel row
+    const float rlo = (float)(ty0 + 2 * warp) + 0.5f;  // centre of the warp's first row
     uint32_t m = 0;
     float lut_scale = 0.f;
     if (MODE == 2) {
         m = fp->lut_size;
         lut_scale = -(float)m / 5.55f;
         for (uint32_t i = threadIdx.x; i <= m; i += BL_THREADS) s_lut[i] = lut[i];
+        __syncthreads();
     }
     const uint2 rg = ranges[tile];
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-    bool done = !inside;
-    uint32_t evals = 0;
-    for (uint32_t b = rg.x; b < rg.y; b += BL_BATCH) {
-        if (__syncthreads_and(done)) break;
-        const uint32_t j = b + threadIdx.x;
-        uint32_t mask = 0;
+    BlendPixel p;
+    p.fxp = (float)px + 0.5f;
+    p.fyp = (float)py + 0.5f;
+    p.done = !inside;
+    float4* wA = sA[warp];
+    float4* wB = sB[warp];
+    float4* wC = sC[warp];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 nA = z4, nB = z4, nC = z4;
+    {
+        const uint32_t j = rg.x + lane;
         if (j < rg.y) {
             const uint32_t rk = pair_rank[j];
-            const float4 A = srecA[rk];
-            const float4 B = srecB[rk];
-            sA[threadIdx.x] = A;
-            sB[threadIdx.x] = B;
-            sC[threadIdx.x] = srecC[rk];
-            if (MODE == 1) {
-                mask = 0xFFu;
-            } else {
-                // rows r with |row0 + r - v| <= half-height, as row pairs (warps)
-                const float lo = fmaxf(0.f, ceilf(A.y - B.w - row0));
-                const float hi = fminf((float)(TILE - 1), floorf(A.y + B.w - row0));
-                if (lo <= hi) {
-                    const uint32_t w0 = (uint32_t)lo >> 1, w1 = (uint32_t)hi >> 1;
-                    mask = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
-                }
-            }
+            nA = srecA[rk]; nB = srecB[rk]; nC = srecC[rk];
         }
-        s_mask[threadIdx.x] = (uint8_t)mask;
-        __syncthreads();
-        // this warp's records, in depth order
-        uint32_t n = 0;
-#pragma unroll
-        for (int c = 0; c < BL_BATCH / 32; ++c) {
-            const bool bit = (s_mask[c * 32 + lane] >> warp) & 1u;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
-            if (bit) s_list[warp][n + __popc(bal & lanemask_lt())] = (uint8_t)(c * 32 + lane);
-            n += __popc(bal);
+    }
+    for (uint32_t b = rg.x; b < rg.y; b += 32) {
+        if (__all_sync(FULL, p.done)) break;
+        const float4 A = nA, B = nB, C = nC;
+        bool hit = b + lane < rg.y;
+        if (MODE != 1) hit = hit && (A.y - B.w <= rlo + 1.0f) && (A.y + B.w >= rlo);
+        const uint32_t hits = __ballot_sync(FULL, hit);
+        if (hit) {
+            const uint32_t s = __popc(hits & lanemask_lt());
+            wA[s] = A; wB[s] = B; wC[s] = C;
+        }
+        {   // next 32 records in flight while these are walked
+            const uint32_t j = b + 32 + lane;
+            if (j < rg.y) {
+                const uint32_t rk = pair_rank[j];
+                nA = srecA[rk]; nB = srecB[rk]; nC = srecC[rk];
+            }
         }
         __syncwarp();
-        if (!done) {
-            for (uint32_t i = 0; i < n; ++i) {
-                const uint32_t k = s_list[warp][i];
-                const float4 A = sA[k];
-                const float dx = A.x - fxp, dy = A.y - fyp;
-                const float4 B = sB[k];
-                const float rho = fmaf(A.z * dx, dx, fmaf(B.x * dy, dy, A.w * dx * dy));
-                ++evals;
-                float alpha;
-                if (MODE == 1) {  // canonical: Eq. 3, then the alpha* test
-                    alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
-                    if (alpha < ALPHA_MIN) continue;
-                } else {
-                    if (rho < B.y) continue;  // Eq. 4 before Eq. 3
-                    if (MODE == 0) {
-                        alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
-                    } else {  // Eq. 5: nearest of m intervals over [-5.55, 0]
-                        const uint32_t idx = min(m, (uint32_t)__float2int_rn(rho * lut_scale));
-                        alpha = fminf(ALPHA_MAX, B.z * s_lut[idx]);
-                    }
-                }
-                const float Tn = T * (1.f - alpha);
-                if (Tn < T_MIN) { done = true; break; }
-                const float w = alpha * T;
-                const float4 C4 = sC[k];
-                cr = fmaf(w, C4.x, cr);
-                cg = fmaf(w, C4.y, cg);
-                cb = fmaf(w, C4.z, cb);
-                T = Tn;
+        const uint32_t nh = __popc(hits);
+        if (!p.done) {
+            uint32_t i = 0;
+            for (; i + 2 <= nh; i += 2) {
+                const float4 A0 = wA[i], B0 = wB[i], A1 = wA[i + 1], B1 = wB[i + 1];
+                const float r0 = blend_rho(p, A0, B0), r1 = blend_rho(p, A1, B1);
+                if (!blend_step<MODE>(p, A0, B0, wC, i, r0, s_lut, m, lut_scale)) break;
+                if (!blend_step<MODE>(p, A1, B1, wC, i + 1, r1, s_lut, m, lut_scale)) break;
+            }
+            if (!p.done && i < nh) {
+                const float4 A0 = wA[i], B0 = wB[i];
+                blend_step<MODE>(p, A0, B0, wC, i, blend_rho(p, A0, B0), s_lut, m, lut_scale);
             }
         }
+        __syncwarp();
     }
     if (inside) {
         float* o = image + ((size_t)py * W + px) * 3;
-        o[0] = cr;
-        o[1] = cg;
-        o[2] = cb;
+        o[0] = p.cr;
+        o[1] = p.cg;
+        o[2] = p.cb;
     }
-    const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, evals);
-    if (lane == 0 && wsum) atomicAdd(&ctr->pix_evals, (unsigned long long)wsum);
+    const uint32_t wsum = __reduce_add_sync(FULL, p.evals);
+    const uint32_t csum = __reduce_add_sync(FULL, p.contribs);
+    if (lane == 0 && wsum) {
+        atomicAdd(&ctr->pix_evals, (unsigned long long)wsum);
+        atomicAdd(&ctr->pix_contribs, (unsigned long long)csum);
+    }
 }
 
 void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_rank,

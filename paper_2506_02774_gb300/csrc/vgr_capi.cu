@@ -84,6 +84,16 @@ struct vgr_hierarchy {
     int num_sms = 0;
 };
 
+// A submitted frame, kept until vgr_finish_frame.
+struct PendingFrame {
+    vgr_camera cam{};
+    float tau = 0.f, f = 0.f, k = 0.f;
+    bool scratch = false;
+    int tile_passes = 1;
+    uint32_t kernels = 0;
+    float* host = nullptr;
+};
+
 struct vgr_view {
     vgr_hierarchy* h = nullptr;
     vgr_view_opts opts{};
@@ -134,6 +144,17 @@ struct vgr_view {
     int last_tile_buf = 0;
     uint32_t last_n_cut = 0, last_n_vis = 0, last_n_front = 0;
     uint64_t last_n_pairs = 0;
+    // captured frames, one per (top-down cut?, buffer parity); every kernel
+    // argument they hold is a buffer address or a size fixed by the tile
+    // grid, and the per-frame values travel through fp_host (read by the
+    // captured host-to-device copy at replay), so a graph stays valid until a
+    // buffer is reallocated or the tile grid changes
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    uint32_t graph_tiles = 0;
+    // frame in flight between submit and finish
+    bool pending = false;
+    PendingFrame pend;
+    cudaEvent_t done_ev = nullptr;
     uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
 };
 
@@ -369,7 +390,14 @@ vgr_status vgr_hierarchy_info(const vgr_hierarchy* h, uint64_t* bytes, uint32_t*
 // ------------------------------------------------------------------ views
 namespace {
 
+void drop_graphs(vgr_view* v) {
+    for (auto& row : v->graph)
+        for (auto& g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
 void free_vis(vgr_view* v) {
+    drop_graphs(v);
     dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
     dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
@@ -398,6 +426,7 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
 }
 
 void free_pairs(vgr_view* v) {
+    drop_graphs(v);
     for (int i = 0; i < 2; ++i) { dfree(v->pairK[i]); dfree(v->pairV[i]); }
     v->pair_bytes = 0;
 }
@@ -417,6 +446,7 @@ vgr_status alloc_pairs(vgr_view* v, uint64_t cap) {
 }
 
 void free_cut(vgr_view* v) {
+    drop_graphs(v);
     dfree(v->cut[0]); dfree(v->cut[1]); dfree(v->front_list);
     v->cut_bytes = 0;
 }
@@ -437,6 +467,7 @@ vgr_status alloc_cut(vgr_view* v, uint32_t cap) {
 
 // look-back word regions; sized from the current capacities
 vgr_status alloc_status(vgr_view* v) {
+    drop_graphs(v);
     dfree(v->status);
     const uint32_t RT = radix_tile();
     v->st_compact = 0;
@@ -457,6 +488,7 @@ vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
     const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
     const uint64_t px = (uint64_t)W * H, tiles = (uint64_t)TW * TH;
     if (px <= v->cap_pixels && tiles <= v->cap_tiles) return VGR_OK;
+    drop_graphs(v);
     dfree(v->image);
     dfree(v->ranges);
     dfree(v->tile_order);
@@ -475,6 +507,7 @@ vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
 }
 
 void destroy_view(vgr_view* v) {
+    drop_graphs(v);
     free_vis(v);
     free_pairs(v);
     free_cut(v);
@@ -486,6 +519,7 @@ void destroy_view(vgr_view* v) {
     if (v->vstate_host) cudaFreeHost(v->vstate_host);
     for (auto& e : v->ev)
         if (e) cudaEventDestroy(e);
+    if (v->done_ev) cudaEventDestroy(v->done_ev);
     if (v->own_stream && v->stream) cudaStreamDestroy(v->stream);
     delete v;
 }
@@ -558,6 +592,10 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
         cudaError_t ce = cudaEventCreate(&e);
         if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
     }
+    {
+        cudaError_t ce = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
+        if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
+    }
     // Eq. 5 table: entry i = e^(-5.55 i / m), i = 0..m
     {
         float host_lut[260] = {0};
@@ -581,7 +619,34 @@ vgr_status vgr_destroy_view(vgr_view* v) {
 
 vgr_status vgr_reset_view(vgr_view* v) {
     if (!v) return fail(VGR_E_INVALID, "null view");
+    if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is in flight");
     v->has_prev = false;
+    return VGR_OK;
+}
+
+vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* opts, uint32_t width,
+                                   uint32_t height, uint64_t* bytes) {
+    if (!h || !bytes) return fail(VGR_E_INVALID, "null argument");
+    vgr_view_opts o;
+    if (opts) o = *opts;
+    else vgr_default_view_opts(&o);
+    // the allocations of vgr_create_view and of the first frame at this size
+    const uint64_t N = h->n_nodes;
+    const uint64_t cap_cut = std::min<uint64_t>(N, o.cut_capacity ? o.cut_capacity : std::max<uint64_t>(1u << 20, N / 4));
+    const uint64_t cap_vis = cap_cut;
+    const uint64_t cap_pairs = o.pair_capacity ? o.pair_capacity : 2 * cap_vis;
+    const uint64_t TW = cut_compact_tile_words();
+    const uint64_t n_words = ((N + 31) / 32 + TW - 1) / TW * TW;
+    const uint64_t per_vis = 3 * sizeof(uint32_t) + sizeof(uint2) + 3 * sizeof(float4) /* visible SoA */ +
+                             4 * sizeof(uint32_t) /* depth-sort ping-pong */ + 3 * sizeof(float4) /* rank records */;
+    const uint64_t RT = radix_tile();
+    const uint64_t status_words = 2 * (cut_compact_tiles((uint32_t)n_words) + 1) + ceil_div(cap_vis, emit_tile()) + 1 +
+                                  4 * (ceil_div(cap_vis, RT) + 1) * 256 + 4 * (ceil_div(cap_pairs, RT) + 1) * 256;
+    const uint64_t tiles = (uint64_t)((width + TILE - 1) / TILE) * ((height + TILE - 1) / TILE);
+    uint64_t b = 3 * 4 * cap_cut + per_vis * cap_vis + 4 * 4 * cap_pairs + 2 * 4 * n_words + 2 * 4 * N +
+                 sizeof(Counters) + sizeof(ViewState) + sizeof(FrameParams) + 260 * 4 + 8 * status_words;
+    b += (uint64_t)width * height * 3 * 4 + tiles * (sizeof(uint2) + 4);
+    *bytes = b;
     return VGR_OK;
 }
 
@@ -601,6 +666,12 @@ int tile_passes_for(uint32_t n_tiles) {
     int bits = 0;
     while (bits < 32 && ((uint64_t)1 << bits) <= n_tiles) ++bits;
     return std::max(1, (bits + 7) / 8);
+}
+
+uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
+    const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
+    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
+           1u /*emit*/ + (uint32_t)tile_passes + 2u /*ranges, tile order*/ + 1u /*blend*/;
 }
 
 // Enqueue one frame.  'scratch' selects the top-down cut.  Returns the
@@ -666,9 +737,41 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_N_STAGES);
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
-    const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
-    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
-           1u /*emit*/ + (uint32_t)tile_passes + 2u /*ranges, tile order*/ + 1u /*blend*/;
+    return frame_kernels(v, scratch, tile_passes);
+}
+
+// One frame on the view's stream: the plain launch sequence, or (use_graph,
+// no stage timing) the replay of the captured sequence for this
+// (top-down?, parity) pair, captured on first use.
+vgr_status run_frame(vgr_view* v, bool scratch, int tile_passes, uint32_t n_tiles, uint32_t* kernels) {
+    if (!v->opts.use_graph || v->opts.timing) {
+        *kernels += enqueue_frame(v, scratch, tile_passes);
+        VGR_CK(cudaGetLastError());
+        return VGR_OK;
+    }
+    if (v->graph_tiles != n_tiles) {
+        drop_graphs(v);
+        v->graph_tiles = n_tiles;
+    }
+    cudaGraphExec_t& ge = v->graph[scratch ? 1 : 0][v->parity];
+    if (!ge) {
+        VGR_CK(cudaStreamBeginCapture(v->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_frame(v, scratch, tile_passes);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(v->stream, &g);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge = nullptr;
+            cudaGetLastError();
+            return fail(VGR_E_CUDA, "frame capture: %s", cudaGetErrorString(e));
+        }
+    }
+    v->last_tile_buf = tile_passes & 1;
+    VGR_CK(cudaGraphLaunch(ge, v->stream));
+    *kernels += frame_kernels(v, scratch, tile_passes);
+    return VGR_OK;
 }
 
 vgr_status check_camera(const vgr_camera* c, float tau) {
@@ -688,84 +791,121 @@ vgr_status check_camera(const vgr_camera* c, float tau) {
     return VGR_OK;
 }
 
-vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
+void fill_params(vgr_view* v, const vgr_camera* cam, float k) {
+    const uint32_t W = cam->width, H = cam->height;
+    FrameParams& p = *v->fp_host;
+    memcpy(p.R, cam->R, sizeof(p.R));
+    memcpy(p.pos, cam->pos, sizeof(p.pos));
+    p.fx = cam->fx; p.fy = cam->fy; p.cx = cam->cx; p.cy = cam->cy;
+    p.z_near = cam->z_near;
+    p.k = k;
+    p.limx = 1.3f * (0.5f * (float)W / cam->fx);
+    p.limy = 1.3f * (0.5f * (float)H / cam->fy);
+    p.width_f = (float)W; p.height_f = (float)H;
+    p.width = W; p.height = H;
+    p.tiles_x = (W + TILE - 1) / TILE; p.tiles_y = (H + TILE - 1) / TILE;
+    p.epoch = ++v->epoch;  // fresh look-back tags for every launch sequence
+    if ((p.epoch & 0x3FFFFFFFu) == 0) p.epoch = ++v->epoch;
+    p.filter = v->opts.filter; p.exp_mode = v->opts.exp_mode; p.lut_size = v->opts.lut_size;
+    p.lut_step = 5.55f / (float)v->opts.lut_size;
+    p.lod_budget = v->opts.lod_budget;
+    p.max_depth = v->h->max_depth;
+}
+
+// Enqueue the frame (and the image copy to host_rgb, if given) and record the
+// view's completion event; nothing waits.
+vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
     if (!v) return fail(VGR_E_INVALID, "null view");
+    if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is already in flight");
     vgr_status s = check_camera(cam, tau);
     if (s != VGR_OK) return s;
     VGR_CK(cudaSetDevice(v->h->device));
     const uint32_t W = cam->width, H = cam->height;
     if ((s = ensure_image(v, W, H)) != VGR_OK) return s;
     const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
-    const int tile_passes = tile_passes_for(TW * TH);
+    PendingFrame& q = v->pend;
+    q = PendingFrame{};
+    q.cam = *cam;
+    q.tau = tau;
+    q.host = host_rgb;
+    q.tile_passes = tile_passes_for(TW * TH);
     volatile float f = std::max(cam->fx, cam->fy);
     volatile float t = tau / f;
     volatile float k = t * t;
-    bool scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || f != v->prev_f;
-    uint32_t replays = 0, kernels = 0;
-    uint32_t flags = 0;
+    q.f = f;
+    q.k = k;
+    q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
+    fill_params(v, cam, q.k);
+    if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
+    if (host_rgb)
+        VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               v->stream));
+    VGR_CK(cudaEventRecord(v->done_ev, v->stream));
+    v->pending = true;
+    return VGR_OK;
+}
+
+// Wait for the submitted frame, read its status, replay it when the
+// temporal update fell back or a buffer overflowed, and commit the view's
+// temporal state.
+vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    if (!v->pending) return fail(VGR_E_INVALID, "no frame of this view is in flight");
+    v->pending = false;
+    VGR_CK(cudaSetDevice(v->h->device));
+    PendingFrame& q = v->pend;
+    const uint32_t W = q.cam.width, H = q.cam.height;
+    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
     const Counters* ch = reinterpret_cast<const Counters*>(v->ctr_host);
+    VGR_CK(cudaEventSynchronize(v->done_ev));
+    vgr_status s = VGR_OK;
+    uint32_t replays = 0;
     for (int attempt = 0;; ++attempt) {
-        if (attempt > 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt);
-        FrameParams& p = *v->fp_host;
-        memcpy(p.R, cam->R, sizeof(p.R));
-        memcpy(p.pos, cam->pos, sizeof(p.pos));
-        p.fx = cam->fx; p.fy = cam->fy; p.cx = cam->cx; p.cy = cam->cy;
-        p.z_near = cam->z_near;
-        p.k = k;
-        p.limx = 1.3f * (0.5f * (float)W / cam->fx);
-        p.limy = 1.3f * (0.5f * (float)H / cam->fy);
-        p.width_f = (float)W; p.height_f = (float)H;
-        p.width = W; p.height = H; p.tiles_x = TW; p.tiles_y = TH;
-        p.epoch = ++v->epoch;
-        if ((p.epoch & 0x3FFFFFFFu) == 0) p.epoch = ++v->epoch;
-        p.filter = v->opts.filter; p.exp_mode = v->opts.exp_mode; p.lut_size = v->opts.lut_size;
-        p.lut_step = 5.55f / (float)v->opts.lut_size;
-        p.lod_budget = v->opts.lod_budget;
-        p.max_depth = v->h->max_depth;
-        kernels += enqueue_frame(v, scratch, tile_passes);
-        VGR_CK(cudaGetLastError());
-        VGR_CK(cudaStreamSynchronize(v->stream));
-        flags = ch->flags;
+        const uint32_t flags = ch->flags;
         const int cur = v->parity ^ 1;
         const uint32_t n_cut = v->vstate_host->n_cut[cur];
         if (flags & F_SPIN_TIMEOUT) return fail(VGR_E_TIMEOUT, "a look-back wait timed out");
         if (flags & F_NONMONOTONE)
             return fail(VGR_E_NONMONOTONE, "granularity test not monotone: a child expands while its parent does not");
         if (flags & F_OVF_FRONTIER) return fail(VGR_E_OVERFLOW, "frontier overflow");
-        if ((flags & F_LOD_FALLBACK) && !scratch) { scratch = true; ++replays; continue; }
-        if (flags & F_LOD_FALLBACK) return fail(VGR_E_TIMEOUT, "top-down cut exceeded the tree depth");
-        if (flags & F_OVF_CUT) {
+        bool again = false;
+        if ((flags & F_LOD_FALLBACK) && !q.scratch) {
+            q.scratch = true;
+            again = true;
+        } else if (flags & F_LOD_FALLBACK) {
+            return fail(VGR_E_TIMEOUT, "top-down cut exceeded the tree depth");
+        } else if (flags & F_OVF_CUT) {
             const uint32_t nc = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)n_cut + n_cut / 4 + 1024);
             if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_vis(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK)
                 return s;
-            scratch = true;  // the previous cut lived in the old buffers
-            ++replays;
-            continue;
-        }
-        if (flags & F_OVF_PAIRS) {
+            q.scratch = true;  // the previous cut lived in the old buffers
+            again = true;
+        } else if (flags & F_OVF_PAIRS) {
             const uint64_t np = ch->n_cand + ch->n_cand / 4 + 4096;
             if (np >= 0xFFFFFFFFull) return fail(VGR_E_OVERFLOW, "more than 2^32 pairs");
             if ((s = alloc_pairs(v, np)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
-            ++replays;
-            continue;
+            again = true;
         }
-        break;
+        if (!again) break;
+        if (attempt >= 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt + 1);
+        ++replays;
+        fill_params(v, &q.cam, q.k);
+        if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
+        if (q.host)
+            VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                   v->stream));
+        VGR_CK(cudaStreamSynchronize(v->stream));
     }
     const int cur = v->parity ^ 1;
     v->parity = cur;
     v->has_prev = true;
-    v->prev_tau = tau;
-    v->prev_f = f;
+    v->prev_tau = q.tau;
+    v->prev_f = q.f;
     v->last_w = W; v->last_h = H; v->last_tw = TW; v->last_th = TH;
     v->last_n_cut = v->vstate_host->n_cut[cur];
     v->last_n_vis = ch->n_vis;
     v->last_n_front = ch->n_front;
     v->last_n_pairs = ch->n_pairs;
-    if (host_rgb) {
-        VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
-                               v->stream));
-        VGR_CK(cudaStreamSynchronize(v->stream));
-    }
     if (out) {
         memset(out, 0, sizeof(*out));
         out->image = v->image;
@@ -780,16 +920,23 @@ vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
         st.pair_count = ch->n_pairs;
         st.candidate_pairs = ch->n_cand;
         st.nodes_evaluated = ch->nodes_eval;
-        st.lod_from_scratch = scratch ? 1u : 0u;
+        st.lod_from_scratch = q.scratch ? 1u : 0u;
         st.replays = replays;
-        st.kernels = kernels;
+        st.kernels = q.kernels;
         st.pixel_pair_evals = ch->pix_evals;
+        st.pixel_pair_contribs = ch->pix_contribs;
         if (v->opts.timing) {
             for (int i = 0; i < VGR_N_STAGES; ++i) cudaEventElapsedTime(&st.stage_ms[i], v->ev[i], v->ev[i + 1]);
             cudaEventElapsedTime(&st.frame_ms, v->ev[0], v->ev[VGR_N_STAGES]);
         }
     }
     return VGR_OK;
+}
+
+vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
+    vgr_status s = submit_impl(v, cam, tau, host_rgb);
+    if (s != VGR_OK) return s;
+    return finish_impl(v, out);
 }
 
 }  // namespace
@@ -805,8 +952,52 @@ vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, 
     return render_impl(v, cam, tau, host_rgb, out);
 }
 
+vgr_status vgr_submit_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+    return submit_impl(v, cam, tau, host_rgb);
+}
+
+vgr_status vgr_frame_done(vgr_view* v, int* done) {
+    if (!v || !done) return fail(VGR_E_INVALID, "null argument");
+    if (!v->pending) return fail(VGR_E_INVALID, "no frame of this view is in flight");
+    const cudaError_t e = cudaEventQuery(v->done_ev);
+    if (e == cudaErrorNotReady) { *done = 0; return VGR_OK; }
+    if (e != cudaSuccess) return fail(VGR_E_CUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+    *done = 1;
+    return VGR_OK;
+}
+
+vgr_status vgr_finish_frame(vgr_view* v, vgr_frame* out) { return finish_impl(v, out); }
+
+vgr_status vgr_render_batch(vgr_view* const* views, const vgr_camera* cams, const float* taus,
+                            float* const* host_rgb, uint32_t n, vgr_frame* outs) {
+    if (n == 0) return VGR_OK;
+    if (!views || !cams || !taus) return fail(VGR_E_INVALID, "null argument");
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!views[i]) return fail(VGR_E_INVALID, "views[%u] is null", i);
+        for (uint32_t j = 0; j < i; ++j)
+            if (views[j] == views[i]) return fail(VGR_E_INVALID, "views[%u] and views[%u] are the same view", j, i);
+    }
+    // submit every view, then finish them in order; on a failed submission
+    // the views already submitted are still finished
+    uint32_t submitted = 0;
+    vgr_status first = VGR_OK;
+    std::string first_msg;
+    for (; submitted < n; ++submitted) {
+        const vgr_status s = submit_impl(views[submitted], &cams[submitted], taus[submitted],
+                                         host_rgb ? host_rgb[submitted] : nullptr);
+        if (s != VGR_OK) { first = s; first_msg = g_err; break; }
+    }
+    for (uint32_t i = 0; i < submitted; ++i) {
+        const vgr_status s = finish_impl(views[i], outs ? &outs[i] : nullptr);
+        if (s != VGR_OK && first == VGR_OK) { first = s; first_msg = g_err; }
+    }
+    if (first != VGR_OK) g_err = first_msg;
+    return first;
+}
+
 vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     if (!v || !o) return fail(VGR_E_INVALID, "null argument");
+    if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is in flight");
     if (!v->has_prev) return fail(VGR_E_INVALID, "no frame rendered yet");
     memset(o, 0, sizeof(*o));
     o->n_cut = v->last_n_cut;

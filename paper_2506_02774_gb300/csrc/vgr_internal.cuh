@@ -69,12 +69,13 @@ struct Counters {
     unsigned long long n_cand;
     unsigned long long nodes_eval;
     unsigned long long pix_evals;
+    unsigned long long pix_contribs;
     uint32_t tickets[TK_COUNT];
     uint32_t frontier_n[MAX_TREE_DEPTH + 2];
     uint32_t depth_hist[4][256];
     uint32_t tile_hist[4][256];
 };
-constexpr size_t COUNTERS_HEAD = 48;  // bytes read back per frame (n_vis .. pix_evals)
+constexpr size_t COUNTERS_HEAD = 56;  // bytes read back per frame (n_vis .. pix_contribs)
 
 // Persistent per-view values (not cleared per frame).
 struct ViewState {

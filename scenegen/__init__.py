@@ -209,6 +209,33 @@ CONFIGS = {
 }
 
 
+# image sizes of the multi-view and serving workloads
+RESOLUTIONS = {"360p": (640, 360), "720p": (1280, 720), "1080p": (1920, 1080), "1440p": (2560, 1440)}
+
+
+def street_trajectory(name: str, seed: int, frame: int, width: int, height: int) -> dict:
+    """Camera of ``frame`` on a street walk of its own (one per view or
+    client, chosen by ``seed``): a street of the city grid (x- or y-street,
+    index 1..36 of the 40 m grid), a direction and a starting point drawn from
+    ``seed``; the workload's height, speed and yaw law; focal length scaled
+    with the image width (fx = focal * width / the workload's width)."""
+    c = CONFIGS[name]
+    rng = np.random.default_rng(seed)
+    along_x = bool(rng.random() < 0.5)
+    k = int(rng.integers(1, 37))
+    forward = bool(rng.random() < 0.5)
+    s0 = float(rng.uniform(200.0, 1300.0))
+    z = c["start"][2]
+    if along_x:
+        start, heading = (s0, 40.0 * k, z), (0.0 if forward else math.pi)
+    else:
+        start, heading = (40.0 * k, s0, z), (0.5 * math.pi if forward else -0.5 * math.pi)
+    t = frame / c["fps"]
+    pos = np.asarray(start) + c["speed"] * t * np.array([math.cos(heading), math.sin(heading), 0.0])
+    yaw = heading + math.radians(c["yaw_amp_deg"]) * math.sin(2.0 * math.pi * t / c["yaw_period"])
+    return camera(pos, yaw, width, height, c["focal"] * width / c["width"])
+
+
 def make_scene(name: str, n_leaves: int | None = None, seed: int | None = None) -> dict:
     """Generate the named workload's scene (optionally with fewer leaves)."""
     c = CONFIGS[name]

@@ -75,3 +75,45 @@ def test_null_arguments(lib):
     assert lib.vgr_free_hierarchy(None) == _abi.VGR_E_INVALID
     assert lib.vgr_destroy_view(None) == _abi.VGR_E_INVALID
     assert lib.vgr_render_frame(None, None, 3.0, None) == _abi.VGR_E_INVALID
+
+
+def test_ctypes_layout_matches_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler
+    gives the structs of include/vgr.h."""
+    import subprocess
+    from paper_2506_02774_gb300 import _build
+    structs = {"vgr_scene_desc": _abi.SceneDesc, "vgr_camera": _abi.Camera, "vgr_view_opts": _abi.ViewOpts,
+               "vgr_frame_stats": _abi.FrameStats, "vgr_frame": _abi.Frame, "vgr_debug_buffers": _abi.DebugBuffers,
+               "vgr_serve_opts": _abi.ServeOpts, "vgr_request": _abi.Request, "vgr_request_result": _abi.RequestResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vgr.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", _build.INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert int(got["%s.%s" % (cname, f[0])]) == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_async_and_server_argument_errors(lib):
+    assert lib.vgr_submit_frame(None, None, 3.0, None) == _abi.VGR_E_INVALID
+    d = ctypes.c_int32()
+    assert lib.vgr_frame_done(None, ctypes.byref(d)) == _abi.VGR_E_INVALID
+    assert lib.vgr_finish_frame(None, None) == _abi.VGR_E_INVALID
+    assert lib.vgr_render_batch(None, None, None, None, 0, None) == _abi.VGR_OK  # nothing to do
+    assert lib.vgr_render_batch(None, None, None, None, 2, None) == _abi.VGR_E_INVALID
+    o = _abi.ServeOpts()
+    lib.vgr_default_serve_opts(ctypes.byref(o))
+    assert o.n_clients == 1 and o.view.use_graph == 1 and o.view.temporal == 1
+    s = ctypes.c_void_p()
+    assert lib.vgr_create_server(None, ctypes.byref(o), ctypes.byref(s)) == _abi.VGR_E_INVALID
+    assert lib.vgr_destroy_server(None) == _abi.VGR_E_INVALID
+    assert lib.vgr_serve_trace(None, None, 0, None) == _abi.VGR_E_INVALID
