@@ -161,7 +161,8 @@ typedef struct {
     const float* rank_rgb;        /* [4 n_visible] r g b 0 in depth-rank order */
     const uint32_t* depth_order;  /* [n_front] in-front index by depth rank; the first n_visible are visible */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
-    const uint32_t* pair_rank;    /* [n_pairs] depth rank of the Gaussian */
+    const uint32_t* pair_val;     /* [n_pairs] depth rank << 8 | row mask (bit w: the footprint box reaches
+                                     pixel row 2w or 2w + 1 of the tile; all ones in the canonical mode) */
     const uint32_t* tile_range;   /* [2 tiles] start, end into the pair list */
 } vgr_debug_buffers;
 

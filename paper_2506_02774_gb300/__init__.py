@@ -234,13 +234,14 @@ class View:
         vis = ntile > 0
         compact = np.cumsum(vis) - 1
         order = u32(d.depth_order, nf)[:nv]
+        pval = u32(d.pair_val, npairs)
         assert vis[order].all(), "the first n_visible depth ranks must be visible entries"
         return dict(n_cut=nc, n_front=nf, n_visible=nv, n_pairs=npairs, tiles=(int(d.tiles_x), int(d.tiles_y)),
                     cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nf)[vis], vis_depth=u32(d.vis_depth, nf)[vis],
                     vis_ntile=ntile[vis], vis_rect=u32(d.vis_rect, 2 * nf).reshape(nf, 2)[vis],
                     vis_recA=f32(d.vis_recA, (nf, 4))[vis], vis_recB=f32(d.vis_recB, (nf, 4))[vis],
                     rank_rgb=f32(d.rank_rgb, (nv, 4)), depth_order=compact[order].astype(np.uint32),
-                    pair_tile=u32(d.pair_tile, npairs), pair_rank=u32(d.pair_rank, npairs),
+                    pair_tile=u32(d.pair_tile, npairs), pair_rank=pval >> 8, pair_rowmask=pval & 0xFF,
                     tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
 
     def close(self):

@@ -4,18 +4,20 @@
 //
 // One CTA of 256 threads per tile, one pixel per thread; warp w shades pixel
 // rows 2w and 2w+1 and walks the tile's pair range on its own (no CTA-wide
-// barrier): 32 records at a time (48 bytes each, depth-rank order), it keeps
-// those whose opacity-aware footprint box reaches one of its two rows -- the
-// box half-height is part of the record, and outside the box
-// rho < ln alpha* - ln theta holds with a margin, so a skipped record would
-// have failed the Eq. 4 test at every pixel of those rows -- stages them in
-// its own slice of shared memory and walks them in order, two at a time for
-// instruction-level parallelism.  The next 32 records are loaded while the
-// current ones are walked; the eight warps of a tile read the same records,
-// so all but the first read of each record hit L1.  A warp stops when its 32
-// pixels have stopped; tiles crossing the horizon (tens of thousands of
-// small distant Gaussians, each reaching one or two rows) cost each warp a
-// fraction of the pairs.  Per pixel:
+// barrier).  Each pair value carries the Gaussian's depth rank and its row
+// mask in the tile (set by the emission from the footprint box: outside the
+// box rho < ln alpha* - ln theta holds with a margin, so a pair whose box
+// misses the warp's two rows would fail the Eq. 4 test at every one of its
+// pixels).  The warp reads 32 pair values at a time (coalesced), keeps those
+// with its row bit, and copies their 48-byte records (depth-rank order) with
+// cp.async into its own double-buffered slice of shared memory; the copies
+// of the next 32 pairs are in flight while the current ones are walked, two
+// at a time for instruction-level parallelism.  Records are read only for
+// the pairs a warp needs, and the eight warps of a tile share them through
+// L1.  A warp stops when its 32 pixels have stopped; tiles crossing the
+// horizon (tens of thousands of small distant Gaussians, each reaching one
+// or two rows) cost each warp a scan of 4-byte values and a fraction of the
+// records.  Per pixel:
 //   rho   = A dx^2 + B dx dy + C dy^2      (A = -a/2, B = -b, C = -c/2)
 //   skip if rho < ln alpha* - ln theta     (Eq. 4: alpha < alpha*, no exp)
 //   alpha = min(0.99, theta e^rho)         (Eq. 3)
@@ -23,7 +25,8 @@
 //   C    += alpha T rgb; T = T'
 // CTAs take tiles heaviest first (k_tile_order).  Modes: canonical (every
 // record at every pixel of the tile, alpha first, then the alpha* test; for
-// the filtered-vs-unfiltered comparison) and the Eq. 5 lookup table for e^rho.
+// the filtered-vs-unfiltered comparison; its row masks are all ones) and the
+// Eq. 5 lookup table for e^rho.
 #include "vgr_internal.cuh"
 #include "vgr_launch.h"
 
@@ -75,19 +78,26 @@ __device__ __forceinline__ float blend_rho(const BlendPixel& p, const float4& A,
     return fmaf(A.z * dx, dx, fmaf(B.x * dy, dy, A.w * dx * dy));
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <int MODE>
 __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict__ tile_order,
                                                       const uint2* __restrict__ ranges,
-                                                      const uint32_t* __restrict__ pair_rank,
+                                                      const uint32_t* __restrict__ pair_val,
                                                       const float4* __restrict__ srecA,
                                                       const float4* __restrict__ srecB,
                                                       const float4* __restrict__ srecC,
                                                       const FrameParams* __restrict__ fp,
                                                       const float* __restrict__ lut, float* __restrict__ image,
                                                       Counters* __restrict__ ctr) {
-    __shared__ float4 sA[BL_WARPS][32];
-    __shared__ float4 sB[BL_WARPS][32];
-    __shared__ float4 sC[BL_WARPS][32];
+    // [buffer][record part A, B, C][warp][slot]
+    __shared__ __align__(16) float4 sbuf[2][3][BL_WARPS][32];
     __shared__ float s_lut[260];
     const uint32_t W = fp->width, H = fp->height, TW = fp->tiles_x;
     const uint32_t tile = tile_order[blockIdx.x];  // heaviest tiles first
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     const uint32_t ty0 = (tile / TW) * TILE;
     const uint32_t py = ty0 + 2 * warp + (lane >> 4);
     const bool inside = px < W && py < H;
-    const float rlo = (float)(ty0 + 2 * warp) + 0.5f;  // centre of the warp's first row
+    const uint32_t wbit = 1u << warp;
     uint32_t m = 0;
     float lut_scale = 0.f;
     if (MODE == 2) {
@@ -110,37 +120,33 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     p.fxp = (float)px + 0.5f;
     p.fyp = (float)py + 0.5f;
     p.done = !inside;
-    float4* wA = sA[warp];
-    float4* wB = sB[warp];
-    float4* wC = sC[warp];
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 nA = z4, nB = z4, nC = z4;
-    {
-        const uint32_t j = rg.x + lane;
-        if (j < rg.y) {
-            const uint32_t rk = pair_rank[j];
-            nA = srecA[rk]; nB = srecB[rk]; nC = srecC[rk];
-        }
-    }
-    for (uint32_t b = rg.x; b < rg.y; b += 32) {
-        if (__all_sync(FULL, p.done)) break;
-        const float4 A = nA, B = nB, C = nC;
-        bool hit = b + lane < rg.y;
-        if (MODE != 1) hit = hit && (A.y - B.w <= rlo + 1.0f) && (A.y + B.w >= rlo);
+    // stage the records of the pairs in [b, b + 32) that reach this warp's rows
+    auto issue = [&](uint32_t v, int buf) -> uint32_t {
+        const bool hit = (v & wbit) != 0u;  // entries past the range hold 0
         const uint32_t hits = __ballot_sync(FULL, hit);
         if (hit) {
-            const uint32_t s = __popc(hits & lanemask_lt());
-            wA[s] = A; wB[s] = B; wC[s] = C;
+            const uint32_t slot = __popc(hits & lanemask_lt()), rk = v >> 8;
+            cp_async16(&sbuf[buf][0][warp][slot], srecA + rk);
+            cp_async16(&sbuf[buf][1][warp][slot], srecB + rk);
+            cp_async16(&sbuf[buf][2][warp][slot], srecC + rk);
         }
-        {   // next 32 records in flight while these are walked
-            const uint32_t j = b + 32 + lane;
-            if (j < rg.y) {
-                const uint32_t rk = pair_rank[j];
-                nA = srecA[rk]; nB = srecB[rk]; nC = srecC[rk];
-            }
-        }
+        cp_async_commit();
+        return hits;
+    };
+    uint32_t b = rg.x;
+    uint32_t hits_cur = issue(b + lane < rg.y ? pair_val[b + lane] : 0u, 0);
+    uint32_t v_next = b + 32 + lane < rg.y ? pair_val[b + 32 + lane] : 0u;
+    int buf = 0;
+    for (; b < rg.y; b += 32) {
+        if (__all_sync(FULL, p.done)) break;
+        const uint32_t hits_next = issue(v_next, buf ^ 1);  // next 32 pairs in flight during this walk
+        v_next = b + 64 + lane < rg.y ? pair_val[b + 64 + lane] : 0u;
+        cp_async_wait<1>();  // this chunk's copies (all but the newest group)
         __syncwarp();
-        const uint32_t nh = __popc(hits);
+        const float4* wA = sbuf[buf][0][warp];
+        const float4* wB = sbuf[buf][1][warp];
+        const float4* wC = sbuf[buf][2][warp];
+        const uint32_t nh = __popc(hits_cur);
         if (!p.done) {
             uint32_t i = 0;
             for (; i + 2 <= nh; i += 2) {
@@ -154,8 +160,11 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
                 blend_step<MODE>(p, A0, B0, wC, i, blend_rho(p, A0, B0), s_lut, m, lut_scale);
             }
         }
-        __syncwarp();
+        __syncwarp();  // the walk is done with this buffer before it is refilled
+        buf ^= 1;
+        hits_cur = hits_next;
     }
+    cp_async_wait<0>();
     if (inside) {
         float* o = image + ((size_t)py * W + px) * 3;
         o[0] = p.cr;
@@ -170,16 +179,16 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     }
 }
 
-void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_rank,
+void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
                   const float4* srecA,
                   const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s) {
     if (filter == VGR_FILTER_CANONICAL)
-        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
     else if (exp_mode == VGR_EXP_LUT)
-        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
     else
-        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_rank, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
 }
 
 }  // namespace vgr

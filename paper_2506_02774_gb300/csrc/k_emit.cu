@@ -12,10 +12,17 @@
 // each slot the tile-level form of Eq. 4 (paper Sec. 4.2) decides: a kept
 // slot gets key = tile id, a dropped one the sentinel key, which the stable
 // tile sort moves behind every real pair.  The slot's value is the
-// Gaussian's depth rank; the Gaussian's record (mean, conic, threshold,
+// Gaussian's depth rank << 8 | its row mask in that tile: bit w is set when
+// the footprint box reaches pixel row 2w or 2w+1 of the tile (the rows the
+// blend's warp w shades; outside the box the Eq. 4 test fails at every
+// pixel), so the blend skips a pair without reading its record.  Ranks
+// therefore take 24 bits: a frame with more visible Gaussians reports an
+// overflow.  The Gaussian's record (mean, conic, threshold,
 // opacity, colour) is copied to rank order so the blend reads the records of a tile
 // at increasing addresses.  The digit histograms of the tile sort are
 // accumulated here as well.
+#include <cuda_fp16.h>
+
 #include "vgr_internal.cuh"
 #include "vgr_launch.h"
 #include "vgr_tiletest.cuh"
@@ -40,8 +47,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
     __shared__ uint32_t s_off[EM_TILE + 1];   // candidate counts, then exclusive slot offsets
     __shared__ float4 s_g[EM_TILE];           // u v a b
     __shared__ float4 s_h[EM_TILE];           // c rx ry thre
-    __shared__ uint32_t s_rect[EM_TILE];      // x0 | y0 << 16
-    __shared__ uint16_t s_w[EM_TILE];         // candidate rectangle width
+    __shared__ uint32_t s_rect[EM_TILE];      // x0 | y0 << 10 | width << 20 (tiles; 16384-px images: < 2^10)
+    __shared__ __half s_hh[EM_TILE];          // footprint half-height, rounded up
     __shared__ uint32_t s_hist[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     const uint32_t n_vis = min(ctr->n_vis, cap_vis);
@@ -51,6 +58,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
     const float Wf = fp->width_f, Hf = fp->height_f;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     uint32_t kept = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_vis > MAX_RANKS) atomicOr(&ctr->flags, F_OVF_VIS);
     __syncthreads();
 
     for (;;) {
@@ -77,8 +85,9 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
                 const float ca = -2.0f * A.z, cb = -A.w, cc = -2.0f * B.x;
                 s_g[q] = make_float4(A.x, A.y, ca, cb);
                 s_h[q] = make_float4(cc, __fdiv_rn(-cb, ca), __fdiv_rn(-cb, cc), B.y - TILE_EPS);
-                s_rect[q] = rect.x;
-                s_w[q] = (uint16_t)((rect.y & 0xFFFFu) - (rect.x & 0xFFFFu) + 1u);
+                const uint32_t x0 = rect.x & 0xFFFFu, y0 = rect.x >> 16;
+                s_rect[q] = x0 | (y0 << 10) | (((rect.y & 0xFFFFu) - x0 + 1u) << 20);
+                s_hh[q] = __float2half_ru(B.w);
             }
             s_off[q] = area;
         }
@@ -110,20 +119,31 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
             }
             const uint32_t g = lo;
             const uint32_t local = j - s_off[g];
-            const uint32_t w = s_w[g];
-            const int tx = (int)(s_rect[g] & 0xFFFFu) + (int)(local % w);
-            const int ty = (int)(s_rect[g] >> 16) + (int)(local / w);
+            const uint32_t rc = s_rect[g];
+            const uint32_t w = rc >> 20;
+            const int tx = (int)(rc & 0x3FFu) + (int)(local % w);
+            const int ty = (int)((rc >> 10) & 0x3FFu) + (int)(local / w);
             bool keep = true;
+            uint32_t rows = 0xFFu;
             if (!canonical) {
                 const float4 G = s_g[g], Hh = s_h[g];
                 keep = tile_keep(G.x, G.y, G.z, G.w, Hh.x, Hh.y, Hh.z, Hh.w, tx, ty, Wf, Hf);
+                // tile rows r with |row0 + r - v| <= half-height, as row pairs
+                const float row0 = (float)(ty * TILE) + 0.5f, hh = __half2float(s_hh[g]);
+                const float lo = fmaxf(0.f, ceilf(G.y - hh - row0));
+                const float hi = fminf((float)(TILE - 1), floorf(G.y + hh - row0));
+                rows = 0u;
+                if (lo <= hi) {
+                    const uint32_t w0 = (uint32_t)lo >> 1, w1 = (uint32_t)hi >> 1;
+                    rows = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+                }
             }
             const uint32_t key = keep ? (uint32_t)ty * TW + (uint32_t)tx : sentinel;
             kept += keep;
             const uint64_t pos = base + j;
             if (pos < cap) {
                 pair_key[pos] = key;
-                pair_val[pos] = tile * EM_TILE + g;
+                pair_val[pos] = ((tile * EM_TILE + g) << 8) | rows;
                 for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
             }
         }

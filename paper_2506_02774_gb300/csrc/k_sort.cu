@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 //  4. the look-back over earlier tiles gives each digit its global start;
 //  5. every thread writes consecutive staged elements, so each digit's run
 //     is stored contiguously (coalesced).
+constexpr int LB_BATCH = 8;  // look-back words read per round trip
+
 __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
@@ -148,23 +150,41 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __
                 s_val[pos] = val[it];
             }
         }
-        // 4. look-back for digit d over earlier tiles (aggregate already published)
+        // 4. look-back for digit d over earlier tiles (aggregate already
+        // published), LB_BATCH status words per round trip: the words are
+        // read together and consumed in order up to the first inclusive
+        // prefix (done) or the first one not yet published (wait, retry there)
         uint32_t prefix = 0;
         if (tile > 0) {
             const uint32_t ep = epoch & 0x3FFFFFFFu;
             int64_t j = (int64_t)tile - 1;
             uint32_t spins = 0;
-            while (j >= 0) {
-                const unsigned long long w = lb_load(status + (size_t)j * RS_BINS + d);
-                const uint32_t wep = (uint32_t)(w >> 34), fl = (uint32_t)(w >> 32) & 3u;
-                if (wep != ep || fl == 0u) {
+            for (;;) {
+                unsigned long long wv[LB_BATCH];
+#pragma unroll
+                for (int q = 0; q < LB_BATCH; ++q)
+                    wv[q] = j - q >= 0 ? lb_load(status + (size_t)(j - q) * RS_BINS + d) : 0ull;
+                uint32_t consumed = 0;
+                int state = 0;  // 0: all consumed, 1: inclusive prefix reached, 2: wait
+#pragma unroll
+                for (int q = 0; q < LB_BATCH; ++q) {
+                    if (state == 0) {
+                        const uint32_t wep = (uint32_t)(wv[q] >> 34), fl = (uint32_t)(wv[q] >> 32) & 3u;
+                        if (wep != ep || fl == 0u) {
+                            state = 2;
+                        } else {
+                            prefix += (uint32_t)wv[q];
+                            ++consumed;
+                            if (fl == 2u) state = 1;
+                        }
+                    }
+                }
+                if (state == 1) break;
+                j -= consumed;  // tile 0 always holds an inclusive prefix, so j stays >= 0
+                if (state == 2) {
                     if (++spins > SPIN_LIMIT) { atomicOr(&ctr->flags, F_SPIN_TIMEOUT); break; }
                     __nanosleep(20);
-                    continue;
                 }
-                prefix += (uint32_t)w;
-                if (fl == 2u) break;
-                --j;
             }
             lb_store(my, lb_pack(epoch, 2u, prefix + run));
         }

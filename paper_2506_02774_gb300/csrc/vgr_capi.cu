@@ -868,6 +868,7 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         if (flags & F_NONMONOTONE)
             return fail(VGR_E_NONMONOTONE, "granularity test not monotone: a child expands while its parent does not");
         if (flags & F_OVF_FRONTIER) return fail(VGR_E_OVERFLOW, "frontier overflow");
+        if (flags & F_OVF_VIS) return fail(VGR_E_OVERFLOW, "more than 2^24 visible Gaussians in one frame");
         bool again = false;
         if ((flags & F_LOD_FALLBACK) && !q.scratch) {
             q.scratch = true;
@@ -1016,7 +1017,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     o->rank_rgb = reinterpret_cast<const float*>(v->srecC);
     o->depth_order = v->sortV[1];
     o->pair_tile = v->pairK[v->last_tile_buf];
-    o->pair_rank = v->pairV[v->last_tile_buf];
+    o->pair_val = v->pairV[v->last_tile_buf];
     o->tile_range = reinterpret_cast<const uint32_t*>(v->ranges);
     return VGR_OK;
 }

@@ -15,6 +15,7 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr float ALPHA_MIN = 1.0f / 255.0f;    // alpha* (Sec. 3.1 'Rasterization')
 constexpr float LN_ALPHA_MIN = -5.5412635451584260f;  // ln(1/255)
 constexpr float T_MIN = 1e-4f;                // early-termination transmittance
+constexpr uint32_t MAX_RANKS = 1u << 24;        // visible Gaussians per frame (pair value = rank << 8 | row mask)
 constexpr float ALPHA_MAX = 0.99f;            // Eq. 3 clamp
 constexpr float DILATE = 0.3f;                // low-pass added to the 2D covariance
 constexpr float TILE_EPS = 2e-3f;             // slack of the FP32 tile-level test (nats)
@@ -32,7 +33,7 @@ enum : uint32_t {
     F_NONMONOTONE = 2u,    // child expands while the parent does not
     F_SPIN_TIMEOUT = 4u,   // a look-back wait ran out
     F_OVF_CUT = 8u,
-    F_OVF_VIS = 16u,
+    F_OVF_VIS = 16u,       // more visible Gaussians than a pair value's 24-bit rank holds
     F_OVF_PAIRS = 32u,
     F_OVF_FRONTIER = 64u,
 };

@@ -64,7 +64,7 @@ void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs
 void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
 
 // k_blend.cu
-void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_rank,
+void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
                   const float4* srecA,
                   const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);

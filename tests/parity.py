@@ -75,6 +75,25 @@ def _pairkey(tile, node):
     return (np.asarray(tile, np.int64) << 32) | np.asarray(node, np.int64)
 
 
+def _rows_needed(A, B, tile, TW, chunk=8192):
+    """Bit w set when some pixel of rows 2w, 2w+1 of the pair's tile has
+    rho >= thr - 1e-3 (FP64, from the pair's FP32 record)."""
+    out = np.zeros(len(tile), np.int64)
+    c16 = np.arange(16, dtype=np.float64) + 0.5
+    for s0 in range(0, len(tile), chunk):
+        sl = slice(s0, s0 + chunk)
+        t = tile[sl]
+        a, b, c = (A[sl, 2].astype(np.float64), A[sl, 3].astype(np.float64), B[sl, 0].astype(np.float64))
+        dx = A[sl, 0].astype(np.float64)[:, None] - ((t % TW) * 16)[:, None] - c16[None, :]   # [P, col]
+        dy = A[sl, 1].astype(np.float64)[:, None] - ((t // TW) * 16)[:, None] - c16[None, :]  # [P, row]
+        rho = (a[:, None, None] * dx[:, None, :] ** 2 + b[:, None, None] * dx[:, None, :] * dy[:, :, None]
+               + c[:, None, None] * dy[:, :, None] ** 2)                                       # [P, row, col]
+        rows = (rho >= B[sl, 1].astype(np.float64)[:, None, None] - 1e-3).any(axis=2)         # [P, row]
+        pairs = rows[:, 0::2] | rows[:, 1::2]
+        out[sl] = (pairs * (1 << np.arange(8))).sum(axis=1)
+    return out
+
+
 def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     """Stage-by-stage parity of one frame.  With tile_mask, pair checks are
     restricted to the masked tiles (the oracle binned only those)."""
@@ -156,6 +175,17 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
         marg = dict(zip(ckeys.tolist(), ref["cand_margin"].tolist()))
         mm = np.array([marg[int(k)] for k in missing])
         assert np.all(mm < MARGIN_DELTA), mm.max()
+    # ---- row masks: a pair's bit w must be set wherever some pixel of the
+    # tile's rows 2w, 2w+1 passes the Eq. 4 test (or misses it by < 1e-3)
+    # with the pair's own record; otherwise the blend would skip a pixel
+    # the Gaussian contributes to
+    if "pair_rowmask" in dbg and len(pr):
+        TW = int(dbg["tiles"][0])
+        vis = order[pr]
+        need = _rows_needed(A[vis], B[vis], pt, TW)
+        got = dbg["pair_rowmask"].astype(np.int64)
+        bad = (got & need) != need
+        assert not bad.any(), (int(bad.sum()), got[bad][:5], need[bad][:5])
     # ---- per-tile order of the common pairs equals the oracle's
     common = np.intersect1d(gkeys, okeys)
     g_common = gkeys[np.isin(gkeys, common)]
