@@ -140,7 +140,7 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
         preprocess=(4 + 16 + 32 + 52) * F,           # ids, centre, covariance + opacity, records out
         depth_sort=4 * 2 * 8 * F + 4 * F,            # 4 passes x (key+value) read+write, histogram read
         color=4 * F + (4 + 16 + shb) * V + 16 * V,   # culled flags, node, centre, SH; rgb out
-        emit=(4 + 4 + 8 + 32) * V + 32 * V + 8 * P0,  # order, count, rect, records in and out, slots
+        emit=(4 + 4 + 8 + 32) * V + 8 * P0,          # order, count, rect, record halves; slots
         tile_sort=tile_passes * 2 * 8 * P0,
         ranges=4 * P + 8 * (W // 16 + 1) * (H // 16 + 1),
         blend=(4 + 48) * P + 12 * W * H,
@@ -240,6 +240,40 @@ def run_ours(args) -> dict:
     stage_ms /= max(1, n_t)
     view_t.close()
 
+    # ---- the same walk with the reduced-precision store (FP16 SH + BF16
+    # covariance, FP32 arithmetic): second run of the city configuration
+    half_store = None
+    if args.config == "city" and not args.leaves and args.storage == "fp32" and not args.no_half:
+        h16 = vgr.Hierarchy(sc, storage=vgr.STORE_HALF)
+        v16 = vgr.View(h16, stream=stream.cuda_stream, use_graph=not args.no_graph)
+        ms16, _, st16, _ = timed(v16)
+        half_store = dict(value=round(frames / (ms16 / 1e3), 2), unit="frames/s", ms_per_step=round(ms16 / args.steps, 4),
+                          scene_device_gb=round(h16.device_bytes / 1e9, 2),
+                          pairs=round(float(np.mean([s["pair_count"] for s in st16])), 1))
+        v16.close()
+        h16.close()
+
+    # ---- cut reuse between consecutive frames (the motivation of the
+    # temporal update, Sec. 4.1): overlap of the cuts of two consecutive
+    # frames and the nodes each LoD form evaluates for the same frame
+    lod_reuse = None
+    if ws == 1 or rank == 0:
+        vr = vgr.View(h, stream=stream.cuda_stream)
+        vs = vgr.View(h, stream=stream.cuda_stream, temporal=False)
+        i0 = args.warmup + args.steps // 2
+        a = vr.render(cams[i0], tau)
+        ca = a.cut().cpu().numpy().copy()
+        b = vr.render(cams[i0 + 1], tau)
+        cb = b.cut().cpu().numpy()
+        s_ = vs.render(cams[i0 + 1], tau)
+        common = int(np.intersect1d(ca, cb, assume_unique=True).size)
+        lod_reuse = dict(frames="%d, %d" % (i0, i0 + 1), cut=int(cb.size), common_with_previous=common,
+                         overlap=round(common / max(1, cb.size), 5),
+                         nodes_evaluated_temporal=b.stats["nodes_evaluated"],
+                         nodes_evaluated_top_down=s_.stats["nodes_evaluated"])
+        vr.close()
+        vs.close()
+
     # ---- end to end through the host-buffer entry point
     host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
     hp = host_img.data_ptr()
@@ -307,10 +341,14 @@ def run_ours(args) -> dict:
                stage_ms={k: round(v, 4) for k, v in shares.items()},
                stage_gbs={k: round(v, 1) for k, v in hbm_stages.items()},
                counts={k: round(v, 1) for k, v in mean.items()},
+               lod_reuse=lod_reuse,
+               half_store=half_store,
                setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
     view.close()
     if args.config == "city" and not args.leaves and not args.no_served:
-        out["served"] = run_served(sc, h, args.serve_clients, args.serve_rate, args.serve_seconds)
+        out["served"] = run_served(sc, h, args.serve_clients, args.serve_rate, args.serve_seconds,
+                                   [float(x) for x in args.serve_sweep.split(",") if x], args.sweep_seconds,
+                                   args.p99_bound)
         out["p50_ms"], out["p99_ms"] = out["served"]["continuous"]["p50_ms"], out["served"]["continuous"]["p99_ms"]
     h.close()
     if args.config == "city" and not args.leaves and not args.no_batched:
@@ -338,7 +376,17 @@ def run_batched(sc, n_views: int, steps: int, warmup: int, seed: int = 4) -> dic
     sizes = [scenegen.RESOLUTIONS[n] for n in pick]
     tau = scenegen.CONFIGS["city"]["tau"]
     h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF)
-    views = [vgr.View(h, use_graph=True) for _ in range(n_views)]
+    # launch geometry per image size from the autotuner (a 13-frame walk of
+    # the first view of each size, frames 287..299)
+    from paper_2506_02774_gb300 import autotune
+    geom = {}
+    for name in names:
+        if name in pick:
+            i = pick.index(name)
+            walk = [scenegen.street_trajectory("city", 200 + i, fr, *sizes[i]) for fr in range(287, 300)]
+            geom[name] = autotune.tune(h, walk, tau)
+    views = [vgr.View(h, use_graph=True, grid_wide=geom[pick[i]]["grid_wide"], grid_scan=geom[pick[i]]["grid_scan"])
+             for i in range(n_views)]
     frames = list(range(300 - warmup, 300 + steps))
     cams = {fr: [scenegen.street_trajectory("city", 200 + i, fr, *sizes[i]) for i in range(n_views)] for fr in frames}
     taus = [tau] * n_views
@@ -365,29 +413,25 @@ def run_batched(sc, n_views: int, steps: int, warmup: int, seed: int = 4) -> dic
         v.close()
     h.close()
     counts = {n: pick.count(n) for n in names}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    tuned = {n: dict(grid_wide_per_sm=g["grid_wide"] // sms, grid_scan_per_sm=g["grid_scan"] // sms,
+                     ms=g["ms"], default_ms=g["default_ms"]) for n, g in geom.items()}
     return dict(views=n_views, sizes=counts, frames="300..%d of each view's own street walk" % (300 + steps - 1),
+                autotuned=tuned,
                 storage="fp16 SH + bf16 covariance", views_device_gb=round(dev_bytes / 1e9, 1),
                 speedup=round(out["batched"]["views_per_s"] / out["sequential"]["views_per_s"], 3), **out)
 
 
-def run_served(sc, h, n_clients: int, rate: float, seconds: float, seed: int = 5) -> dict:
-    """Serving: n_clients clients with Poisson arrivals (rate req/s each) for
-    `seconds`, image sizes uniform over 720p/1080p/1440p, each client on its
-    own street walk (one frame step per request), images copied to pinned
-    host memory.  Latency = completion - arrival.  Continuous batching (every
-    client's frame may be in flight) against one frame at a time."""
+def _serve_trace(n_clients: int, rate: float, seconds: float, seed: int, pick, frame0: int):
+    """Poisson arrivals (rate req/s per client) over `seconds`; client c's
+    k-th request renders frame frame0 + k of its own street walk."""
     import scenegen
-    import paper_2506_02774_gb300 as vgr
     rng = np.random.default_rng(seed)
-    names = ["720p", "1080p", "1440p"]
-    pick = [names[i] for i in rng.integers(0, 3, n_clients)]
     tau = scenegen.CONFIGS["city"]["tau"]
-    warm, trace = [], []
+    trace = []
     for c in range(n_clients):
         W, H = scenegen.RESOLUTIONS[pick[c]]
-        for k in range(2):
-            warm.append(dict(client=c, arrival_s=0.0, tau=tau, cam=scenegen.street_trajectory("city", 300 + c, k, W, H)))
-        t, k = 0.0, 2
+        t, k = 0.0, frame0
         while True:
             t += float(rng.exponential(1.0 / rate))
             if t > seconds:
@@ -395,20 +439,54 @@ def run_served(sc, h, n_clients: int, rate: float, seconds: float, seed: int = 5
             trace.append(dict(client=c, arrival_s=t, tau=tau, cam=scenegen.street_trajectory("city", 300 + c, k, W, H)))
             k += 1
     trace.sort(key=lambda r: r["arrival_s"])
-    out = {}
-    for mode, inflight in (("continuous", 0), ("one_at_a_time", 1)):
-        sv = vgr.Server(h, n_clients, max_inflight=inflight, host_images=True)
-        sv.serve(warm)
-        r = sv.serve(trace)
-        sv.close()
-        ok = r["status"] == 0
-        lat = 1e3 * (r["finish_s"] - r["arrival_s"])[ok]
-        span = float(r["finish_s"].max() - r["arrival_s"].min())
-        out[mode] = dict(p50_ms=round(float(np.percentile(lat, 50)), 3), p99_ms=round(float(np.percentile(lat, 99)), 3),
-                         mean_ms=round(float(lat.mean()), 3), completed=int(ok.sum()), refused=int((r["status"] == 2).sum()),
-                         frames_per_s=round(float(ok.sum()) / span, 1))
+    return trace
+
+
+def _serve_once(h, n_clients, inflight, pick, trace):
+    import scenegen
+    import paper_2506_02774_gb300 as vgr
+    tau = scenegen.CONFIGS["city"]["tau"]
+    warm = [dict(client=c, arrival_s=0.0, tau=tau, cam=scenegen.street_trajectory("city", 300 + c, k, *scenegen.RESOLUTIONS[pick[c]]))
+            for c in range(n_clients) for k in range(2)]
+    sv = vgr.Server(h, n_clients, max_inflight=inflight, host_images=True)
+    sv.serve(warm)
+    r = sv.serve(trace)
+    sv.close()
+    ok = r["status"] == 0
+    lat = 1e3 * (r["finish_s"] - r["arrival_s"])[ok]
+    span = float(r["finish_s"].max() - r["arrival_s"].min())
+    return dict(p50_ms=round(float(np.percentile(lat, 50)), 3), p99_ms=round(float(np.percentile(lat, 99)), 3),
+                mean_ms=round(float(lat.mean()), 3), completed=int(ok.sum()), refused=int((r["status"] == 2).sum()),
+                frames_per_s=round(float(ok.sum()) / span, 1))
+
+
+def run_served(sc, h, n_clients: int, rate: float, seconds: float, sweep, sweep_seconds: float,
+               p99_bound_ms: float, seed: int = 5) -> dict:
+    """Serving: n_clients clients with Poisson arrivals (rate req/s each) for
+    `seconds`, image sizes uniform over 720p/1080p/1440p, each client on its
+    own street walk (one frame step per request), images copied to pinned
+    host memory.  Latency = completion - arrival.  Continuous batching (every
+    client's frame may be in flight) against one frame at a time; then a
+    sweep of the offered load, reporting for each mode the highest
+    throughput whose p99 stays within p99_bound_ms."""
+    rng = np.random.default_rng(seed)
+    names = ["720p", "1080p", "1440p"]
+    pick = [names[i] for i in rng.integers(0, 3, n_clients)]
+    modes = (("continuous", 0), ("one_at_a_time", 1))
+    trace = _serve_trace(n_clients, rate, seconds, seed, pick, 2)
+    out = {m: _serve_once(h, n_clients, inf, pick, trace) for m, inf in modes}
+    pts = {m: [] for m, _ in modes}
+    for r in sweep:
+        tr = _serve_trace(n_clients, r, sweep_seconds, seed + int(r), pick, 2)
+        for m, inf in modes:
+            x = _serve_once(h, n_clients, inf, pick, tr)
+            pts[m].append(dict(rate_per_client=r, offered=round(n_clients * r, 1), frames_per_s=x["frames_per_s"],
+                               p50_ms=x["p50_ms"], p99_ms=x["p99_ms"]))
+    best = {m: max([p["frames_per_s"] for p in pts[m] if p["p99_ms"] <= p99_bound_ms] or [0.0]) for m, _ in modes}
     return dict(clients=n_clients, rate_per_client=rate, seconds=seconds, requests=len(trace),
-                sizes={n: pick.count(n) for n in names}, host_images=True, **out)
+                sizes={n: pick.count(n) for n in names}, host_images=True, **out,
+                sweep=dict(seconds=sweep_seconds, p99_bound_ms=p99_bound_ms, points=pts,
+                           max_frames_per_s_within_bound=best))
 
 
 def cpu_baseline(sc, cams, tau, budget_s: float = 20.0) -> dict:
@@ -468,12 +546,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--no-graph", action="store_true", help="headline view without CUDA graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batch leg")
+    ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16-store run of the walk")
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--serve-clients", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-sweep", default="12,16,20,24,28,32", help="per-client request rates of the load sweep")
+    ap.add_argument("--sweep-seconds", type=float, default=4.0)
+    ap.add_argument("--p99-bound", type=float, default=10.0, help="p99 latency bound (ms) of the load sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="city", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="fp32", choices=["fp32", "half"])

@@ -112,6 +112,10 @@ typedef struct {
     uint64_t cut_capacity;   /* initial capacities; 0 = automatic.  Grown on demand. */
     uint64_t pair_capacity;
     uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
+    uint32_t grid_wide;      /* CTAs of the grid-stride kernels (LoD, preprocess, colour, ranges);
+                                0 = 8 per SM.  Launch geometry only: results do not depend on it. */
+    uint32_t grid_scan;      /* CTAs of the ticketed look-back kernels (compaction, radix passes,
+                                emission); 0 = 4 per SM.  Launch geometry only. */
 } vgr_view_opts;
 
 enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT, VGR_STAGE_COLOR,
@@ -158,10 +162,10 @@ typedef struct {
     const uint32_t* vis_rect;     /* [2 n_front] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
     const float* vis_recA;        /* [4 n_front] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
     const float* vis_recB;        /* [4 n_front] C thr theta h, thr = ln alpha* - ln theta, h = box half-height */
-    const float* rank_rgb;        /* [4 n_visible] r g b 0 in depth-rank order */
+    const float* vis_rgb;         /* [4 n_front] r g b 0 (visible entries only) */
     const uint32_t* depth_order;  /* [n_front] in-front index by depth rank; the first n_visible are visible */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
-    const uint32_t* pair_val;     /* [n_pairs] depth rank << 8 | row mask (bit w: the footprint box reaches
+    const uint32_t* pair_val;     /* [n_pairs] in-front index << 8 | row mask (bit w: the footprint box reaches
                                      pixel row 2w or 2w + 1 of the tile; all ones in the canonical mode) */
     const uint32_t* tile_range;   /* [2 tiles] start, end into the pair list */
 } vgr_debug_buffers;

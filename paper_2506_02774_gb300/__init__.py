@@ -145,7 +145,8 @@ class View:
 
     def __init__(self, hier: Hierarchy, *, filter: int = FILTER_PREEMPTIVE, exp_mode: int = EXP_EXACT,
                  lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
-                 cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, stream=None):
+                 cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, grid_wide: int = 0,
+                 grid_scan: int = 0, stream=None):
         lib = _abi.load()
         o = _abi.ViewOpts()
         lib.vgr_default_view_opts(ctypes.byref(o))
@@ -154,6 +155,7 @@ class View:
         o.cut_capacity, o.pair_capacity = cut_capacity, pair_capacity
         if lod_budget:
             o.lod_budget = lod_budget
+        o.grid_wide, o.grid_scan = int(grid_wide), int(grid_scan)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(stream))
         v = ctypes.c_void_p()
@@ -235,13 +237,15 @@ class View:
         compact = np.cumsum(vis) - 1
         order = u32(d.depth_order, nf)[:nv]
         pval = u32(d.pair_val, npairs)
+        rank_of_front = np.full(max(nf, 1), 0xFFFFFFFF, np.int64)  # in-front index -> depth rank
+        rank_of_front[order] = np.arange(nv)
         assert vis[order].all(), "the first n_visible depth ranks must be visible entries"
         return dict(n_cut=nc, n_front=nf, n_visible=nv, n_pairs=npairs, tiles=(int(d.tiles_x), int(d.tiles_y)),
                     cut=u32(d.cut, nc), vis_node=u32(d.vis_node, nf)[vis], vis_depth=u32(d.vis_depth, nf)[vis],
                     vis_ntile=ntile[vis], vis_rect=u32(d.vis_rect, 2 * nf).reshape(nf, 2)[vis],
                     vis_recA=f32(d.vis_recA, (nf, 4))[vis], vis_recB=f32(d.vis_recB, (nf, 4))[vis],
-                    rank_rgb=f32(d.rank_rgb, (nv, 4)), depth_order=compact[order].astype(np.uint32),
-                    pair_tile=u32(d.pair_tile, npairs), pair_rank=pval >> 8, pair_rowmask=pval & 0xFF,
+                    vis_rgb=f32(d.vis_rgb, (nf, 4))[vis], depth_order=compact[order].astype(np.uint32),
+                    pair_tile=u32(d.pair_tile, npairs), pair_rank=rank_of_front[pval >> 8], pair_rowmask=pval & 0xFF,
                     tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
 
     def close(self):

@@ -32,7 +32,7 @@ class Camera(ctypes.Structure):
 class ViewOpts(ctypes.Structure):
     _fields_ = [("stream", c_vp), ("filter", c_u32), ("exp_mode", c_u32), ("lut_size", c_u32),
                 ("temporal", c_u32), ("timing", c_u32), ("use_graph", c_u32), ("cut_capacity", c_u64),
-                ("pair_capacity", c_u64), ("lod_budget", c_u32)]
+                ("pair_capacity", c_u64), ("lod_budget", c_u32), ("grid_wide", c_u32), ("grid_scan", c_u32)]
 
 
 class FrameStats(ctypes.Structure):
@@ -52,7 +52,7 @@ class DebugBuffers(ctypes.Structure):
     _fields_ = [("n_cut", c_u32), ("n_front", c_u32), ("n_visible", c_u32), ("n_pairs", c_u64), ("tiles_x", c_u32),
                 ("tiles_y", c_u32), ("cut", c_vp), ("vis_node", c_vp), ("vis_depth", c_vp),
                 ("vis_ntile", c_vp), ("vis_rect", c_vp), ("vis_recA", c_vp), ("vis_recB", c_vp),
-                ("rank_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_val", c_vp),
+                ("vis_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_val", c_vp),
                 ("tile_range", c_vp)]
 
 

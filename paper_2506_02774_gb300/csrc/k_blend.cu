@@ -9,8 +9,8 @@
 // box rho < ln alpha* - ln theta holds with a margin, so a pair whose box
 // misses the warp's two rows would fail the Eq. 4 test at every one of its
 // pixels).  The warp reads 32 pair values at a time (coalesced), keeps those
-// with its row bit, and copies their 48-byte records (depth-rank order) with
-// cp.async into its own double-buffered slice of shared memory; the copies
+// with its row bit, and copies their 48-byte records (mean, conic,
+// threshold, opacity, colour) with cp.async into its own double-buffered slice of shared memory; the copies
 // of the next 32 pairs are in flight while the current ones are walked, two
 // at a time for instruction-level parallelism.  Records are read only for
 // the pairs a warp needs, and the eight warps of a tile share them through
@@ -90,9 +90,9 @@ template <int MODE>
 __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict__ tile_order,
                                                       const uint2* __restrict__ ranges,
                                                       const uint32_t* __restrict__ pair_val,
-                                                      const float4* __restrict__ srecA,
-                                                      const float4* __restrict__ srecB,
-                                                      const float4* __restrict__ srecC,
+                                                      const float4* __restrict__ recA,
+                                                      const float4* __restrict__ recB,
+                                                      const float4* __restrict__ rgb,
                                                       const FrameParams* __restrict__ fp,
                                                       const float* __restrict__ lut, float* __restrict__ image,
                                                       Counters* __restrict__ ctr) {
@@ -125,10 +125,10 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
         const bool hit = (v & wbit) != 0u;  // entries past the range hold 0
         const uint32_t hits = __ballot_sync(FULL, hit);
         if (hit) {
-            const uint32_t slot = __popc(hits & lanemask_lt()), rk = v >> 8;
-            cp_async16(&sbuf[buf][0][warp][slot], srecA + rk);
-            cp_async16(&sbuf[buf][1][warp][slot], srecB + rk);
-            cp_async16(&sbuf[buf][2][warp][slot], srecC + rk);
+            const uint32_t slot = __popc(hits & lanemask_lt()), gi = v >> 8;
+            cp_async16(&sbuf[buf][0][warp][slot], recA + gi);
+            cp_async16(&sbuf[buf][1][warp][slot], recB + gi);
+            cp_async16(&sbuf[buf][2][warp][slot], rgb + gi);
         }
         cp_async_commit();
         return hits;
@@ -180,15 +180,14 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
 }
 
 void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
-                  const float4* srecA,
-                  const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
+                  const float4* recA, const float4* recB, const float4* rgb, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s) {
     if (filter == VGR_FILTER_CANONICAL)
-        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
     else if (exp_mode == VGR_EXP_LUT)
-        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
     else
-        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, srecA, srecB, srecC, fp, lut, image, ctr);
+        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
 }
 
 }  // namespace vgr

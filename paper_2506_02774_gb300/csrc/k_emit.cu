@@ -11,16 +11,15 @@
 // candidate tiles costs no more per thread than one with a single tile.  For
 // each slot the tile-level form of Eq. 4 (paper Sec. 4.2) decides: a kept
 // slot gets key = tile id, a dropped one the sentinel key, which the stable
-// tile sort moves behind every real pair.  The slot's value is the
-// Gaussian's depth rank << 8 | its row mask in that tile: bit w is set when
+// tile sort moves behind every real pair (which stay in depth order within
+// a tile, the sort being stable).  The slot's value is the Gaussian's index
+// in the in-front arrays << 8 | its row mask in that tile: bit w is set when
 // the footprint box reaches pixel row 2w or 2w+1 of the tile (the rows the
 // blend's warp w shades; outside the box the Eq. 4 test fails at every
-// pixel), so the blend skips a pair without reading its record.  Ranks
-// therefore take 24 bits: a frame with more visible Gaussians reports an
-// overflow.  The Gaussian's record (mean, conic, threshold,
-// opacity, colour) is copied to rank order so the blend reads the records of a tile
-// at increasing addresses.  The digit histograms of the tile sort are
-// accumulated here as well.
+// pixel), so the blend reads only the records a warp needs, straight from
+// the in-front arrays.  Indices therefore take 24 bits: a frame with more
+// cut nodes in front of the camera reports an overflow.  The digit
+// histograms of the tile sort are accumulated here as well.
 #include <cuda_fp16.h>
 
 #include "vgr_internal.cuh"
@@ -36,8 +35,7 @@ constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
 uint32_t emit_tile() { return EM_TILE; }
 
 __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
-                                                     VisBuffers vis, float4* __restrict__ srecA,
-                                                     float4* __restrict__ srecB, float4* __restrict__ srecC,
+                                                     VisBuffers vis,
                                                      uint32_t* __restrict__ pair_key,
                                                      uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,
                                                      uint32_t sentinel, unsigned long long* __restrict__ status,
@@ -58,7 +56,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
     const float Wf = fp->width_f, Hf = fp->height_f;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     uint32_t kept = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n_vis > MAX_RANKS) atomicOr(&ctr->flags, F_OVF_VIS);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->n_front > MAX_RANKS) atomicOr(&ctr->flags, F_OVF_VIS);
     __syncthreads();
 
     for (;;) {
@@ -78,9 +76,6 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
                 const uint2 rect = vis.rect[vi];
                 const float4 A = vis.recA[vi];
                 const float4 B = vis.recB[vi];
-                srecA[r] = A;
-                srecB[r] = B;
-                srecC[r] = vis.rgb[vi];
                 // the conic is stored pre-scaled (A = -a/2, B = -b, C = -c/2): exact to undo
                 const float ca = -2.0f * A.z, cb = -A.w, cc = -2.0f * B.x;
                 s_g[q] = make_float4(A.x, A.y, ca, cb);
@@ -110,40 +105,54 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
         }
         __syncthreads();
         const uint64_t base = s_prefix;
-        for (uint32_t j = threadIdx.x; j < total; j += EM_THREADS) {
-            // owner of slot j: the last g with s_off[g] <= j
+        // slots in warp-sized runs: the owner of the run's first slot by a
+        // warp-uniform binary search, the other lanes' owners by counting the
+        // Gaussians that start inside the run (every visible Gaussian has at
+        // least one slot, so starts are distinct)
+        const uint32_t lane = lane_id();
+        for (uint32_t j0 = (threadIdx.x & ~31u); j0 < total; j0 += EM_THREADS) {
             uint32_t lo = 0, hi = EM_TILE;
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (s_off[mid] <= j) lo = mid; else hi = mid;
+                if (s_off[mid] <= j0) lo = mid; else hi = mid;
             }
-            const uint32_t g = lo;
-            const uint32_t local = j - s_off[g];
-            const uint32_t rc = s_rect[g];
-            const uint32_t w = rc >> 20;
-            const int tx = (int)(rc & 0x3FFu) + (int)(local % w);
-            const int ty = (int)((rc >> 10) & 0x3FFu) + (int)(local / w);
-            bool keep = true;
+            const uint32_t gi = lo + 1u + lane;
+            const uint32_t d = (gi <= (uint32_t)EM_TILE ? s_off[gi] : 0xFFFFFFFFu) - j0;  // >= 1
+            const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, d < 32u ? 1u << d : 0u);
+            const uint32_t j = j0 + lane;
+            const bool valid = j < total;
+            const uint32_t g = lo + __popc(starts & ((2u << lane) - 1u));
+            uint32_t key = 0xFFFFFFFFu;
+            bool keep = false;
             uint32_t rows = 0xFFu;
-            if (!canonical) {
-                const float4 G = s_g[g], Hh = s_h[g];
-                keep = tile_keep(G.x, G.y, G.z, G.w, Hh.x, Hh.y, Hh.z, Hh.w, tx, ty, Wf, Hf);
-                // tile rows r with |row0 + r - v| <= half-height, as row pairs
-                const float row0 = (float)(ty * TILE) + 0.5f, hh = __half2float(s_hh[g]);
-                const float lo = fmaxf(0.f, ceilf(G.y - hh - row0));
-                const float hi = fminf((float)(TILE - 1), floorf(G.y + hh - row0));
-                rows = 0u;
-                if (lo <= hi) {
-                    const uint32_t w0 = (uint32_t)lo >> 1, w1 = (uint32_t)hi >> 1;
-                    rows = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+            if (valid) {
+                const uint32_t local = j - s_off[g];
+                const uint32_t rc = s_rect[g];
+                const uint32_t w = rc >> 20;
+                const int tx = (int)(rc & 0x3FFu) + (int)(local % w);
+                const int ty = (int)((rc >> 10) & 0x3FFu) + (int)(local / w);
+                keep = true;
+                if (!canonical) {
+                    const float4 G = s_g[g], Hh = s_h[g];
+                    keep = tile_keep(G.x, G.y, G.z, G.w, Hh.x, Hh.y, Hh.z, Hh.w, tx, ty, Wf, Hf);
+                    // tile rows r with |row0 + r - v| <= half-height, as row pairs
+                    const float row0 = (float)(ty * TILE) + 0.5f, hh = __half2float(s_hh[g]);
+                    const float rlo = fmaxf(0.f, ceilf(G.y - hh - row0));
+                    const float rhi = fminf((float)(TILE - 1), floorf(G.y + hh - row0));
+                    rows = 0u;
+                    if (rlo <= rhi) {
+                        const uint32_t w0 = (uint32_t)rlo >> 1, w1 = (uint32_t)rhi >> 1;
+                        rows = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+                    }
                 }
+                key = keep ? (uint32_t)ty * TW + (uint32_t)tx : sentinel;
+                kept += keep;
             }
-            const uint32_t key = keep ? (uint32_t)ty * TW + (uint32_t)tx : sentinel;
-            kept += keep;
             const uint64_t pos = base + j;
-            if (pos < cap) {
+            const bool write = valid && pos < cap;
+            if (write) {
                 pair_key[pos] = key;
-                pair_val[pos] = ((tile * EM_TILE + g) << 8) | rows;
+                pair_val[pos] = (order[tile * EM_TILE + g] << 8) | rows;  // L1: loaded by the gather above
                 for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
             }
         }
@@ -163,11 +172,10 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
     }
 }
 
-void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, float4* srecA, float4* srecB,
-                 float4* srecC, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
+void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
                  uint32_t sentinel, unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
                  cudaStream_t s) {
-    k_emit<<<grid, EM_THREADS, 0, s>>>(order, cap_vis, vis, srecA, srecB, srecC, pair_key, pair_val, cap_pairs,
+    k_emit<<<grid, EM_THREADS, 0, s>>>(order, cap_vis, vis, pair_key, pair_val, cap_pairs,
                                        tile_passes, sentinel, status, ctr, fp);
 }
 

@@ -46,7 +46,9 @@ struct CutOut {
     float R0, R1, R2, R3, R4, R5, R6, R7, R8, Cx, Cy, Cz, z_near;
     float fx, fy, cx, cy, kx, ky, umax, vmax;
     bool canonical;
-    __device__ __forceinline__ void add(uint32_t n, float4 c) const {
+    __device__ __forceinline__ void add(uint32_t n, float4 c) const { add(n, c, lmax[n]); }
+    // lm = lmax[n], loaded by the caller together with the node's centre
+    __device__ __forceinline__ void add(uint32_t n, float4 c, float lm) const {
         bitmap_set(cut_bm, n);
         const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
         const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
@@ -55,7 +57,7 @@ struct CutOut {
         const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
         const float iz = 1.0f / z;
         const float u = fmaf(fx, x * iz, cx), v = fmaf(fy, y * iz, cy);
-        const float t = lmax[n] * iz * iz;
+        const float t = lm * iz * iz;
         float bx, by;
         if (!canonical) {
             bx = 3.34f * sqrtf(fmaf(t, kx, 0.3f)) + 0.01f;
@@ -101,15 +103,12 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     const CutOut out = make_cut_out(fp, sc, bitmap, front);
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_prev; i += stride) {
-        const uint32_t n = prev_cut[i];
-        const float4 cn = sc.cr[n];
+    // one previous-cut node: stay, collapse or expand
+    auto visit = [&](uint32_t n, float4 cn, uint32_t p, float4 cp, float ln) {
         const bool en = lod_expand(cn, px, py, pz, k);
-        const uint32_t p = sc.parent[n];
         bool ep = true;
-        float4 cp = cn;
         ++evals;
-        if (p != NONE) { cp = sc.cr[p]; ep = lod_expand(cp, px, py, pz, k); ++evals; }
+        if (p != NONE) { ep = lod_expand(cp, px, py, pz, k); ++evals; }
         if (!ep) {
             if (en) flags |= F_NONMONOTONE;
             // collapse: climb while the parent of a does not expand
@@ -151,8 +150,21 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
             }
             evals += local;
         } else {
-            out.add(n, cn);
+            out.add(n, cn, ln);  // stay
         }
+    };
+    // two nodes per thread and round, their loads in flight together
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n_prev; i0 += 2 * stride) {
+        const uint32_t i1 = i0 + stride;
+        const bool has1 = i1 < n_prev;
+        const uint32_t n0 = prev_cut[i0], n1 = has1 ? prev_cut[i1] : n0;
+        const float4 c0 = sc.cr[n0], c1 = sc.cr[n1];
+        const uint32_t p0 = sc.parent[n0], p1 = sc.parent[n1];
+        const float l0 = sc.lmax[n0], l1 = sc.lmax[n1];
+        const float4 q0 = p0 != NONE ? sc.cr[p0] : c0;
+        const float4 q1 = p1 != NONE ? sc.cr[p1] : c1;
+        visit(n0, c0, p0, q0, l0);
+        if (has1) visit(n1, c1, p1, q1, l1);
     }
     // one atomic per warp for the statistics
     uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, evals);

@@ -121,7 +121,7 @@ struct Store<VGR_STORE_HALF> {
 };
 
 template <int STORE>
-__global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
+__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
                                                             const uint32_t* __restrict__ n_front_p, uint32_t cap,
                                                             const FrameParams* __restrict__ fp, VisBuffers vis,
                                                             Counters* __restrict__ ctr) {
@@ -148,14 +148,12 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
         if (v) {
             node = front[i];
             const float4 m = sc.cr[node];
+            float S[6], lnth = 0.f;
+            Store<STORE>::cov(sc, node, S, theta, lnth);  // in flight together with the centre
             const float dx = __fsub_rn(m.x, Cx), dy = __fsub_rn(m.y, Cy), dz = __fsub_rn(m.z, Cz);
             const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
             v = z > z_near;  // always true for the in-front list; kept as the definition
-            float S[6], lnth = 0.f;
-            if (v) {
-                Store<STORE>::cov(sc, node, S, theta, lnth);
-                if (!canonical && !(theta >= ALPHA_MIN)) v = false;  // Gaussian-level filter
-            }
+            if (v && !canonical && !(theta >= ALPHA_MIN)) v = false;  // Gaussian-level filter
             if (v) {
                 const float x = fmaf(R0, dx, fmaf(R1, dy, R2 * dz));
                 const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
@@ -220,7 +218,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(SceneDev sc, const u
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const uint32_t dd = i < n_front ? ((zbits >> (8 * p)) & 255u) : 256u;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dd);
+            const uint32_t peers = match_digit(dd);
             if (dd < 256u && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[p][dd], (uint32_t)__popc(peers));
         }
         if (i < n_front) {

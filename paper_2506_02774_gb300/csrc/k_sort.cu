@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
         const uint32_t k = valid ? keys[i] : 0u;
         for (int p = 0; p < passes; ++p) {
             const uint32_t d = valid ? ((k >> (8 * p)) & 255u) : 256u;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t peers = match_digit(d);
             if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
         }
     }
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
             const uint32_t d = idx < n ? ((key[it] >> shift) & 255u) : 256u;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t peers = match_digit(d);
             const int leader = __ffs(peers) - 1;
             uint32_t before = 0;
             if (d < 256u && (int)lane == leader) before = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));

@@ -114,9 +114,6 @@ struct vgr_view {
     VisBuffers vis{};
     uint32_t* sortK[2] = {nullptr, nullptr};
     uint32_t* sortV[2] = {nullptr, nullptr};
-    float4* srecA = nullptr;
-    float4* srecB = nullptr;
-    float4* srecC = nullptr;  // r g b, depth-rank order
     uint32_t* pairK[2] = {nullptr, nullptr};
     uint32_t* pairV[2] = {nullptr, nullptr};
     uint2* ranges = nullptr;
@@ -401,7 +398,6 @@ void free_vis(vgr_view* v) {
     dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
     dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
-    dfree(v->srecA); dfree(v->srecB); dfree(v->srecC);
     v->vis_bytes = 0;
 }
 
@@ -415,8 +411,7 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
         (s = dalloc(&v->vis.rgb, cap, &b)) ||
         (s = dalloc(&v->sortK[0], cap, &b)) ||
         (s = dalloc(&v->sortK[1], cap, &b)) || (s = dalloc(&v->sortV[0], cap, &b)) ||
-        (s = dalloc(&v->sortV[1], cap, &b)) || (s = dalloc(&v->srecA, cap, &b)) ||
-        (s = dalloc(&v->srecB, cap, &b)) || (s = dalloc(&v->srecC, cap, &b))) {
+        (s = dalloc(&v->sortV[1], cap, &b))) {
         free_vis(v);
         return s;
     }
@@ -560,8 +555,8 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
         if (e != cudaSuccess) { delete v; return fail(VGR_E_CUDA, "stream: %s", cudaGetErrorString(e)); }
         v->own_stream = true;
     }
-    v->grid_wide = h->num_sms * 8;
-    v->grid_scan = h->num_sms * 4;
+    v->grid_wide = v->opts.grid_wide ? (int)std::min<uint32_t>(v->opts.grid_wide, 1u << 16) : h->num_sms * 8;
+    v->grid_scan = v->opts.grid_scan ? (int)std::min<uint32_t>(v->opts.grid_scan, 1u << 16) : h->num_sms * 4;
     const uint32_t cap_cut = (uint32_t)std::min<uint64_t>(N, v->opts.cut_capacity ? v->opts.cut_capacity
                                                                                   : std::max<uint64_t>(1u << 20, N / 4));
     const uint32_t cap_vis = cap_cut;
@@ -717,7 +712,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     launch_color(sc, v->vis.node, v->vis.ntile, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, v->grid_wide, s);
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
-    launch_emit(order, v->cap_vis, v->vis, v->srecA, v->srecB, v->srecC, v->pairK[0], v->pairV[0], v->cap_pairs,
+    launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
                 tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, s);
     mark(VGR_STAGE_TILE_SORT);
     for (int p = 0; p < tile_passes; ++p) {
@@ -732,7 +727,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, n_tiles, v->ranges, v->grid_wide, s);
     launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
     mark(VGR_STAGE_BLEND);
-    launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->srecA, v->srecB, v->srecC, v->fp_dev, v->lut, v->image, v->ctr,
+    launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->vis.recA, v->vis.recB, v->vis.rgb, v->fp_dev, v->lut, v->image, v->ctr,
                  v->opts.filter, v->opts.exp_mode, s);
     mark(VGR_N_STAGES);
     cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
@@ -868,7 +863,7 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         if (flags & F_NONMONOTONE)
             return fail(VGR_E_NONMONOTONE, "granularity test not monotone: a child expands while its parent does not");
         if (flags & F_OVF_FRONTIER) return fail(VGR_E_OVERFLOW, "frontier overflow");
-        if (flags & F_OVF_VIS) return fail(VGR_E_OVERFLOW, "more than 2^24 visible Gaussians in one frame");
+        if (flags & F_OVF_VIS) return fail(VGR_E_OVERFLOW, "more than 2^24 cut nodes in front of the camera in one frame");
         bool again = false;
         if ((flags & F_LOD_FALLBACK) && !q.scratch) {
             q.scratch = true;
@@ -1014,7 +1009,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     o->vis_rect = reinterpret_cast<const uint32_t*>(v->vis.rect);
     o->vis_recA = reinterpret_cast<const float*>(v->vis.recA);
     o->vis_recB = reinterpret_cast<const float*>(v->vis.recB);
-    o->rank_rgb = reinterpret_cast<const float*>(v->srecC);
+    o->vis_rgb = reinterpret_cast<const float*>(v->vis.rgb);
     o->depth_order = v->sortV[1];
     o->pair_tile = v->pairK[v->last_tile_buf];
     o->pair_val = v->pairV[v->last_tile_buf];

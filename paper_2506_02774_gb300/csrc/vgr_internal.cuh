@@ -251,4 +251,17 @@ __device__ __forceinline__ bool lod_expand(float4 c, float px, float py, float p
 
 __device__ __forceinline__ void bitmap_set(uint32_t* bm, uint32_t n) { atomicOr(&bm[n >> 5], 1u << (n & 31u)); }
 
+// Lanes of the (full) warp holding the same 9-bit value (a radix digit
+// 0..255, or 256 for "no digit"): one ballot per bit.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d) {
+    uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
+        m &= bit ? vote : ~vote;
+    }
+    return m;
+}
+
 }  // namespace vgr

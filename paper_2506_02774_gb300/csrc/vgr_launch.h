@@ -55,8 +55,7 @@ void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
                        Counters* ctr, int grid, cudaStream_t s);
 
 // k_emit.cu
-void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, float4* srecA, float4* srecB,
-                 float4* srecC, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
+void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
                  unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
 uint32_t emit_tile();
 void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
@@ -65,8 +64,7 @@ void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, c
 
 // k_blend.cu
 void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
-                  const float4* srecA,
-                  const float4* srecB, const float4* srecC, const FrameParams* fp, const float* lut, float* image,
+                  const float4* recA, const float4* recB, const float4* rgb, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
 
 // vgr_sort_api.cu: enqueue a standalone pair sort on caller-provided scratch

@@ -137,9 +137,7 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None) -> dict:
     cref = p["conic"]
     cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))[:, None]
     assert np.max(np.abs(con - cref) / cs) < 2e-3
-    rank_of = np.empty(len(gv), np.int64)
-    rank_of[dbg["depth_order"]] = np.arange(len(gv))
-    rgb = dbg["rank_rgb"][rank_of, :3]
+    rgb = dbg["vis_rgb"][:, :3]
     assert np.max(np.abs(rgb - p["rgb"])) < 2e-5
     np.testing.assert_array_equal(B[:, 2], p["theta"].astype(np.float32))
     assert np.max(np.abs(B[:, 1] - p["thr"])) < 1e-5

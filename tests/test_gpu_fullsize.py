@@ -101,3 +101,29 @@ def test_city_1080p_sampled_tiles():
         print("city frame", fr, res.stats["cut_count"], res.stats["visible_count"], res.stats["pair_count"], r, s)
     v.close()
     h.close()
+
+
+def test_city_half_storage_sampled_tiles():
+    """FP16 SH + BF16 covariance store on the full city: the cut is the FP32
+    one (centres and radii stay FP32); sampled tiles within the image bar of
+    the oracle run on the quantized scene; the error against the FP32 scene
+    is reported."""
+    from parity import image_report, quantize_scene
+    sc = scenegen.make_scene("city")
+    h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF)
+    v = vgr.View(h)
+    tau = scenegen.CONFIGS["city"]["tau"]
+    q = quantize_scene(sc)
+    for fr in (0, 1):
+        cam = scenegen.trajectory("city", fr)
+        res = v.render(cam, tau)
+        mask = _tile_mask(v.debug(), 200 + fr)
+        refq = oracle.render(q, cam, tau, tile_mask=mask)
+        np.testing.assert_array_equal(res.cut().cpu().numpy().view(np.uint32), refq["cut"])
+        img = res.image().cpu().numpy()
+        r = check_image(img, refq, tile_mask=mask)
+        ref = oracle.render(sc, cam, tau, tile_mask=mask)
+        print("city half store frame", fr, "vs quantized-scene oracle", r, "vs FP32-scene oracle",
+              image_report(img, ref, mask))
+    v.close()
+    h.close()
