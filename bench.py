@@ -257,20 +257,30 @@ def run_ours(args) -> dict:
     # temporal update, Sec. 4.1): overlap of the cuts of two consecutive
     # frames and the nodes each LoD form evaluates for the same frame
     lod_reuse = None
-    if ws == 1 or rank == 0:
-        vr = vgr.View(h, stream=stream.cuda_stream)
-        vs = vgr.View(h, stream=stream.cuda_stream, temporal=False)
+    if (ws == 1 or rank == 0) and not args.no_lod_reuse:
+        vr = vgr.View(h, stream=stream.cuda_stream, timing=True)
+        vs = vgr.View(h, stream=stream.cuda_stream, temporal=False, timing=True)
         i0 = args.warmup + args.steps // 2
+        for i in range(max(0, i0 - 3), i0):
+            vr.render(cams[i], tau)
         a = vr.render(cams[i0], tau)
         ca = a.cut().cpu().numpy().copy()
-        b = vr.render(cams[i0 + 1], tau)
-        cb = b.cut().cpu().numpy()
-        s_ = vs.render(cams[i0 + 1], tau)
+        lod_t, lod_s, ev_t, ev_s = [], [], [], []
+        for i in range(i0 + 1, min(len(cams), i0 + 6)):
+            b = vr.render(cams[i], tau)
+            if i == i0 + 1:
+                cb = b.cut().cpu().numpy().copy()
+            s_ = vs.render(cams[i], tau)
+            lod_t.append(b.stats["stage_ms"]["lod"])
+            lod_s.append(s_.stats["stage_ms"]["lod"])
+            ev_t.append(b.stats["nodes_evaluated"])
+            ev_s.append(s_.stats["nodes_evaluated"])
         common = int(np.intersect1d(ca, cb, assume_unique=True).size)
         lod_reuse = dict(frames="%d, %d" % (i0, i0 + 1), cut=int(cb.size), common_with_previous=common,
                          overlap=round(common / max(1, cb.size), 5),
-                         nodes_evaluated_temporal=b.stats["nodes_evaluated"],
-                         nodes_evaluated_top_down=s_.stats["nodes_evaluated"])
+                         nodes_evaluated_temporal=int(np.mean(ev_t)), nodes_evaluated_top_down=int(np.mean(ev_s)),
+                         lod_ms_temporal=round(float(np.mean(lod_t)), 4),
+                         lod_ms_top_down=round(float(np.mean(lod_s)), 4))
         vr.close()
         vs.close()
 
@@ -455,9 +465,15 @@ def _serve_once(h, n_clients, inflight, pick, trace):
     ok = r["status"] == 0
     lat = 1e3 * (r["finish_s"] - r["arrival_s"])[ok]
     span = float(r["finish_s"].max() - r["arrival_s"].min())
+    svc = 1e3 * (r["finish_s"] - r["start_s"])[ok]
+    arr = r["arrival_s"][ok]
+    slow = np.argsort(lat)[::-1][:5]
     return dict(p50_ms=round(float(np.percentile(lat, 50)), 3), p99_ms=round(float(np.percentile(lat, 99)), 3),
                 mean_ms=round(float(lat.mean()), 3), completed=int(ok.sum()), refused=int((r["status"] == 2).sum()),
-                frames_per_s=round(float(ok.sum()) / span, 1))
+                frames_per_s=round(float(ok.sum()) / span, 1),
+                service_p99_ms=round(float(np.percentile(svc, 99)), 3),
+                slowest=[dict(arrival_s=round(float(arr[i]), 4), latency_ms=round(float(lat[i]), 3),
+                              service_ms=round(float(svc[i]), 3)) for i in slow])
 
 
 def run_served(sc, h, n_clients: int, rate: float, seconds: float, sweep, sweep_seconds: float,
@@ -547,6 +563,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="headline view without CUDA graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batch leg")
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16-store run of the walk")
+    ap.add_argument("--no-lod-reuse", action="store_true", help="skip the cut-reuse statistics")
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)
