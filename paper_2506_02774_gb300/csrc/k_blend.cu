@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
                                                       const FrameParams* __restrict__ fp,
                                                       const float* __restrict__ lut, float* __restrict__ image,
                                                       Counters* __restrict__ ctr) {
+    pdl_wait();
     // [buffer][record part A, B, C][warp][slot]
     __shared__ __align__(16) float4 sbuf[2][3][BL_WARPS][32];
     __shared__ float s_lut[260];
@@ -183,11 +184,11 @@ void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ran
                   const float4* recA, const float4* recB, const float4* rgb, const FrameParams* fp, const float* lut, float* image,
                   Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s) {
     if (filter == VGR_FILTER_CANONICAL)
-        k_blend<1><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
+        launch_k(k_blend<1>, n_tiles, BL_THREADS, s, tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
     else if (exp_mode == VGR_EXP_LUT)
-        k_blend<2><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
+        launch_k(k_blend<2>, n_tiles, BL_THREADS, s, tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
     else
-        k_blend<0><<<n_tiles, BL_THREADS, 0, s>>>(tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
+        launch_k(k_blend<0>, n_tiles, BL_THREADS, s, tile_order, ranges, pair_val, recA, recB, rgb, fp, lut, image, ctr);
 }
 
 }  // namespace vgr

@@ -3,7 +3,7 @@
 // pair list.
 //
 // Visible Gaussians are visited in depth order (the output of the depth
-// sort), 1024 per CTA tile (4 per thread).  Each one owns as many pair slots as it has
+// sort), 512 per CTA tile (2 per thread).  Each one owns as many pair slots as it has
 // candidate tiles; a decoupled look-back scan over the candidate counts gives
 // every CTA tile its global slot range.  The CTA then walks its slots with
 // all 256 threads (slot -> Gaussian by binary search over the CTA's
@@ -29,7 +29,7 @@
 namespace vgr {
 
 constexpr int EM_THREADS = 256;
-constexpr int EM_ITEMS = 4;
+constexpr int EM_ITEMS = 2;
 constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
 
 uint32_t emit_tile() { return EM_TILE; }
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
                                                      uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,
                                                      uint32_t sentinel, unsigned long long* __restrict__ status,
                                                      Counters* __restrict__ ctr, const FrameParams* __restrict__ fp) {
+    pdl_wait();
     __shared__ uint32_t s_scan[9];
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_off[EM_TILE + 1];   // candidate counts, then exclusive slot offsets
@@ -87,7 +88,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
             s_off[q] = area;
         }
         __syncthreads();
-        // exclusive scan of the candidate counts in rank order: thread t owns entries 4t .. 4t+3
+        // exclusive scan of the candidate counts in rank order: thread t owns entries
+        // EM_ITEMS t .. EM_ITEMS t + EM_ITEMS - 1
         uint32_t a4[EM_ITEMS];
         uint32_t sum = 0;
 #pragma unroll
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
 void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
                  uint32_t sentinel, unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
                  cudaStream_t s) {
-    k_emit<<<grid, EM_THREADS, 0, s>>>(order, cap_vis, vis, pair_key, pair_val, cap_pairs,
+    launch_k(k_emit, grid, EM_THREADS, s, order, cap_vis, vis, pair_key, pair_val, cap_pairs,
                                        tile_passes, sentinel, status, ctr, fp);
 }
 
@@ -183,6 +185,7 @@ void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32
 // sort last and are skipped.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const Counters* __restrict__ ctr, uint64_t cap,
                          uint32_t n_tiles, uint2* __restrict__ ranges) {
+    pdl_wait();
     uint64_t n64 = ctr->n_pairs;
     if (n64 > cap) n64 = cap;
     const uint32_t n = (uint32_t)n64;
@@ -196,7 +199,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const Counters* __re
 
 void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
                    int grid, cudaStream_t s) {
-    k_ranges<<<grid, 256, 0, s>>>(keys, ctr, cap_pairs, n_tiles, ranges);
+    launch_k(k_ranges, grid, 256, s, keys, ctr, cap_pairs, n_tiles, ranges);
 }
 
 // Blend order: tiles by descending pair count (buckets of floor(log2(count+1)),
@@ -205,6 +208,7 @@ void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs
 // not matter (tiles are independent).
 __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, uint32_t n_tiles,
                                                      uint32_t* __restrict__ order) {
+    pdl_wait();
     __shared__ uint32_t s_cnt[33], s_start[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
 }
 
 void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {
-    k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order);
+    launch_k(k_tile_order, 1, 1024, s, ranges, n_tiles, order);
 }
 
 }  // namespace vgr

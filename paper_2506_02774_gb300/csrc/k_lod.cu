@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
                                                     SceneDev sc, const FrameParams* __restrict__ fp,
                                                     uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
                                                     Counters* __restrict__ ctr) {
+    pdl_wait();
     const uint32_t n_prev = min(*n_prev_p, cap_prev);
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const uint32_t budget = fp->lod_budget, max_depth = fp->max_depth;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
                                                    const FrameParams* __restrict__ fp,
                                                    uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
                                                    Counters* __restrict__ ctr) {
+    pdl_wait();
     const uint32_t n_in = level == 0 ? 1u : min(ctr->frontier_n[level], cap);
     uint32_t* n_out = &ctr->frontier_n[level + 1];
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitm
                                                      unsigned long long* __restrict__ status_front,
                                                      Counters* __restrict__ ctr,
                                                      const FrameParams* __restrict__ fp) {
+    pdl_wait();
     __shared__ uint32_t s_scan[9];
     __shared__ uint32_t s_tile, s_prefix[2];
     const uint32_t ntiles = (n_words + CC_TILE_WORDS - 1) / CC_TILE_WORDS;
@@ -302,20 +305,20 @@ __global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitm
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
                        const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
                        cudaStream_t s) {
-    k_lod_update<<<grid, 256, 0, s>>>(prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
+    launch_k(k_lod_update, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
 }
 
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
                       cudaStream_t s) {
-    k_lod_level<<<grid, 256, 0, s>>>(level, fin, fout, cap, sc, fp, bitmap, front, ctr);
+    launch_k(k_lod_level, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
 }
 
 void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,
                         uint32_t cap, uint32_t* n_cut_out, unsigned long long* status,
                         unsigned long long* status_front, Counters* ctr, const FrameParams* fp, int grid,
                         cudaStream_t s) {
-    k_cut_compact<<<grid, 256, 0, s>>>(bitmap, front, n_words, cut, front_list, cap, n_cut_out, status,
+    launch_k(k_cut_compact, grid, 256, s, bitmap, front, n_words, cut, front_list, cap, n_cut_out, status,
                                        status_front, ctr, fp);
 }
 

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
                                                             const uint32_t* __restrict__ n_front_p, uint32_t cap,
                                                             const FrameParams* __restrict__ fp, VisBuffers vis,
                                                             Counters* __restrict__ ctr) {
+    pdl_wait();
     __shared__ uint32_t s_hist[4][256];  // digit histograms of the depth keys (the sort's passes)
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     __syncthreads();
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __re
                                                const uint32_t* __restrict__ vis_ntile, uint32_t cap,
                                                const FrameParams* __restrict__ fp, const Counters* __restrict__ ctr,
                                                float4* __restrict__ rgb_out) {
+    pdl_wait();
     constexpr int K = (DEG + 1) * (DEG + 1);
     const uint32_t n = min(ctr->n_front, cap);
     const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
@@ -290,9 +292,9 @@ void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
 void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
                        const FrameParams* fp, VisBuffers vis, Counters* ctr, int grid, cudaStream_t s) {
     if (sc.storage == VGR_STORE_HALF)
-        k_preprocess<VGR_STORE_HALF><<<grid, PRE_THREADS, 0, s>>>(sc, front, n_front, cap, fp, vis, ctr);
+        launch_k(k_preprocess<VGR_STORE_HALF>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
     else
-        k_preprocess<VGR_STORE_FP32><<<grid, PRE_THREADS, 0, s>>>(sc, front, n_front, cap, fp, vis, ctr);
+        launch_k(k_preprocess<VGR_STORE_FP32>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
 }
 
 void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, uint32_t cap,
@@ -300,8 +302,8 @@ void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* 
     const bool half = sc.storage == VGR_STORE_HALF;
 #define VGR_COLOR_CASE(D)                                                                                   \
     case D:                                                                                                 \
-        if (half) k_color<D, VGR_STORE_HALF><<<grid, 256, 0, s>>>(sc, vis_node, vis_ntile, cap, fp, ctr, rgb); \
-        else k_color<D, VGR_STORE_FP32><<<grid, 256, 0, s>>>(sc, vis_node, vis_ntile, cap, fp, ctr, rgb);      \
+        if (half) launch_k(k_color<D, VGR_STORE_HALF>, grid, 256, s, sc, vis_node, vis_ntile, cap, fp, ctr, rgb); \
+        else launch_k(k_color<D, VGR_STORE_FP32>, grid, 256, s, sc, vis_node, vis_ntile, cap, fp, ctr, rgb);      \
         break;
     switch (sc.sh_degree) {
         VGR_COLOR_CASE(0)

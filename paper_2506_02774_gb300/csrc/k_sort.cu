@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 //     is stored contiguously (coalesced).
 constexpr int LB_BATCH = 8;  // look-back words read per round trip
 
-__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
                                                            uint32_t* __restrict__ vals_out,
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_pass(const uint32_t* __
                                                            uint32_t* __restrict__ ticket,
                                                            const FrameParams* __restrict__ fp,
                                                            Counters* __restrict__ ctr) {
+    pdl_wait();
     __shared__ uint32_t s_wc[RS_WARPS][RS_BINS];  // per-warp digit counts, then per-warp run offsets
     __shared__ uint32_t s_gbase[RS_BINS];         // global start of each digit (all tiles)
     __shared__ uint32_t s_lstart[RS_BINS];        // start of each digit's run in the staged tile
@@ -213,7 +214,7 @@ void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
                        const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
                        const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
                        Counters* ctr, int grid, cudaStream_t s) {
-    k_radix_pass<<<grid, RS_THREADS, 0, s>>>(keys_in, vals_in, keys_out, vals_out, n32, n64, cap, shift, hist,
+    launch_k(k_radix_pass, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32, n64, cap, shift, hist,
                                              status, ticket, fp, ctr);
 }
 

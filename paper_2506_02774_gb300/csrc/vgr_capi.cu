@@ -69,6 +69,14 @@ uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); 
 
 void vgr::set_last_error(const char* msg) { g_err = msg; }
 
+bool vgr::pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("VGR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 struct vgr_hierarchy {
     SceneDev dev{};
     float4* cr = nullptr;

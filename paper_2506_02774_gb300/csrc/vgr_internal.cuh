@@ -100,6 +100,11 @@ struct SceneDev {
 
 // ------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// First statement of every frame kernel: wait until the previous kernel in
+// the stream has completed (a no-op when launched without programmatic
+// stream serialization).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

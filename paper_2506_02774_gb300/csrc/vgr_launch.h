@@ -9,6 +9,28 @@ namespace vgr {
 // vgr_capi.cu: the thread-local message returned by vgr_last_error()
 void set_last_error(const char* msg);
 
+// Kernels of a frame are launched with programmatic stream serialization:
+// a kernel's CTAs may be scheduled while the previous kernel drains, and each
+// kernel waits (griddepcontrol.wait, its first statement) until the previous
+// one has completed and its writes are visible, so ordering is unchanged and
+// only the launch latency overlaps.  VGR_PDL=0 in the environment turns it
+// off (plain stream order).
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct SceneDev;
 struct FrameParams;
 struct Counters;
