@@ -12,7 +12,10 @@
 // with its row bit, and copies their 48-byte records (mean, conic,
 // threshold, opacity, colour) with cp.async into its own double-buffered slice of shared memory; the copies
 // of the next 32 pairs are in flight while the current ones are walked, two
-// at a time for instruction-level parallelism.  Records are read only for
+// at a time for instruction-level parallelism.  Before the walk each lane
+// rewrites its staged record for the warp's two rows (the row offsets of the
+// mean folded into the conic terms), so a pixel evaluates rho with one
+// subtraction and two FMAs.  Records are read only for
 // the pairs a warp needs, and the eight warps of a tile share them through
 // L1.  A warp stops when its 32 pixels have stopped; tiles crossing the
 // horizon (tens of thousands of small distant Gaussians, each reaching one
@@ -43,22 +46,35 @@ struct BlendPixel {
     uint32_t evals = 0, contribs = 0;
 };
 
+// A staged record, rewritten for the warp's two pixel rows (dy0, dy1 the
+// offsets of the mean from their centres):
+//   X = (u, A, thr, theta),  R = (B dy0, C dy0^2, B dy1, C dy1^2)
+// so that at a pixel of row r, dx = u - x:  rho = (A dx + B dy_r) dx + C dy_r^2,
+// one subtraction and two FMAs (A = -a/2, B = -b, C = -c/2).
+__device__ __forceinline__ void blend_prepare(float4& a, float4& b, float row0) {
+    const float dy0 = a.y - row0, dy1 = a.y - (row0 + 1.0f);
+    const float Bc = a.w, Cc = b.x;
+    const float4 X = make_float4(a.x, a.z, b.y, b.z);
+    const float4 R = make_float4(Bc * dy0, (Cc * dy0) * dy0, Bc * dy1, (Cc * dy1) * dy1);
+    a = X;
+    b = R;
+}
+
 // One record at one pixel; returns false once the pixel has stopped.
 template <int MODE>
-__device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& A, const float4& B, const float4* __restrict__ sC,
-                                           uint32_t k, float rho, const float* s_lut, uint32_t m, float lut_scale) {
-    ++p.evals;
+__device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& X, const float4* __restrict__ sC, uint32_t k,
+                                           float rho, const float* s_lut, uint32_t m, float lut_scale) {
     float alpha;
     if (MODE == 1) {  // canonical: Eq. 3, then the alpha* test
-        alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
+        alpha = fminf(ALPHA_MAX, X.w * __expf(rho));
         if (alpha < ALPHA_MIN) return true;
     } else {
-        if (rho < B.y) return true;  // Eq. 4 before Eq. 3
+        if (rho < X.z) return true;  // Eq. 4 before Eq. 3
         if (MODE == 0) {
-            alpha = fminf(ALPHA_MAX, B.z * __expf(rho));
+            alpha = fminf(ALPHA_MAX, X.w * __expf(rho));
         } else {  // Eq. 5: nearest of m intervals over [-5.55, 0]
             const uint32_t idx = min(m, (uint32_t)__float2int_rn(rho * lut_scale));
-            alpha = fminf(ALPHA_MAX, B.z * s_lut[idx]);
+            alpha = fminf(ALPHA_MAX, X.w * s_lut[idx]);
         }
     }
     const float Tn = p.T * (1.f - alpha);
@@ -73,9 +89,9 @@ __device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& A, const
     return true;
 }
 
-__device__ __forceinline__ float blend_rho(const BlendPixel& p, const float4& A, const float4& B) {
-    const float dx = A.x - p.fxp, dy = A.y - p.fyp;
-    return fmaf(A.z * dx, dx, fmaf(B.x * dy, dy, A.w * dx * dy));
+__device__ __forceinline__ float blend_rho(const BlendPixel& p, const float4& X, const float2& R) {
+    const float dx = X.x - p.fxp;
+    return fmaf(fmaf(X.y, dx, R.x), dx, R.y);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -108,6 +124,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     const uint32_t py = ty0 + 2 * warp + (lane >> 4);
     const bool inside = px < W && py < H;
     const uint32_t wbit = 1u << warp;
+    const float rlo = (float)(ty0 + 2 * warp) + 0.5f;  // centre of the warp's first row
     uint32_t m = 0;
     float lut_scale = 0.f;
     if (MODE == 2) {
@@ -144,22 +161,28 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
         v_next = b + 64 + lane < rg.y ? pair_val[b + 64 + lane] : 0u;
         cp_async_wait<1>();  // this chunk's copies (all but the newest group)
         __syncwarp();
-        const float4* wA = sbuf[buf][0][warp];
-        const float4* wB = sbuf[buf][1][warp];
+        float4* wA = sbuf[buf][0][warp];
+        float4* wB = sbuf[buf][1][warp];
         const float4* wC = sbuf[buf][2][warp];
         const uint32_t nh = __popc(hits_cur);
+        if (lane < nh) blend_prepare(wA[lane], wB[lane], rlo);  // each lane its own slot
+        __syncwarp();
         if (!p.done) {
-            uint32_t i = 0;
+            // rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31): each reads its half of R
+            const float2* wR = reinterpret_cast<const float2*>(wB) + (lane >> 4);
+            uint32_t i = 0, ev = nh;
             for (; i + 2 <= nh; i += 2) {
-                const float4 A0 = wA[i], B0 = wB[i], A1 = wA[i + 1], B1 = wB[i + 1];
-                const float r0 = blend_rho(p, A0, B0), r1 = blend_rho(p, A1, B1);
-                if (!blend_step<MODE>(p, A0, B0, wC, i, r0, s_lut, m, lut_scale)) break;
-                if (!blend_step<MODE>(p, A1, B1, wC, i + 1, r1, s_lut, m, lut_scale)) break;
+                const float4 X0 = wA[i], X1 = wA[i + 1];
+                const float2 R0 = wR[2 * i], R1 = wR[2 * i + 2];
+                const float r0 = blend_rho(p, X0, R0), r1 = blend_rho(p, X1, R1);
+                if (!blend_step<MODE>(p, X0, wC, i, r0, s_lut, m, lut_scale)) { ev = i + 1; break; }
+                if (!blend_step<MODE>(p, X1, wC, i + 1, r1, s_lut, m, lut_scale)) { ev = i + 2; break; }
             }
             if (!p.done && i < nh) {
-                const float4 A0 = wA[i], B0 = wB[i];
-                blend_step<MODE>(p, A0, B0, wC, i, blend_rho(p, A0, B0), s_lut, m, lut_scale);
+                const float4 X0 = wA[i];
+                if (!blend_step<MODE>(p, X0, wC, i, blend_rho(p, X0, wR[2 * i]), s_lut, m, lut_scale)) ev = i + 1;
             }
+            p.evals += ev;
         }
         __syncwarp();  // the walk is done with this buffer before it is refilled
         buf ^= 1;

@@ -92,6 +92,8 @@ __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const Scen
     return o;
 }
 
+constexpr int LOD_UNROLL = 2;  // previous-cut nodes per thread and round
+
 __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__ prev_cut,
                                                     const uint32_t* __restrict__ n_prev_p, uint32_t cap_prev,
                                                     SceneDev sc, const FrameParams* __restrict__ fp,
@@ -154,18 +156,27 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
             out.add(n, cn, ln);  // stay
         }
     };
-    // two nodes per thread and round, their loads in flight together
-    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n_prev; i0 += 2 * stride) {
-        const uint32_t i1 = i0 + stride;
-        const bool has1 = i1 < n_prev;
-        const uint32_t n0 = prev_cut[i0], n1 = has1 ? prev_cut[i1] : n0;
-        const float4 c0 = sc.cr[n0], c1 = sc.cr[n1];
-        const uint32_t p0 = sc.parent[n0], p1 = sc.parent[n1];
-        const float l0 = sc.lmax[n0], l1 = sc.lmax[n1];
-        const float4 q0 = p0 != NONE ? sc.cr[p0] : c0;
-        const float4 q1 = p1 != NONE ? sc.cr[p1] : c1;
-        visit(n0, c0, p0, q0, l0);
-        if (has1) visit(n1, c1, p1, q1, l1);
+    // LOD_UNROLL nodes per thread and round, their loads in flight together
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n_prev; i0 += LOD_UNROLL * stride) {
+        uint32_t nn[LOD_UNROLL], pp[LOD_UNROLL];
+        float4 cc[LOD_UNROLL], qq[LOD_UNROLL];
+        float ll[LOD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LOD_UNROLL; ++u) {
+            const uint32_t i = i0 + u * stride;
+            nn[u] = i < n_prev ? prev_cut[i] : prev_cut[i0];
+        }
+#pragma unroll
+        for (int u = 0; u < LOD_UNROLL; ++u) {
+            cc[u] = sc.cr[nn[u]];
+            pp[u] = sc.parent[nn[u]];
+            ll[u] = sc.lmax[nn[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < LOD_UNROLL; ++u) qq[u] = pp[u] != NONE ? sc.cr[pp[u]] : cc[u];
+#pragma unroll
+        for (int u = 0; u < LOD_UNROLL; ++u)
+            if (i0 + u * stride < n_prev) visit(nn[u], cc[u], pp[u], qq[u], ll[u]);
     }
     // one atomic per warp for the statistics
     uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, evals);
