@@ -39,6 +39,24 @@ namespace vgr {
 // a Gaussian with u + Bx < 0.5 or u - Bx > 16 tiles_x - 0.5 (or likewise in
 // v) has no candidate tile in preprocess and can be left out here.  The
 // canonical mode's 3-sigma box is bounded the same way.
+// Set bit n of bm in the lanes where pred holds, one atomic per run of lanes
+// that hit the same word (callers pass ascending n across the lanes, so a
+// word's lanes are contiguous): a segmented OR by shuffles gives each run's
+// first lane the run's bits.  All 32 lanes call it.
+__device__ __forceinline__ void warp_bitmap_set(uint32_t* bm, uint32_t n, bool pred) {
+    const uint32_t lane = lane_id();
+    const uint32_t w = pred ? n >> 5 : 0xFFFFFFFFu;
+    uint32_t bits = pred ? 1u << (n & 31u) : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t ob = __shfl_down_sync(0xFFFFFFFFu, bits, d);
+        const uint32_t ow = __shfl_down_sync(0xFFFFFFFFu, w, d);
+        if (lane + d < 32u && ow == w) bits |= ob;
+    }
+    const uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, w, 1);
+    if (pred && (lane == 0u || wprev != w)) atomicOr(&bm[w], bits);
+}
+
 struct CutOut {
     uint32_t* cut_bm;
     uint32_t* front_bm;
@@ -46,13 +64,15 @@ struct CutOut {
     float R0, R1, R2, R3, R4, R5, R6, R7, R8, Cx, Cy, Cz, z_near;
     float fx, fy, cx, cy, kx, ky, umax, vmax;
     bool canonical;
-    __device__ __forceinline__ void add(uint32_t n, float4 c) const { add(n, c, lmax[n]); }
-    // lm = lmax[n], loaded by the caller together with the node's centre
-    __device__ __forceinline__ void add(uint32_t n, float4 c, float lm) const {
+    __device__ __forceinline__ void add(uint32_t n, float4 c) const {
         bitmap_set(cut_bm, n);
+        if (in_front(c, lmax[n])) bitmap_set(front_bm, n);
+    }
+    // may node (centre c, lm = lmax[n]) reach the image in front of the near plane?
+    __device__ __forceinline__ bool in_front(float4 c, float lm) const {
         const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
         const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
-        if (!(z > z_near)) return;
+        if (!(z > z_near)) return false;
         const float x = fmaf(R0, dx, fmaf(R1, dy, R2 * dz));
         const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
         const float iz = 1.0f / z;
@@ -67,8 +87,7 @@ struct CutOut {
             bx = by = 3.01f * sqrtf(fmaf(t, kx + ky, 1.0f)) + 1.01f;
         }
         const float su = 1e-5f * fabsf(u) + 1e-2f, sv = 1e-5f * fabsf(v) + 1e-2f;  // FP32 slack
-        if (u + bx < 0.5f - su || u - bx > umax + su || v + by < 0.5f - sv || v - by > vmax + sv) return;
-        bitmap_set(front_bm, n);
+        return !(u + bx < 0.5f - su || u - bx > umax + su || v + by < 0.5f - sv || v - by > vmax + sv);
     }
 };
 
@@ -107,7 +126,8 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     // one previous-cut node: stay, collapse or expand
-    auto visit = [&](uint32_t n, float4 cn, uint32_t p, float4 cp, float ln) {
+    // (a staying node is only reported: its bits are set warp-aggregated below)
+    auto visit = [&](uint32_t n, float4 cn, uint32_t p, float4 cp) -> bool {
         const bool en = lod_expand(cn, px, py, pz, k);
         bool ep = true;
         ++evals;
@@ -153,18 +173,23 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
             }
             evals += local;
         } else {
-            out.add(n, cn, ln);  // stay
+            return true;  // stay
         }
+        return false;
     };
-    // LOD_UNROLL nodes per thread and round, their loads in flight together
-    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n_prev; i0 += LOD_UNROLL * stride) {
+    // LOD_UNROLL nodes per thread and round, their loads in flight together;
+    // warp-uniform rounds so the staying nodes' bits can be set per warp
+    const uint32_t lane = lane_id();
+    for (uint32_t b0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; b0 < n_prev; b0 += LOD_UNROLL * stride) {
         uint32_t nn[LOD_UNROLL], pp[LOD_UNROLL];
         float4 cc[LOD_UNROLL], qq[LOD_UNROLL];
         float ll[LOD_UNROLL];
+        bool ok[LOD_UNROLL];
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {
-            const uint32_t i = i0 + u * stride;
-            nn[u] = i < n_prev ? prev_cut[i] : prev_cut[i0];
+            const uint32_t i = b0 + u * stride + lane;
+            ok[u] = i < n_prev;
+            nn[u] = ok[u] ? prev_cut[i] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {
@@ -175,8 +200,11 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) qq[u] = pp[u] != NONE ? sc.cr[pp[u]] : cc[u];
 #pragma unroll
-        for (int u = 0; u < LOD_UNROLL; ++u)
-            if (i0 + u * stride < n_prev) visit(nn[u], cc[u], pp[u], qq[u], ll[u]);
+        for (int u = 0; u < LOD_UNROLL; ++u) {
+            const bool stay = ok[u] && visit(nn[u], cc[u], pp[u], qq[u]);
+            warp_bitmap_set(bitmap, nn[u], stay);
+            warp_bitmap_set(front, nn[u], stay && out.in_front(cc[u], ll[u]));
+        }
     }
     // one atomic per warp for the statistics
     uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, evals);
