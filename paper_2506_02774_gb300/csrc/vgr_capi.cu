@@ -671,6 +671,10 @@ int tile_passes_for(uint32_t n_tiles) {
     return std::max(1, (bits + 7) / 8);
 }
 
+// The emission's grid relative to the look-back kernels' (x/4): it keeps
+// five CTAs resident per SM, the radix passes four.
+constexpr int EMIT_GRID_NUM = 5;
+
 uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
     return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
@@ -721,7 +725,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
-                tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, s);
+                tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan * EMIT_GRID_NUM / 4, s);
     mark(VGR_STAGE_TILE_SORT);
     for (int p = 0; p < tile_passes; ++p) {
         launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
