@@ -180,7 +180,14 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     // LOD_UNROLL nodes per thread and round, their loads in flight together;
     // warp-uniform rounds so the staying nodes' bits can be set per warp
     const uint32_t lane = lane_id();
-    for (uint32_t b0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; b0 < n_prev; b0 += LOD_UNROLL * stride) {
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+    uint32_t nx[LOD_UNROLL];  // the next round's node ids, loaded one round ahead
+#pragma unroll
+    for (int u = 0; u < LOD_UNROLL; ++u) {
+        const uint32_t i = first + u * stride + lane;
+        nx[u] = i < n_prev ? prev_cut[i] : 0u;
+    }
+    for (uint32_t b0 = first; b0 < n_prev; b0 += LOD_UNROLL * stride) {
         uint32_t nn[LOD_UNROLL], pp[LOD_UNROLL];
         float4 cc[LOD_UNROLL], qq[LOD_UNROLL];
         float ll[LOD_UNROLL];
@@ -189,7 +196,9 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
         for (int u = 0; u < LOD_UNROLL; ++u) {
             const uint32_t i = b0 + u * stride + lane;
             ok[u] = i < n_prev;
-            nn[u] = ok[u] ? prev_cut[i] : 0u;
+            nn[u] = nx[u];
+            const uint32_t inext = i + LOD_UNROLL * stride;
+            nx[u] = inext < n_prev ? prev_cut[inext] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {

@@ -140,14 +140,17 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
     uint32_t n_visible = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     // uniform trip count per warp so the visible count can use a ballot
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n_front; base += stride) {
+    // the next round's node id is loaded one round ahead
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+    uint32_t node_next = first + lane_id() < n_front ? front[first + lane_id()] : 0u;
+    for (uint32_t base = first; base < n_front; base += stride) {
         const uint32_t i = base + lane_id();
         bool v = i < n_front;
-        uint32_t node = 0, zbits = 0xFFFFFFFFu;
+        uint32_t node = node_next, zbits = 0xFFFFFFFFu;
+        node_next = i + stride < n_front ? front[i + stride] : 0u;
         float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f;
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
-            node = front[i];
             const float4 m = sc.cr[node];
             float S[6], lnth = 0.f;
             Store<STORE>::cov(sc, node, S, theta, lnth);  // in flight together with the centre
