@@ -254,9 +254,15 @@ __global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __re
     constexpr int K = (DEG + 1) * (DEG + 1);
     const uint32_t n = min(ctr->n_front, cap);
     const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        if (vis_ntile[r] == 0u) continue;  // culled
-        const uint32_t node = vis_node[r];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    // the next entry's node id and tile count are loaded one round ahead
+    uint32_t node_next = r < n ? vis_node[r] : 0u, nt_next = r < n ? vis_ntile[r] : 0u;
+    for (; r < n; r += stride) {
+        const uint32_t node = node_next, nt = nt_next;
+        node_next = r + stride < n ? vis_node[r + stride] : 0u;
+        nt_next = r + stride < n ? vis_ntile[r + stride] : 0u;
+        if (nt == 0u) continue;  // culled
         float shc[((3 * K + 7) / 8) * 8];
         Store<STORE>::template sh<K>(sc, node, shc);
         const float4 m = sc.cr[node];
