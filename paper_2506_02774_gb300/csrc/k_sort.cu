@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 //     is stored contiguously (coalesced).
 constexpr int LB_BATCH = 8;  // look-back words read per round trip
 
+template <bool HW_MATCH>
 __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
                                                            uint32_t* __restrict__ keys_out,
@@ -115,7 +116,9 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
             const uint32_t d = idx < n ? ((key[it] >> shift) & 255u) : 256u;
-            const uint32_t peers = match_digit(d);
+            // tile ids (few distinct digits per warp): the match instruction; depth
+            // keys (many distinct low digits): one ballot per digit bit, faster there
+            const uint32_t peers = HW_MATCH ? __match_any_sync(0xFFFFFFFFu, d) : match_digit(d);
             const int leader = __ffs(peers) - 1;
             uint32_t before = 0;
             if (d < 256u && (int)lane == leader) before = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
@@ -213,9 +216,13 @@ void launch_radix_hist(const uint32_t* keys, const uint32_t* n32, const unsigned
 void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                        const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
                        const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
-                       Counters* ctr, int grid, cudaStream_t s) {
-    launch_k(k_radix_pass, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32, n64, cap, shift, hist,
-                                             status, ticket, fp, ctr);
+                       Counters* ctr, int grid, cudaStream_t s, int hw_match) {
+    if (hw_match)
+        launch_k(k_radix_pass<true>, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32,
+                  n64, cap, shift, hist, status, ticket, fp, ctr);
+    else
+        launch_k(k_radix_pass<false>, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32,
+                  n64, cap, shift, hist, status, ticket, fp, ctr);
 }
 
 }  // namespace vgr

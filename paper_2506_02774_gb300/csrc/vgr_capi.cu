@@ -731,7 +731,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
         launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
                           &v->ctr->n_cand, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
                           v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
-                          v->fp_dev, v->ctr, v->grid_scan, s);
+                          v->fp_dev, v->ctr, v->grid_scan, s, 1);
     }
     const int fb = tile_passes & 1;
     v->last_tile_buf = fb;

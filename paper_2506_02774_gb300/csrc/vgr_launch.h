@@ -17,11 +17,12 @@ void set_last_error(const char* msg);
 // off (plain stream order).
 bool pdl_enabled();
 template <typename... KArgs, typename... Args>
-inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+inline void launch_ks(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                      Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -29,6 +30,10 @@ inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cu
     cfg.attrs = attr;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    launch_ks(kernel, grid, block, 0, s, args...);
 }
 
 struct SceneDev;
@@ -74,7 +79,7 @@ void launch_radix_hist(const uint32_t* keys, const uint32_t* n32, const unsigned
 void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                        const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
                        const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
-                       Counters* ctr, int grid, cudaStream_t s);
+                       Counters* ctr, int grid, cudaStream_t s, int hw_match = 0);
 
 // k_emit.cu
 void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
