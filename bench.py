@@ -119,6 +119,28 @@ def _traffic(kernel: str, source: str, algorithmic: float):
     return int(d["dram_bytes_per_launch"])
 
 
+def rank_walk(cfg: dict, rank: int):
+    """(heading, start) of rank's walk: rank 0 the workload's own walk, rank r
+    the parallel street 40 r m over (replicas: every rank renders its own
+    frames of its own scene copy)."""
+    if rank == 0:
+        return 0.0, None
+    start = list(cfg["start"])
+    start[1] += 40.0 * rank
+    return 0.0, start
+
+
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The job's time: the maximum of x over the ranks (no-op for one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,10 +200,7 @@ def run_ours(args) -> dict:
     nfr = cfg["frames"]
     W, H = cfg["width"], cfg["height"]
     # each rank walks its own street (replicas: no data-path collective)
-    heading, start = 0.0, None
-    if rank:
-        start = list(cfg["start"])
-        start[1] += 40.0 * rank
+    heading, start = rank_walk(cfg, rank)
     cams = [scenegen.trajectory(wl["scene"], f % nfr, heading, start) for f in range(args.warmup + args.steps)]
     structs = [vgr.camera_struct(c) for c in cams]
 
@@ -208,11 +227,7 @@ def run_ours(args) -> dict:
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        ms = ev0.elapsed_time(ev1)
-        if ws > 1:
-            tt = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
         return ms, lat, stats, kernels
 
     # ---- timed regions: the plain launch loop, then the headline view
