@@ -4,20 +4,21 @@
 //
 // One CTA of 256 threads per tile, one pixel per thread; warp w shades pixel
 // rows 2w and 2w+1 and walks the tile's pair range on its own (no CTA-wide
-// barrier).  Each pair value carries the Gaussian's depth rank and its row
-// mask in the tile (set by the emission from the footprint box: outside the
-// box rho < ln alpha* - ln theta holds with a margin, so a pair whose box
-// misses the warp's two rows would fail the Eq. 4 test at every one of its
-// pixels).  The warp reads 32 pair values at a time (coalesced), keeps those
-// with its row bit, and copies their 48-byte records (mean, conic,
-// threshold, opacity, colour) with cp.async into its own double-buffered slice of shared memory; the copies
-// of the next 32 pairs are in flight while the current ones are walked, two
-// at a time for instruction-level parallelism.  Before the walk each lane
-// rewrites its staged record for the warp's two rows (the row offsets of the
-// mean folded into the conic terms), so a pixel evaluates rho with one
-// subtraction and two FMAs.  Records are read only for
-// the pairs a warp needs, and the eight warps of a tile share them through
-// L1.  A warp stops when its 32 pixels have stopped; tiles crossing the
+// barrier).  Each pair value carries the Gaussian's index in the in-front
+// arrays and its row mask in the tile (set by the emission from the
+// footprint box: outside the box rho < ln alpha* - ln theta holds with a
+// margin, so a pair whose box misses the warp's two rows would fail the
+// Eq. 4 test at every one of its pixels); within a tile the pairs are in
+// depth order.  The warp reads 32 pair values at a time (coalesced), keeps
+// those with its row bit, and copies their 48-byte records (mean, conic,
+// threshold, opacity, colour) with cp.async into its own double-buffered
+// slice of shared memory; the copies of the next 32 pairs are in flight
+// while the current ones are walked, two at a time for instruction-level
+// parallelism.  Before the walk each lane rewrites its staged record for the
+// warp's two rows (the row offsets of the mean folded into the conic
+// terms), so a pixel evaluates rho with one subtraction and two FMAs.
+// Records are read only for the pairs a warp needs, and the eight warps of
+// a tile share them through L1.  A warp stops when its 32 pixels have stopped; tiles crossing the
 // horizon (tens of thousands of small distant Gaussians, each reaching one
 // or two rows) cost each warp a scan of 4-byte values and a fraction of the
 // records.  Per pixel:

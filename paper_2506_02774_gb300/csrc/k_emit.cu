@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
         // gather EM_ITEMS Gaussians per thread (independent loads in flight)
 #pragma unroll
         for (int k = 0; k < EM_ITEMS; ++k) {
-            const uint32_t q = k * EM_THREADS + threadIdx.x;  // position in rank order within the tile
+            const uint32_t q = k * EM_THREADS + threadIdx.x;  // position in depth order within the CTA tile
             const uint32_t r = tile * EM_TILE + q;
             uint32_t area = 0;
             if (r < n_vis) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
             s_off[q] = area;
         }
         __syncthreads();
-        // exclusive scan of the candidate counts in rank order: thread t owns entries
+        // exclusive scan of the candidate counts in depth order: thread t owns entries
         // EM_ITEMS t .. EM_ITEMS t + EM_ITEMS - 1
         uint32_t a4[EM_ITEMS];
         uint32_t sum = 0;

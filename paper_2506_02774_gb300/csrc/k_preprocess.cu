@@ -18,8 +18,8 @@
 // when it has at least one candidate tile; the tile-level test (Eq. 4 over
 // each candidate tile) runs in the emission, where the work is balanced over
 // candidate slots.  Colour (real SH up to degree 3, +0.5, clamped at 0) is a
-// separate dense kernel over the visible list, so the 192-byte SH reads run
-// at full occupancy, outside the ordered scan, in ascending node order.
+// separate dense kernel over the in-front list (visible entries only), so
+// the 192-byte SH reads run at full occupancy, in ascending node order.
 #include <cuda_fp16.h>
 
 #include "vgr_internal.cuh"
