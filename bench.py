@@ -104,17 +104,29 @@ OPS_PER_EVAL = 9      # 2 FADD (dx, dy), 4 FMUL + 2 FFMA (rho), 1 compare (Eq. 4
 OPS_PER_CONTRIB = 10  # FMUL (exp argument), FMUL (theta e^rho), min, 1 - alpha, T', compare, alpha T, 3 FFMA, + 1 MUFU
 
 
+def code_sha256(path: str) -> str:
+    """SHA-256 of a source file's code: // comments and blank space removed,
+    so an edit of comments alone keeps the hash."""
+    import hashlib
+    import re
+    lines = []
+    for line in open(path).read().splitlines():
+        code = re.sub(r"//.*$", "", line).strip()
+        if code:
+            lines.append(" ".join(code.split()))
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def _traffic(kernel: str, source: str, algorithmic: float):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), used only while the kernel's source is the one
-    the counters were taken on (sha256 of csrc/<source>); else None."""
-    import hashlib
+    (profiles/traffic.json), used only while the kernel's code is the one the
+    counters were taken on (code_sha256 of csrc/<source>); else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2506_02774_gb300", "csrc", source)
     if not os.path.exists(p) or not os.path.exists(src):
         return None
     d = json.load(open(p)).get(kernel)
-    if not d or d.get("source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+    if not d or d.get("code_sha256") != code_sha256(src):
         return None
     return int(d["dram_bytes_per_launch"])
 
