@@ -1,13 +1,15 @@
 // vgr_capi.cu -- the C ABI (include/vgr.h): hierarchy upload and validation,
 // per-view buffers, and the per-frame launch sequence
 //   LoD (temporal update or top-down levels) -> cut compaction ->
-//   preprocess -> depth sort -> emission -> tile sort -> ranges -> blend
-// all enqueued on the view's stream.  Counts stay on the device (every
-// kernel reads its element count from device memory), so a frame needs no
-// host round trip until its end, where a 48-byte status block is read back:
-// buffer overflows are handled by growing the buffer and replaying the
-// frame, a temporal update that ran past its budget by replaying the frame
-// with the top-down cut.
+//   preprocess -> depth sort -> colour -> emission -> tile sort -> ranges
+//   and blend order -> blend
+// all enqueued on the view's stream (or replayed as one captured graph).
+// Counts stay on the device (every kernel reads its element count from
+// device memory), so a frame needs no host round trip until its end, where
+// a 56-byte status block and the cut sizes are read back: buffer overflows
+// are handled by growing the buffer and replaying the frame, a temporal
+// update that ran past its budget by replaying the frame with the top-down
+// cut.
 #include <cuda_runtime.h>
 
 #include <algorithm>
