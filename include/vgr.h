@@ -203,8 +203,10 @@ vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes);
 vgr_status vgr_render_frame(vgr_view* v, const vgr_camera* cam, float tau, vgr_frame* out);
 
 /*
- * As vgr_render_frame, then copies the image into host memory host_rgb
- * (height x width x 3 floats, caller-owned; pinned memory is fastest).
+ * As vgr_render_frame, and the image also lands in host memory host_rgb
+ * (height x width x 3 floats, caller-owned).  Pinned memory of this view's
+ * device is written by the blend itself, over the host link while the frame
+ * runs; any other memory receives a copy after the frame.
  */
 vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb,
                                  vgr_frame* out);

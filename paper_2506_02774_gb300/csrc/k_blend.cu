@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     __shared__ __align__(16) float4 sbuf[2][3][BL_WARPS][32];
     __shared__ float s_lut[260];
     const uint32_t W = fp->width, H = fp->height, TW = fp->tiles_x;
+    float* const host_image = fp->host_image;
     const uint32_t tile = tile_order[blockIdx.x];  // heaviest tiles first
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t px = (tile % TW) * TILE + (lane & (TILE - 1));
@@ -191,10 +192,17 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     }
     cp_async_wait<0>();
     if (inside) {
-        float* o = image + ((size_t)py * W + px) * 3;
+        const size_t at = ((size_t)py * W + px) * 3;
+        float* o = image + at;
         o[0] = p.cr;
         o[1] = p.cg;
         o[2] = p.cb;
+        if (host_image) {  // the caller's pinned host buffer, over the host link
+            float* q = host_image + at;
+            q[0] = p.cr;
+            q[1] = p.cg;
+            q[2] = p.cb;
+        }
     }
     const uint32_t wsum = __reduce_add_sync(FULL, p.evals);
     const uint32_t csum = __reduce_add_sync(FULL, p.contribs);

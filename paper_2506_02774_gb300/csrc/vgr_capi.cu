@@ -102,6 +102,7 @@ struct PendingFrame {
     int tile_passes = 1;
     uint32_t kernels = 0;
     float* host = nullptr;
+    float* host_dev = nullptr;  // device address of host when the blend can write it directly
 };
 
 struct vgr_view {
@@ -800,7 +801,20 @@ vgr_status check_camera(const vgr_camera* c, float tau) {
     return VGR_OK;
 }
 
-void fill_params(vgr_view* v, const vgr_camera* cam, float k) {
+// Device address of a host image buffer the GPU can write directly (pinned
+// memory of this device), or null: then the image is copied after the frame.
+float* mapped_host(const vgr_view* v, float* host) {
+    if (!host) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != v->h->device) return nullptr;
+    return static_cast<float*>(a.devicePointer);
+}
+
+void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
     const uint32_t W = cam->width, H = cam->height;
     FrameParams& p = *v->fp_host;
     memcpy(p.R, cam->R, sizeof(p.R));
@@ -819,6 +833,7 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float k) {
     p.lut_step = 5.55f / (float)v->opts.lut_size;
     p.lod_budget = v->opts.lod_budget;
     p.max_depth = v->h->max_depth;
+    p.host_image = host_dev;
 }
 
 // Enqueue the frame (and the image copy to host_rgb, if given) and record the
@@ -844,9 +859,10 @@ vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
     q.f = f;
     q.k = k;
     q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
-    fill_params(v, cam, q.k);
+    q.host_dev = mapped_host(v, host_rgb);
+    fill_params(v, cam, q.k, q.host_dev);
     if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
-    if (host_rgb)
+    if (host_rgb && !q.host_dev)
         VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
                                v->stream));
     VGR_CK(cudaEventRecord(v->done_ev, v->stream));
@@ -899,9 +915,9 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         if (!again) break;
         if (attempt >= 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt + 1);
         ++replays;
-        fill_params(v, &q.cam, q.k);
+        fill_params(v, &q.cam, q.k, q.host_dev);
         if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
-        if (q.host)
+        if (q.host && !q.host_dev)
             VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
                                    v->stream));
         VGR_CK(cudaStreamSynchronize(v->stream));

@@ -203,6 +203,21 @@ def test_render_host_matches_device(tiny_scene, tiny_h):
     v.close()
 
 
+def test_render_host_pinned_matches_device(tiny_scene, tiny_h):
+    """Pinned host buffers are written by the blend directly; the result is
+    the device image, also after an overflow replay and under graph replay."""
+    for kw in (dict(), dict(use_graph=True), dict(pair_capacity=16, use_graph=True)):
+        v = vgr.View(tiny_h, **kw)
+        for fr in (0, 1, 2):
+            cam = scenegen.trajectory("tiny", fr)
+            out = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, pin_memory=True)
+            fres = vgr._abi.Frame()
+            vgr._abi.check(v.render_host_ptr(vgr.camera_struct(cam), 3.0, out.data_ptr(), fres))
+            r = vgr.FrameResult(fres)
+            assert np.array_equal(out.numpy(), _img(r))
+        v.close()
+
+
 def test_half_storage_error(small_sh3_scene):
     """FP16 SH + BF16 covariance: within 2e-3 of the oracle run on the
     quantized scene; the error against the FP32 scene is reported."""
