@@ -598,7 +598,7 @@ def main():
     ap.add_argument("--serve-clients", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--serve-sweep", default="12,16,20,24,28,32", help="per-client request rates of the load sweep")
+    ap.add_argument("--serve-sweep", default="12,16,20,24,28,32,40,48", help="per-client request rates of the load sweep")
     ap.add_argument("--sweep-seconds", type=float, default=4.0)
     ap.add_argument("--p99-bound", type=float, default=25.0, help="p99 latency bound (ms) of the load sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -233,7 +233,10 @@ vgr_status vgr_finish_frame(vgr_view* v, vgr_frame* out);
  * One frame on each of n distinct views (own camera, tau and image size
  * each; the views may share a hierarchy): every frame is submitted, then
  * every frame is finished in order, so frames of views on different streams
- * overlap on the GPU.  host_rgb is NULL or n pointers (NULL entries: no host
+ * overlap on the GPU.  When every view uses graph replay on a stream of its
+ * own (created with stream 0, no stage timing), the whole batch runs as one
+ * captured CUDA graph, cached per combination of views, cut modes, buffer
+ * parities and image sizes.  host_rgb is NULL or n pointers (NULL entries: no host
  * copy); outs is NULL or n frames.  Returns the first error (VGR_E_INVALID
  * for a repeated or NULL view, before anything is submitted); every frame
  * that was submitted is finished.  The paper renders one view at a time;

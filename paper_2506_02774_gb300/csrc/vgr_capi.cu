@@ -13,10 +13,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -163,6 +165,9 @@ struct vgr_view {
     bool pending = false;
     PendingFrame pend;
     cudaEvent_t done_ev = nullptr;
+    cudaEvent_t join_ev = nullptr;  // end of this view's branch in a captured batch
+    uint64_t uid = 0;               // unique per view ever created (batch graph keys)
+    uint64_t gen = 0;               // bumped whenever the view's buffers change (graphs invalid)
     uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
 };
 
@@ -398,10 +403,39 @@ vgr_status vgr_hierarchy_info(const vgr_hierarchy* h, uint64_t* bytes, uint32_t*
 // ------------------------------------------------------------------ views
 namespace {
 
+// Captured batches (vgr_render_batch): one graph runs every view's frame as
+// a parallel branch.  Keyed by each view's id, buffer generation, cut mode,
+// buffer parity and tile grid; a few recent ones are kept per process.
+struct BatchGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batches;
+uint64_t g_batch_clock = 0;
+constexpr size_t BATCH_GRAPHS_KEPT = 8;
+
+void forget_batches(uint64_t uid) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        bool hit = false;
+        for (size_t k = 0; k < g_batches[i].key.size(); k += 6)
+            if (g_batches[i].key[k] == uid) hit = true;
+        if (hit) {
+            cudaGraphExecDestroy(g_batches[i].exec);
+            g_batches.erase(g_batches.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 void drop_graphs(vgr_view* v) {
     for (auto& row : v->graph)
         for (auto& g : row)
             if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    ++v->gen;  // batch graphs holding this view's buffers no longer match
 }
 
 void free_vis(vgr_view* v) {
@@ -526,6 +560,8 @@ void destroy_view(vgr_view* v) {
     for (auto& e : v->ev)
         if (e) cudaEventDestroy(e);
     if (v->done_ev) cudaEventDestroy(v->done_ev);
+    if (v->join_ev) cudaEventDestroy(v->join_ev);
+    forget_batches(v->uid);
     if (v->own_stream && v->stream) cudaStreamDestroy(v->stream);
     delete v;
 }
@@ -600,7 +636,10 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     }
     {
         cudaError_t ce = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->join_ev, cudaEventDisableTiming);
         if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
+        static std::atomic<uint64_t> next_uid{1};
+        v->uid = next_uid.fetch_add(1);
     }
     // Eq. 5 table: entry i = e^(-5.55 i / m), i = 0..m
     {
@@ -838,7 +877,9 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
 
 // Enqueue the frame (and the image copy to host_rgb, if given) and record the
 // view's completion event; nothing waits.
-vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+// Validate a frame and set up its parameters (pinned fp_host) without
+// launching anything.
+vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
     if (!v) return fail(VGR_E_INVALID, "null view");
     if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is already in flight");
     vgr_status s = check_camera(cam, tau);
@@ -861,12 +902,101 @@ vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
     q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
     q.host_dev = mapped_host(v, host_rgb);
     fill_params(v, cam, q.k, q.host_dev);
-    if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
-    if (host_rgb && !q.host_dev)
-        VGR_CK(cudaMemcpyAsync(host_rgb, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
-                               v->stream));
-    VGR_CK(cudaEventRecord(v->done_ev, v->stream));
+    return VGR_OK;
+}
+
+// After the frame's kernels (on stream s): the host copy when the blend does
+// not write the host buffer itself, and the completion event.
+vgr_status close_frame(vgr_view* v, cudaStream_t s) {
+    PendingFrame& q = v->pend;
+    if (q.host && !q.host_dev)
+        VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)q.cam.width * q.cam.height * 3 * sizeof(float),
+                               cudaMemcpyDeviceToHost, s));
+    VGR_CK(cudaEventRecord(v->done_ev, s));
     v->pending = true;
+    return VGR_OK;
+}
+
+vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+    vgr_status s = prepare_frame(v, cam, tau, host_rgb);
+    if (s != VGR_OK) return s;
+    PendingFrame& q = v->pend;
+    const uint32_t TW = (q.cam.width + TILE - 1) / TILE, TH = (q.cam.height + TILE - 1) / TILE;
+    if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
+    return close_frame(v, v->stream);
+}
+
+// Per device: the stream batches are launched on and its fork event.
+struct BatchStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr;
+};
+BatchStream g_bstream[64];
+
+// All views prepared: run their frames as one captured graph (captured on
+// first use of this combination).
+vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
+    const int dev = views[0]->h->device;
+    if (dev < 0 || dev >= 64) return fail(VGR_E_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchStream& bs = g_bstream[dev];
+    if (!bs.s) {
+        VGR_CK(cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking));
+        VGR_CK(cudaEventCreateWithFlags(&bs.fork, cudaEventDisableTiming));
+    }
+    std::vector<uint64_t> key;
+    key.reserve((size_t)n * 6);
+    for (uint32_t i = 0; i < n; ++i) {
+        const vgr_view* v = views[i];
+        const PendingFrame& q = v->pend;
+        const uint64_t tiles = (uint64_t)((q.cam.width + TILE - 1) / TILE) * ((q.cam.height + TILE - 1) / TILE);
+        key.insert(key.end(), {v->uid, v->gen, (uint64_t)q.scratch, (uint64_t)v->parity, tiles,
+                               (uint64_t)q.tile_passes});
+    }
+    BatchGraph* bg = nullptr;
+    for (auto& b : g_batches)
+        if (b.key == key) bg = &b;
+    if (!bg) {
+        VGR_CK(cudaStreamBeginCapture(bs.s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaEventRecord(bs.fork, bs.s);
+        for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+            vgr_view* v = views[i];
+            e = cudaStreamWaitEvent(v->stream, bs.fork, 0);
+            if (e != cudaSuccess) break;
+            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes);
+            e = cudaEventRecord(v->join_ev, v->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(bs.s, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VGR_E_CUDA, "batch capture: %s", cudaGetErrorString(e));
+        }
+        if (g_batches.size() >= BATCH_GRAPHS_KEPT) {  // evict the least recently used
+            size_t old = 0;
+            for (size_t i = 1; i < g_batches.size(); ++i)
+                if (g_batches[i].last_use < g_batches[old].last_use) old = i;
+            cudaGraphExecDestroy(g_batches[old].exec);
+            g_batches.erase(g_batches.begin() + (long)old);
+        }
+        g_batches.push_back(BatchGraph{key, exec, 0});
+        bg = &g_batches.back();
+    }
+    bg->last_use = ++g_batch_clock;
+    VGR_CK(cudaGraphLaunch(bg->exec, bs.s));
+    for (uint32_t i = 0; i < n; ++i) {
+        vgr_view* v = views[i];
+        v->last_tile_buf = v->pend.tile_passes & 1;
+        v->pend.kernels += frame_kernels(v, v->pend.scratch, v->pend.tile_passes);
+        vgr_status s = close_frame(v, bs.s);
+        if (s != VGR_OK) return s;
+    }
     return VGR_OK;
 }
 
@@ -1003,8 +1133,41 @@ vgr_status vgr_render_batch(vgr_view* const* views, const vgr_camera* cams, cons
         for (uint32_t j = 0; j < i; ++j)
             if (views[j] == views[i]) return fail(VGR_E_INVALID, "views[%u] and views[%u] are the same view", j, i);
     }
-    // submit every view, then finish them in order; on a failed submission
-    // the views already submitted are still finished
+    // every view replaying captured frames on its own stream, none in flight:
+    // one graph for the whole batch
+    bool whole = n >= 2;
+    for (uint32_t i = 0; i < n && whole; ++i) {
+        const vgr_view* v = views[i];
+        whole = v->opts.use_graph && !v->opts.timing && !v->pending && v->own_stream &&
+                v->h->device == views[0]->h->device;
+    }
+    if (whole) {
+        uint32_t prepared = 0;
+        vgr_status s = VGR_OK;
+        for (; prepared < n; ++prepared) {
+            s = prepare_frame(views[prepared], &cams[prepared], taus[prepared], host_rgb ? host_rgb[prepared] : nullptr);
+            if (s != VGR_OK) return s;  // nothing has been launched
+        }
+        if ((s = launch_batch_graph(views, n)) != VGR_OK) {
+            for (uint32_t i = 0; i < n; ++i)
+                if (views[i]->pending) {  // launched: wait for it, keep the first error
+                    const std::string msg = g_err;
+                    finish_impl(views[i], nullptr);
+                    g_err = msg;
+                }
+            return s;
+        }
+        vgr_status first = VGR_OK;
+        std::string first_msg;
+        for (uint32_t i = 0; i < n; ++i) {
+            const vgr_status f = finish_impl(views[i], outs ? &outs[i] : nullptr);
+            if (f != VGR_OK && first == VGR_OK) { first = f; first_msg = g_err; }
+        }
+        if (first != VGR_OK) g_err = first_msg;
+        return first;
+    }
+    // otherwise submit every view, then finish them in order; on a failed
+    // submission the views already submitted are still finished
     uint32_t submitted = 0;
     vgr_status first = VGR_OK;
     std::string first_msg;

@@ -132,3 +132,30 @@ def test_server_admission_refusal(h_small):
     res = sv.serve(_trace(2, 2, 500.0, 6))
     assert (res["status"] == 2).all()  # VGR_E_NOMEM: not admitted, nothing rendered
     sv.close()
+
+
+def test_whole_batch_graph_equals_individual(small_sh3_scene, h_small):
+    """Every view replays captured frames on its own stream: the batch runs
+    as one captured graph (re-captured when a view's buffers grow, reused
+    when the combination repeats) and each frame equals the view rendered
+    alone, over several frames and both buffer parities."""
+    n = len(SIZES)
+    batch = [vgr.View(h_small, use_graph=True, pair_capacity=(16 if i == 1 else 0)) for i in range(n)]
+    solo = [vgr.View(h_small) for _ in range(n)]
+    walks = [_cams(i, 5, SIZES[i]) for i in range(n)]
+    for k in range(5):
+        cams = [walks[i][k] for i in range(n)]
+        pinned = [torch.empty((c["height"], c["width"], 3), dtype=torch.float32, pin_memory=True) for c in cams]
+        hosts = [pinned[0].numpy(), None, np.empty((cams[2]["height"], cams[2]["width"], 3), np.float32), None]
+        res = vgr.render_batch(batch, cams, [3.0] * n, hosts)
+        for i in range(n):
+            r = solo[i].render(cams[i], 3.0)
+            np.testing.assert_array_equal(res[i].cut().cpu().numpy(), r.cut().cpu().numpy())
+            img = res[i].image().cpu().numpy()
+            assert np.array_equal(img, r.image().cpu().numpy())
+            if hosts[i] is not None:
+                assert np.array_equal(hosts[i], img)
+        if k == 0:
+            assert res[1].stats["replays"] >= 1  # the small pair buffer grew
+    for v in batch + solo:
+        v.close()
