@@ -116,7 +116,13 @@ typedef struct {
                                 0 = 8 per SM.  Launch geometry only: results do not depend on it. */
     uint32_t grid_scan;      /* CTAs of the ticketed look-back kernels (compaction, radix passes,
                                 emission); 0 = 4 per SM.  Launch geometry only. */
+    uint32_t test_hooks;     /* 0 in normal use.  VGR_HOOK_WITHHOLD_LOOKBACK: the emission's first
+                                tile never publishes its look-back word, so the later tiles' bounded
+                                waits run out and every frame reports VGR_E_TIMEOUT (the device
+                                stays usable); for testing the timeout path. */
 } vgr_view_opts;
+
+enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1 };
 
 enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT, VGR_STAGE_COLOR,
        VGR_STAGE_EMIT, VGR_STAGE_TILE_SORT, VGR_STAGE_RANGES, VGR_STAGE_BLEND, VGR_N_STAGES };

@@ -146,7 +146,7 @@ class View:
     def __init__(self, hier: Hierarchy, *, filter: int = FILTER_PREEMPTIVE, exp_mode: int = EXP_EXACT,
                  lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
                  cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, grid_wide: int = 0,
-                 grid_scan: int = 0, stream=None):
+                 grid_scan: int = 0, test_hooks: int = 0, stream=None):
         lib = _abi.load()
         o = _abi.ViewOpts()
         lib.vgr_default_view_opts(ctypes.byref(o))
@@ -156,6 +156,7 @@ class View:
         if lod_budget:
             o.lod_budget = lod_budget
         o.grid_wide, o.grid_scan = int(grid_wide), int(grid_scan)
+        o.test_hooks = int(test_hooks)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(stream))
         v = ctypes.c_void_p()

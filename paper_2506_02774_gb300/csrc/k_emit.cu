@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict_
 #pragma unroll
         for (int k = 0; k < EM_ITEMS; ++k) { s_off[EM_ITEMS * threadIdx.x + k] = run; run += a4[k]; }
         if (threadIdx.x < 32) {
-            const uint32_t pre = lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
+            // (test hook: tile 0 stays silent, so the others' bounded waits run out)
+            const bool silent = tile == 0 && (fp->test_hooks & VGR_HOOK_WITHHOLD_LOOKBACK);
+            const uint32_t pre = silent ? 0u : lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
             if (threadIdx.x == 0) {
                 s_off[EM_TILE] = total;
                 s_prefix = pre;

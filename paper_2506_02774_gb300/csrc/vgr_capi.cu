@@ -55,7 +55,13 @@ template <typename T>
 vgr_status dalloc(T** p, size_t count, uint64_t* acct) {
     *p = nullptr;
     if (count == 0) count = 1;
-    VGR_CK(cudaMalloc((void**)p, count * sizeof(T)));
+    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();  // not sticky: clear it so later launches are not blamed
+        return fail(e == cudaErrorMemoryAllocation ? VGR_E_NOMEM : VGR_E_CUDA, "cudaMalloc of %zu bytes: %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
     VGR_CK(cudaMemset(*p, 0, count * sizeof(T)));
     if (acct) *acct += count * sizeof(T);
     return VGR_OK;
@@ -278,17 +284,26 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     {
         const size_t shb = (size_t)N * stride * (half ? 2 : 4);
         cudaError_t e = cudaMalloc(&h->sh, shb);
-        if (e != cudaSuccess) { cleanup(); return fail(VGR_E_NOMEM, "cudaMalloc sh (%zu bytes): %s", shb, cudaGetErrorString(e)); }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return fail(VGR_E_NOMEM, "cudaMalloc sh (%zu bytes): %s", shb, cudaGetErrorString(e));
+        }
         h->bytes += shb;
     }
     // staging in chunks through a pinned buffer
     const uint32_t CH = 1u << 20;
     void* pin = nullptr;
     const size_t pin_bytes = (size_t)CH * std::max<size_t>(64, (size_t)K3 * 4);
-    if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) { cleanup(); return fail(VGR_E_NOMEM, "pinned staging"); }
+    if (cudaMallocHost(&pin, pin_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(VGR_E_NOMEM, "pinned staging");
+    }
     float* tmp_dev = nullptr;
     if (half) {
         if (cudaMalloc(&tmp_dev, (size_t)CH * std::max<uint32_t>(K3, 6) * 4) != cudaSuccess) {
+            cudaGetLastError();
             cudaFreeHost(pin); cleanup(); return fail(VGR_E_NOMEM, "conversion buffer");
         }
     }
@@ -625,6 +640,7 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     if (cudaMallocHost((void**)&v->fp_host, sizeof(FrameParams)) != cudaSuccess ||
         cudaMallocHost((void**)&v->ctr_host, sizeof(Counters)) != cudaSuccess ||
         cudaMallocHost((void**)&v->vstate_host, sizeof(ViewState)) != cudaSuccess) {
+        cudaGetLastError();
         destroy_view(v);
         return fail(VGR_E_NOMEM, "pinned host buffers");
     }
@@ -873,6 +889,7 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
     p.lod_budget = v->opts.lod_budget;
     p.max_depth = v->h->max_depth;
     p.host_image = host_dev;
+    p.test_hooks = v->opts.test_hooks;
 }
 
 // Enqueue the frame (and the image copy to host_rgb, if given) and record the

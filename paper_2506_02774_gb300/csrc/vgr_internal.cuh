@@ -56,8 +56,8 @@ struct FrameParams {
     float lut_step;    // 5.55 / m
     uint32_t lod_budget;
     uint32_t max_depth;
-    uint32_t pad0;
-    float* host_image;  // device-accessible pinned host image the blend also writes, or null
+    uint32_t test_hooks;  // vgr_view_opts.test_hooks (0 in normal use)
+    float* host_image;    // device-accessible pinned host image the blend also writes, or null
 };
 
 // Zeroed at the start of every frame.  Scalars first: the host reads back
