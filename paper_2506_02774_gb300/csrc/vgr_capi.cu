@@ -11,6 +11,7 @@
 // update that ran past its budget by replaying the frame with the top-down
 // cut.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -934,7 +935,14 @@ vgr_status close_frame(vgr_view* v, cudaStream_t s) {
     return VGR_OK;
 }
 
+// NVTX range for tools that show the host timeline (ncu --nvtx, Nsight Systems)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+    NvtxRange r("vgr submit frame");
     vgr_status s = prepare_frame(v, cam, tau, host_rgb);
     if (s != VGR_OK) return s;
     PendingFrame& q = v->pend;
@@ -953,6 +961,7 @@ BatchStream g_bstream[64];
 // All views prepared: run their frames as one captured graph (captured on
 // first use of this combination).
 vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
+    NvtxRange r("vgr batch graph");
     const int dev = views[0]->h->device;
     if (dev < 0 || dev >= 64) return fail(VGR_E_INVALID, "device index out of range");
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -1021,6 +1030,7 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
 // temporal update fell back or a buffer overflowed, and commit the view's
 // temporal state.
 vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
+    NvtxRange r("vgr finish frame");
     if (!v) return fail(VGR_E_INVALID, "null view");
     if (!v->pending) return fail(VGR_E_INVALID, "no frame of this view is in flight");
     v->pending = false;

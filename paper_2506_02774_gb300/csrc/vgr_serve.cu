@@ -14,6 +14,7 @@
 // Host code only: the frames themselves go through vgr_submit_frame /
 // vgr_frame_done / vgr_finish_frame.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -147,6 +148,7 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
         }
     }
     for (uint32_t i = 0; i < n; ++i) res[i] = vgr_request_result{};
+    nvtxRangePushA("vgr serve trace");
     const uint32_t C = (uint32_t)sv->clients.size();
     std::vector<int64_t> inflight(C, -1);  // request index in flight per client
     std::deque<uint32_t> arrived;          // arrived and not started, arrival order
@@ -221,6 +223,7 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
             }
         }
     }
+    nvtxRangePop();
     return first_err;
 }
 
