@@ -241,19 +241,25 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
     uint32_t evals = 0;
     for (uint32_t base = warp_global * 32u; base < n_in; base += nwarps * 32u) {
         const uint32_t i = base + lane;
-        uint32_t cnt = 0, first = 0;
+        uint32_t cnt = 0, first = 0, n = 0;
+        bool is_cut = false, in_front = false;
         if (i < n_in) {
-            const uint32_t n = level == 0 ? 0u : fin[i];
+            n = level == 0 ? 0u : fin[i];
             const float4 cn = sc.cr[n];
+            const float lm = sc.lmax[n];
             ++evals;
             if (lod_expand(cn, px, py, pz, k)) {
                 const uint32_t c = sc.child[n];
                 first = c & CHILD_MASK;
                 cnt = c >> CHILD_SHIFT;
             } else {
-                out.add(n, cn);
+                is_cut = true;
+                in_front = out.in_front(cn, lm);
             }
         }
+        // one atomic per bitmap word and warp (a node's siblings are neighbours)
+        warp_bitmap_set(bitmap, n, is_cut);
+        warp_bitmap_set(front, n, in_front);
         uint32_t total;
         const uint32_t off = warp_excl_scan(cnt, &total);
         uint32_t basepos = 0;
