@@ -310,6 +310,64 @@ def run_ours(args) -> dict:
                          lod_ms_top_down=round(float(np.mean(lod_s)), 4))
         vr.close()
         vs.close()
+        # across granularities (Sec. 2 motivation): the share of an exhaustive
+        # pass over all nodes that the top-down traversal never needs, and the
+        # cut overlap between consecutive frames
+        levels = []
+        for tau_l in (1.5, 3.0, 6.0, 12.0, 24.0):
+            vr = vgr.View(h, stream=stream.cuda_stream, timing=True)
+            vs = vgr.View(h, stream=stream.cuda_stream, temporal=False, timing=True)
+            ia, ib = min(i0, len(cams) - 2), min(i0, len(cams) - 2) + 1
+            for i in range(max(0, ia - 2), ia):
+                vr.render(cams[i], tau_l)
+            ca = vr.render(cams[ia], tau_l).cut().cpu().numpy().copy()
+            b = vr.render(cams[ib], tau_l)
+            cb = b.cut().cpu().numpy().copy()
+            s_ = vs.render(cams[ib], tau_l)
+            common = int(np.intersect1d(ca, cb, assume_unique=True).size)
+            levels.append(dict(tau=tau_l, cut=int(cb.size), overlap=round(common / max(1, cb.size), 5),
+                               exhaustive_redundant=round(1.0 - s_.stats["nodes_evaluated"] / h.n_nodes, 4),
+                               nodes_evaluated_temporal=b.stats["nodes_evaluated"],
+                               nodes_evaluated_top_down=s_.stats["nodes_evaluated"],
+                               lod_ms_temporal=round(b.stats["stage_ms"]["lod"], 4),
+                               lod_ms_top_down=round(s_.stats["stage_ms"]["lod"], 4)))
+            vr.close()
+            vs.close()
+        lod_reuse.update(nodes=h.n_nodes, by_tau=levels)
+
+    # ---- frustum-aware granularity test (node boxes against the view
+    # frustum widened by 2 pixels): the same walk, timed like the headline
+    frustum_lod = None
+    if sc.get("bbox") is not None and not args.no_frustum:
+        vf = vgr.View(h, stream=stream.cuda_stream, use_graph=not args.no_graph, lod_frustum=True)
+        msf, _, stf, _ = timed(vf)
+        vf.close()
+        vft = vgr.View(h, stream=stream.cuda_stream, timing=True, lod_frustum=True)
+        vd = vgr.View(h, stream=stream.cuda_stream)
+        for i in range(args.warmup):
+            vft.render(cams[i], tau)
+        st_ms, n_st = np.zeros(3), min(args.steps, 50)
+        for i in range(args.warmup, args.warmup + n_st):
+            r_f = vft.render(cams[i], tau)
+            st_ms += np.array([r_f.stats["stage_ms"][k] for k in ("lod", "compact", "preprocess")])
+        st_ms /= n_st
+        i1 = args.warmup + n_st - 1  # the last frame above, against the distance-only cut
+        vd.render(cams[i1 - 1], tau)
+        r_d = vd.render(cams[i1], tau)
+        img_f, img_d = r_f.image().double(), r_d.image().double()
+        mse = float(((img_f - img_d) ** 2).mean())
+        frustum_lod = dict(value=round(frames / (msf / 1e3), 2), unit="frames/s",
+                           ms_per_step=round(msf / args.steps, 4), guard_px=2.0,
+                           cut=round(float(np.mean([x["cut_count"] for x in stf])), 1),
+                           front=round(float(np.mean([x["front_count"] for x in stf])), 1),
+                           visible=round(float(np.mean([x["visible_count"] for x in stf])), 1),
+                           replays=int(sum(x["replays"] for x in stf)),
+                           stage_ms=dict(lod=round(st_ms[0], 4), compact=round(st_ms[1], 4),
+                                         preprocess=round(st_ms[2], 4)),
+                           psnr_vs_distance_only_db=round(10 * math.log10(1.0 / mse), 2) if mse > 0 else None,
+                           max_abs_vs_distance_only=round(float((img_f - img_d).abs().max()), 5))
+        vft.close()
+        vd.close()
 
     # ---- end to end through the host-buffer entry point
     host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
@@ -380,6 +438,7 @@ def run_ours(args) -> dict:
                counts={k: round(v, 1) for k, v in mean.items()},
                lod_reuse=lod_reuse,
                half_store=half_store,
+               frustum_lod=frustum_lod,
                setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
     view.close()
     if args.config == "city" and not args.leaves and not args.no_served:
@@ -592,6 +651,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batch leg")
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16-store run of the walk")
     ap.add_argument("--no-lod-reuse", action="store_true", help="skip the cut-reuse statistics")
+    ap.add_argument("--no-frustum", action="store_true", help="skip the frustum-aware LoD run of the walk")
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)

@@ -70,6 +70,11 @@ typedef struct vgr_view vgr_view;
  *   radius2  1 float, squared node radius R^2 of the granularity test; the
  *            radii must nest (R_parent >= R_child + |mean_parent - mean_child|)
  *            for the cut to be well defined under the test below.
+ *   bbox     6 floats or NULL: axis-aligned node box lo x, y, z, hi x, y, z,
+ *            nested exactly (a child's box inside its parent's); needed only
+ *            by the frustum-aware granularity test (vgr_view_opts.lod_frustum).
+ *            A box that covers the node's Gaussian and its subtree keeps that
+ *            variant from coarsening anything that reaches the image.
  */
 typedef struct {
     uint32_t n_nodes;
@@ -83,6 +88,7 @@ typedef struct {
     const float* sh;
     const float* radius2;
     int32_t storage; /* VGR_STORE_* */
+    const float* bbox; /* optional, see above */
 } vgr_scene_desc;
 
 /*
@@ -120,6 +126,9 @@ typedef struct {
                                 tile never publishes its look-back word, so the later tiles' bounded
                                 waits run out and every frame reports VGR_E_TIMEOUT (the device
                                 stays usable); for testing the timeout path. */
+    uint32_t lod_frustum;    /* 1: frustum-aware granularity test (needs bbox; default 0), see
+                                vgr_render_frame */
+    float lod_frustum_guard; /* pixels the frustum test adds beyond each image edge (default 2) */
 } vgr_view_opts;
 
 enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1 };
@@ -201,6 +210,16 @@ vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes);
  * with f = max(fx, fy), t = fl(tau / f), k = fl(t t) and single-rounded FP32
  * arithmetic:  d2 = (dx dx + dy dy) + dz dz,  (dx, dy, dz) = pos - mean[n],
  * expand(n) = n_child[n] > 0 and fl(d2 k) < radius2[n]   (Sec. 3.1).
+ * With lod_frustum set, expand(n) also needs n's box to meet the view
+ * frustum widened by g = lod_frustum_guard pixels (the tree "identifies the
+ * Gaussians inside the view frustum", Sec. 3.1): for each of five planes
+ * (camera-space inward normal a, offset o_c: near (0, 0, 1), z_near; left
+ * (fx, 0, cx + g), right (-fx, 0, W - cx + g), top (0, fy, cy + g), bottom
+ * (0, -fy, H - cy + g), 0) take w_j = fl32(fma(R2j, a2, fma(R1j, a1, R0j a0)))
+ * and o = fl32(fma(w2, pos2, fma(w1, pos1, w0 pos0)) + o_c) in FP64, the box
+ * corner X furthest along w (hi where w_j >= 0, else lo) and require
+ * fl(fl(fl(w0 X0) + fl(w1 X1)) + fl(w2 X2)) - o >= 0 (single-rounded FP32).
+ * Nested boxes keep this monotone, so the temporal update stays exact.
  * Between frames with equal tau and f the cut is updated from the previous
  * one (Sec. 4.1, Algorithm 1); the result equals the top-down cut.
  * Requires 0 <= tau <= f, width, height in [1, 16384], z_near > 0.

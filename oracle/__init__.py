@@ -43,7 +43,7 @@ class _Scene(ctypes.Structure):
                 ("parent", ctypes.c_void_p), ("first_child", ctypes.c_void_p),
                 ("n_child", ctypes.c_void_p), ("mean", ctypes.c_void_p),
                 ("cov6", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
-                ("sh", ctypes.c_void_p), ("radius2", ctypes.c_void_p)]
+                ("sh", ctypes.c_void_p), ("radius2", ctypes.c_void_p), ("bbox", ctypes.c_void_p)]
 
 
 class _Camera(ctypes.Structure):
@@ -81,17 +81,21 @@ def _load():
             P = ctypes.c_void_p
             lib.orc_lod_k.argtypes = [ctypes.c_float, ctypes.c_float]
             lib.orc_lod_k.restype = ctypes.c_float
-            lib.orc_expand_node.argtypes = [ctypes.POINTER(_Scene), ctypes.c_uint32, P, ctypes.c_float]
+            lib.orc_expand_node.argtypes = [ctypes.POINTER(_Scene), ctypes.c_uint32, P, ctypes.c_float, P]
             lib.orc_expand_node.restype = ctypes.c_int
             for fn in (lib.orc_cut_topdown, lib.orc_cut_bruteforce):
-                fn.argtypes = [ctypes.POINTER(_Scene), P, ctypes.c_float, P]
+                fn.argtypes = [ctypes.POINTER(_Scene), P, ctypes.c_float, P, P]
                 fn.restype = ctypes.c_int64
+            lib.orc_frustum_planes.argtypes = [ctypes.POINTER(_Camera), ctypes.c_float, P]
+            lib.orc_frustum_planes.restype = None
+            lib.orc_box_meets.argtypes = [P, P]
+            lib.orc_box_meets.restype = ctypes.c_int
             lib.orc_sh_basis.argtypes = [ctypes.c_int, P, P]
             lib.orc_sh_basis.restype = None
             lib.orc_rho_max_rect.argtypes = [P] + [ctypes.c_double] * 6
             lib.orc_rho_max_rect.restype = ctypes.c_double
             lib.orc_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_float,
-                                       P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+                                       P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_float]
             lib.orc_render.restype = ctypes.POINTER(_Frame)
             lib.orc_frame_free.argtypes = [ctypes.POINTER(_Frame)]
             lib.orc_frame_free.restype = None
@@ -117,7 +121,12 @@ class _SceneRef:
         assert a[0].dtype == np.uint32 and a[1].dtype == np.uint32 and a[2].dtype == np.uint8
         for x in a[3:]:
             assert x.dtype == np.float32
-        self.s = _Scene(int(sc["n_nodes"]), int(sc["sh_degree"]), *[_ptr(x) for x in a])
+        box = sc.get("bbox")
+        if box is not None:
+            box = np.ascontiguousarray(box, np.float32)
+            self.arrays.append(box)
+        self.s = _Scene(int(sc["n_nodes"]), int(sc["sh_degree"]), *[_ptr(x) for x in a[:8]],
+                        _ptr(box) if box is not None else None)
 
 
 def _camera(cam: dict) -> _Camera:
@@ -147,20 +156,46 @@ def lod_k(tau: float, f: float) -> np.float32:
     return np.float32(_load().orc_lod_k(float(np.float32(tau)), float(np.float32(f))))
 
 
-def expand(sc: dict, node: int, cam_pos, k) -> bool:
+def frustum_planes(cam: dict, guard: float) -> np.ndarray:
+    """The five (w0, w1, w2, o) planes of the frustum-aware test (5 x 4 float32)."""
+    c = _camera(cam)
+    out = np.zeros((5, 4), np.float32)
+    _load().orc_frustum_planes(ctypes.byref(c), float(np.float32(guard)), _ptr(out))
+    return out
+
+
+def box_meets(box6, planes) -> bool:
+    """Does the box (lo xyz, hi xyz) meet all five half-spaces?"""
+    b = np.ascontiguousarray(box6, np.float32)
+    pl = np.ascontiguousarray(planes, np.float32)
+    return bool(_load().orc_box_meets(_ptr(b), _ptr(pl)))
+
+
+def _planes_arg(planes):
+    if planes is None:
+        return None, None
+    pl = np.ascontiguousarray(planes, np.float32).reshape(20)
+    return pl, _ptr(pl)
+
+
+def expand(sc: dict, node: int, cam_pos, k, planes=None) -> bool:
+    """The granularity test (with the frustum-aware box test when ``planes`` is given)."""
     ref = _SceneRef(sc)
     p = np.asarray(cam_pos, np.float32)
-    return bool(_load().orc_expand_node(ctypes.byref(ref.s), node, _ptr(p), float(np.float32(k))))
+    keep, pp = _planes_arg(planes)
+    return bool(_load().orc_expand_node(ctypes.byref(ref.s), node, _ptr(p), float(np.float32(k)), pp))
 
 
-def cut(sc: dict, cam_pos, k, bruteforce: bool = False) -> np.ndarray:
-    """Ascending node ids of the cut for camera position ``cam_pos`` and ``k``."""
+def cut(sc: dict, cam_pos, k, bruteforce: bool = False, planes=None) -> np.ndarray:
+    """Ascending node ids of the cut for camera position ``cam_pos`` and ``k``
+    (frustum-aware when ``planes``, from :func:`frustum_planes`, is given)."""
     lib = _load()
     ref = _SceneRef(sc)
     p = np.ascontiguousarray(cam_pos, np.float32)
     out = np.empty(max(1, int(sc["n_nodes"])), np.uint32)
     fn = lib.orc_cut_bruteforce if bruteforce else lib.orc_cut_topdown
-    n = fn(ctypes.byref(ref.s), _ptr(p), float(np.float32(k)), _ptr(out))
+    keep, pp = _planes_arg(planes)
+    n = fn(ctypes.byref(ref.s), _ptr(p), float(np.float32(k)), pp, _ptr(out))
     if n < 0:
         raise MemoryError("oracle cut")
     return out[:n].copy()
@@ -188,7 +223,7 @@ def _arr(ptr, dtype, n):
 
 
 def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-3, t_flag: float = 0.05,
-           exhaustive: bool = False) -> dict:
+           exhaustive: bool = False, frustum_guard: float | None = None) -> dict:
     """Render one frame; returns the cut, per-cut projection, pairs and image.
 
     ``tile_mask`` (bool per tile, row-major) restricts binning and blending
@@ -196,6 +231,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     ``band`` (nats) of ln alpha* - ln theta while the transmittance is still
     >= ``t_flag``: there an FP32 renderer may take the other side of the
     alpha >= alpha* test and move the pixel by up to ~alpha* T max(rgb).
+    ``frustum_guard`` (pixels; needs ``sc["bbox"]``) selects the
+    frustum-aware cut.
     """
     lib = _load()
     ref = _SceneRef(sc)
@@ -207,7 +244,7 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
         mask = np.ascontiguousarray(np.asarray(tile_mask, bool).reshape(TW * TH).astype(np.uint8))
     fp = lib.orc_render(ctypes.byref(ref.s), ctypes.byref(c), float(np.float32(tau)),
                         _ptr(mask) if mask is not None else None, float(band), float(t_flag),
-                        int(bool(exhaustive)))
+                        int(bool(exhaustive)), float(-1.0 if frustum_guard is None else frustum_guard))
     if not fp:
         raise MemoryError("oracle render")
     try:

@@ -17,6 +17,19 @@
  *        d2 = (dx*dx + dy*dy) + dz*dz
  *        expand(n) = n has children  and  fl(d2 * k) < radius2[n]
  *     (compiled with -ffp-contract=off: no FMA contraction).
+ *  1b. Frustum-aware variant (the tree also "identifies the Gaussians inside
+ *     the view frustum", Sec. 3.1; the paper gives no test, this is the
+ *     reading used): expand(n) additionally needs n's axis-aligned box to
+ *     meet five half-spaces.  In camera space their inward normals a and
+ *     offsets o_c are: near (0,0,1), z_near; left (fx, 0, cx+g); right
+ *     (-fx, 0, W-cx+g); top (0, fy, cy+g); bottom (0, -fy, H-cy+g); o_c = 0
+ *     for the four sides (planes through the camera centre and the image
+ *     edges moved out by g pixels).  World normal w = R^T a and offset
+ *     o = w . C + o_c, computed in FP64 with correctly rounded fma in the
+ *     order w_j = fma(R[2][j], a2, fma(R[1][j], a1, R[0][j] a0)), rounded to
+ *     FP32, then o = fma(w2, C2, fma(w1, C1, w0 C0)) + o_c rounded to FP32.
+ *     The box corner X furthest along w (hi where w_j >= 0, else lo) is
+ *     tested: fl(fl(fl(w0 X0) + fl(w1 X1)) + fl(w2 X2)) - o >= 0.
  *  2. Cut = { n : every strict ancestor expands and n does not }, found by a
  *     plain top-down traversal from the root.  A brute-force form (walk the
  *     ancestor chain of every node) is provided as a cross-check.
@@ -71,6 +84,7 @@ typedef struct {
     const float* opacity;        /* N */
     const float* sh;             /* N * (deg+1)^2 * 3, coefficient-major */
     const float* radius2;        /* N */
+    const float* bbox;           /* 6N: lo xyz, hi xyz (frustum-aware variant only) */
 } orc_scene;
 
 typedef struct {
@@ -94,18 +108,63 @@ float orc_lod_k(float tau, float f) {
     return t * t;
 }
 
-static int orc_expand(const orc_scene* s, uint32_t n, const float cam[3], float k) {
+/* 1b: the five planes as (w0, w1, w2, o) in planes[4 i ..] */
+void orc_frustum_planes(const orc_camera* cam, float guard, float planes[20]) {
+    double g = guard, W = cam->width, H = cam->height;
+    double a[5][3] = {{0.0, 0.0, 1.0},
+                      {cam->fx, 0.0, (double)cam->cx + g},
+                      {-(double)cam->fx, 0.0, (W - cam->cx) + g},
+                      {0.0, cam->fy, (double)cam->cy + g},
+                      {0.0, -(double)cam->fy, (H - cam->cy) + g}};
+    double oc[5] = {cam->z_near, 0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < 5; ++i) {
+        float w[3];
+        for (int j = 0; j < 3; ++j) {
+            /* (R^T a)_j = sum over camera axes r of R[r][j] a_r */
+            double acc = (double)cam->R[0 * 3 + j] * a[i][0];
+            acc = fma((double)cam->R[1 * 3 + j], a[i][1], acc);
+            acc = fma((double)cam->R[2 * 3 + j], a[i][2], acc);
+            w[j] = (float)acc;
+        }
+        double o = (double)w[0] * (double)cam->pos[0];
+        o = fma((double)w[1], (double)cam->pos[1], o);
+        o = fma((double)w[2], (double)cam->pos[2], o);
+        planes[4 * i + 0] = w[0];
+        planes[4 * i + 1] = w[1];
+        planes[4 * i + 2] = w[2];
+        planes[4 * i + 3] = (float)(o + oc[i]);
+    }
+}
+
+/* 1b: does the box lo[3], hi[3] meet every half-space w . x - o >= 0? */
+int orc_box_meets(const float box[6], const float planes[20]) {
+    for (int i = 0; i < 5; ++i) {
+        const float* p = planes + 4 * i;
+        float X = p[0] >= 0.0f ? box[3] : box[0];
+        float Y = p[1] >= 0.0f ? box[4] : box[1];
+        float Z = p[2] >= 0.0f ? box[5] : box[2];
+        float t0 = p[0] * X, t1 = p[1] * Y, t2 = p[2] * Z;
+        float sum = (t0 + t1) + t2;
+        float sd = sum - p[3];
+        if (!(sd >= 0.0f)) return 0;
+    }
+    return 1;
+}
+
+/* planes == NULL: the distance test of step 1 alone; else also step 1b */
+static int orc_expand(const orc_scene* s, uint32_t n, const float cam[3], float k, const float* planes) {
     if (s->n_child[n] == 0) return 0;
     float dx = cam[0] - s->mean[3 * (size_t)n + 0];
     float dy = cam[1] - s->mean[3 * (size_t)n + 1];
     float dz = cam[2] - s->mean[3 * (size_t)n + 2];
     float d2 = (dx * dx + dy * dy) + dz * dz;
     float lhs = d2 * k;
-    return lhs < s->radius2[n];
+    if (!(lhs < s->radius2[n])) return 0;
+    return planes ? orc_box_meets(s->bbox + 6 * (size_t)n, planes) : 1;
 }
 
-int orc_expand_node(const orc_scene* s, uint32_t n, const float cam[3], float k) {
-    return orc_expand(s, n, cam, k);
+int orc_expand_node(const orc_scene* s, uint32_t n, const float cam[3], float k, const float* planes) {
+    return orc_expand(s, n, cam, k, planes);
 }
 
 static int orc_cmp_u32(const void* a, const void* b) {
@@ -116,7 +175,7 @@ static int orc_cmp_u32(const void* a, const void* b) {
 /* ------------------------------------------------------------ 2. the cut */
 /* Top-down traversal from the root; out must hold n_nodes ids; returns |C|
  * with the ids in ascending order. */
-int64_t orc_cut_topdown(const orc_scene* s, const float cam[3], float k, uint32_t* out) {
+int64_t orc_cut_topdown(const orc_scene* s, const float cam[3], float k, const float* planes, uint32_t* out) {
     if (s->n_nodes == 0) return 0;
     uint32_t* stack = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)s->n_nodes);
     if (!stack) return -1;
@@ -124,7 +183,7 @@ int64_t orc_cut_topdown(const orc_scene* s, const float cam[3], float k, uint32_
     stack[sp++] = 0;
     while (sp > 0) {
         uint32_t n = stack[--sp];
-        if (orc_expand(s, n, cam, k)) {
+        if (orc_expand(s, n, cam, k, planes)) {
             for (uint32_t c = 0; c < s->n_child[n]; ++c) stack[sp++] = s->first_child[n] + c;
         } else {
             out[nc++] = n;
@@ -137,13 +196,13 @@ int64_t orc_cut_topdown(const orc_scene* s, const float cam[3], float k, uint32_
 
 /* The definition read literally: n is in the cut iff it does not expand and
  * every node on its ancestor chain does. */
-int64_t orc_cut_bruteforce(const orc_scene* s, const float cam[3], float k, uint32_t* out) {
+int64_t orc_cut_bruteforce(const orc_scene* s, const float cam[3], float k, const float* planes, uint32_t* out) {
     int64_t nc = 0;
     for (uint32_t n = 0; n < s->n_nodes; ++n) {
-        if (orc_expand(s, n, cam, k)) continue;
+        if (orc_expand(s, n, cam, k, planes)) continue;
         int ok = 1;
         for (uint32_t a = s->parent[n]; a != 0xFFFFFFFFu; a = s->parent[a])
-            if (!orc_expand(s, a, cam, k)) { ok = 0; break; }
+            if (!orc_expand(s, a, cam, k, planes)) { ok = 0; break; }
         if (ok) out[nc++] = n;
     }
     return nc;
@@ -427,16 +486,20 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
  * Render one frame.  tile_mask (optional, n_tiles bytes) restricts binning
  * and blending to the flagged tiles.  band and t_flag parameterise the
  * ambiguity flag (see orc_blend_pixel).  exhaustive != 0 selects mode 7.
+ * frustum_guard >= 0 (with s->bbox) selects the frustum-aware cut (1b).
  */
 orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, const uint8_t* tile_mask,
-                      double band, double t_flag, int exhaustive) {
+                      double band, double t_flag, int exhaustive, float frustum_guard) {
     orc_frame* F = (orc_frame*)calloc(1, sizeof(orc_frame));
     if (!F) return NULL;
     float f = cam->fx > cam->fy ? cam->fx : cam->fy;
     float k = orc_lod_k(tau, f);
     F->cut = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(s->n_nodes ? s->n_nodes : 1));
     if (!F->cut) { orc_frame_free(F); return NULL; }
-    F->n_cut = orc_cut_topdown(s, cam->pos, k, F->cut);
+    float planes[20];
+    const int frustum = frustum_guard >= 0.0f && s->bbox;  /* step 1b when a guard is given */
+    if (frustum) orc_frustum_planes(cam, frustum_guard, planes);
+    F->n_cut = orc_cut_topdown(s, cam->pos, k, frustum ? planes : NULL, F->cut);
     if (F->n_cut < 0) { orc_frame_free(F); return NULL; }
     int64_t nc = F->n_cut;
     F->proj = (orc_proj*)calloc((size_t)(nc ? nc : 1), sizeof(orc_proj));

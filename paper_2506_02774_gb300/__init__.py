@@ -89,7 +89,13 @@ class Hierarchy:
         assert a[0].dtype == np.uint32 and a[1].dtype == np.uint32 and a[2].dtype == np.uint8
         for x in a[3:]:
             assert x.dtype == np.float32
-        d = _abi.SceneDesc(int(scene["n_nodes"]), int(scene["sh_degree"]), *[_ptr(x) for x in a], int(storage))
+        box = scene.get("bbox")
+        if box is not None:
+            box = np.ascontiguousarray(box, np.float32)
+            assert box.shape == (int(scene["n_nodes"]), 6)
+            self._keep.append(box)
+        d = _abi.SceneDesc(int(scene["n_nodes"]), int(scene["sh_degree"]), *[_ptr(x) for x in a[:8]], int(storage),
+                           _ptr(box) if box is not None else None)
         h = ctypes.c_void_p()
         _abi.check(lib.vgr_load_hierarchy(ctypes.byref(d), ctypes.byref(h)))
         self._keep = None  # the library copied everything
@@ -146,7 +152,8 @@ class View:
     def __init__(self, hier: Hierarchy, *, filter: int = FILTER_PREEMPTIVE, exp_mode: int = EXP_EXACT,
                  lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
                  cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, grid_wide: int = 0,
-                 grid_scan: int = 0, test_hooks: int = 0, stream=None):
+                 grid_scan: int = 0, test_hooks: int = 0, lod_frustum: bool = False,
+                 lod_frustum_guard: float = 2.0, stream=None):
         lib = _abi.load()
         o = _abi.ViewOpts()
         lib.vgr_default_view_opts(ctypes.byref(o))
@@ -157,6 +164,7 @@ class View:
             o.lod_budget = lod_budget
         o.grid_wide, o.grid_scan = int(grid_wide), int(grid_scan)
         o.test_hooks = int(test_hooks)
+        o.lod_frustum, o.lod_frustum_guard = int(lod_frustum), float(lod_frustum_guard)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(stream))
         v = ctypes.c_void_p()

@@ -21,7 +21,7 @@ STAGES = ["lod", "compact", "preprocess", "depth_sort", "color", "emit", "tile_s
 class SceneDesc(ctypes.Structure):
     _fields_ = [("n_nodes", c_u32), ("sh_degree", c_u32), ("parent", c_vp), ("first_child", c_vp),
                 ("n_child", c_vp), ("mean", c_vp), ("cov6", c_vp), ("opacity", c_vp), ("sh", c_vp),
-                ("radius2", c_vp), ("storage", c_i32)]
+                ("radius2", c_vp), ("storage", c_i32), ("bbox", c_vp)]
 
 
 class Camera(ctypes.Structure):
@@ -33,7 +33,7 @@ class ViewOpts(ctypes.Structure):
     _fields_ = [("stream", c_vp), ("filter", c_u32), ("exp_mode", c_u32), ("lut_size", c_u32),
                 ("temporal", c_u32), ("timing", c_u32), ("use_graph", c_u32), ("cut_capacity", c_u64),
                 ("pair_capacity", c_u64), ("lod_budget", c_u32), ("grid_wide", c_u32), ("grid_scan", c_u32),
-                ("test_hooks", c_u32)]
+                ("test_hooks", c_u32), ("lod_frustum", c_u32), ("lod_frustum_guard", c_f32)]
 
 
 class FrameStats(ctypes.Structure):

@@ -113,6 +113,7 @@ __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const Scen
 
 constexpr int LOD_UNROLL = 2;  // previous-cut nodes per thread and round
 
+template <bool FR>
 __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__ prev_cut,
                                                     const uint32_t* __restrict__ n_prev_p, uint32_t cap_prev,
                                                     SceneDev sc, const FrameParams* __restrict__ fp,
@@ -123,15 +124,23 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const uint32_t budget = fp->lod_budget, max_depth = fp->max_depth;
     const CutOut out = make_cut_out(fp, sc, bitmap, front);
+    LodFrustum fr;
+    if (FR) fr.load(fp, sc.box);
+    // the granularity test, and in the frustum-aware variant the box test
+    auto expand = [&](uint32_t node, float4 c) -> bool {
+        if (!lod_expand(c, px, py, pz, k)) return false;
+        if constexpr (FR) return fr.meets(node);
+        return true;
+    };
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     // one previous-cut node: stay, collapse or expand
     // (a staying node is only reported: its bits are set warp-aggregated below)
     auto visit = [&](uint32_t n, float4 cn, uint32_t p, float4 cp) -> bool {
-        const bool en = lod_expand(cn, px, py, pz, k);
+        const bool en = expand(n, cn);
         bool ep = true;
         ++evals;
-        if (p != NONE) { ep = lod_expand(cp, px, py, pz, k); ++evals; }
+        if (p != NONE) { ep = expand(p, cp); ++evals; }
         if (!ep) {
             if (en) flags |= F_NONMONOTONE;
             // collapse: climb while the parent of a does not expand
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
                 if (pa == NONE) break;
                 ++evals;
                 const float4 cpa = sc.cr[pa];
-                if (lod_expand(cpa, px, py, pz, k)) break;
+                if (expand(pa, cpa)) break;
                 a = pa;
                 ca = cpa;
                 if (steps > max_depth) { flags |= F_LOD_FALLBACK; break; }
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
                 const uint32_t m = nxt[sp - 1]++;
                 if (++local > budget) { flags |= F_LOD_FALLBACK; break; }
                 const float4 cm = sc.cr[m];
-                if (lod_expand(cm, px, py, pz, k)) {
+                if (expand(m, cm)) {
                     if (sp == MAX_TREE_DEPTH) { flags |= F_LOD_FALLBACK; break; }
                     const uint32_t chm = sc.child[m];
                     nxt[sp] = chm & CHILD_MASK;
@@ -225,6 +234,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
 }
 
 // One level of the top-down traversal.  Level 0 starts from the root.
+template <bool FR>
 __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __restrict__ fin,
                                                    uint32_t* __restrict__ fout, uint32_t cap, SceneDev sc,
                                                    const FrameParams* __restrict__ fp,
@@ -235,6 +245,8 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
     uint32_t* n_out = &ctr->frontier_n[level + 1];
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const CutOut out = make_cut_out(fp, sc, bitmap, front);
+    LodFrustum fr;
+    if (FR) fr.load(fp, sc.box);
     const uint32_t lane = lane_id();
     const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
             const float4 cn = sc.cr[n];
             const float lm = sc.lmax[n];
             ++evals;
-            if (lod_expand(cn, px, py, pz, k)) {
+            if (lod_expand(cn, px, py, pz, k) && (!FR || fr.meets(n))) {
                 const uint32_t c = sc.child[n];
                 first = c & CHILD_MASK;
                 cnt = c >> CHILD_SHIFT;
@@ -358,14 +370,16 @@ __global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitm
 // ------------------------------------------------------------ launchers
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
                        const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                       cudaStream_t s) {
-    launch_k(k_lod_update, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
+                       bool frustum, cudaStream_t s) {
+    if (frustum) launch_k(k_lod_update<true>, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
+    else launch_k(k_lod_update<false>, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
 }
 
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                      cudaStream_t s) {
-    launch_k(k_lod_level, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
+                      bool frustum, cudaStream_t s) {
+    if (frustum) launch_k(k_lod_level<true>, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
+    else launch_k(k_lod_level<false>, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
 }
 
 void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,

@@ -96,6 +96,7 @@ struct vgr_hierarchy {
     float4* covA = nullptr;
     float4* covB = nullptr;
     float* lmax = nullptr;
+    float2* box = nullptr;  // nested node boxes (optional)
     void* sh = nullptr;
     uint32_t n_nodes = 0, max_depth = 0;
     uint64_t bytes = 0;
@@ -192,6 +193,8 @@ void vgr_default_view_opts(vgr_view_opts* o) {
     o->timing = 0;
     o->use_graph = 0;
     o->lod_budget = 4096;
+    o->lod_frustum = 0;
+    o->lod_frustum_guard = 2.0f;
 }
 
 // ------------------------------------------------------------- hierarchy
@@ -248,6 +251,19 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
             if (std::sqrt((double)d->radius2[p]) < need * (1.0 - 1e-6))
                 return fail(VGR_E_INVALID, "radius of node %u does not contain child %u (nesting violated)", p, n);
         }
+        if (d->bbox) {
+            const float* b = d->bbox + 6 * (size_t)n;
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(b[a]) || !std::isfinite(b[3 + a]) || !(b[a] <= b[3 + a]))
+                    return fail(VGR_E_INVALID, "box of node %u invalid", n);
+            if (n > 0) {
+                const float* bp = d->bbox + 6 * (size_t)d->parent[n];
+                for (int a = 0; a < 3; ++a)
+                    if (!(bp[a] <= b[a] && bp[3 + a] >= b[3 + a]))
+                        return fail(VGR_E_INVALID, "box of node %u does not contain child %u (nesting violated)",
+                                    d->parent[n], n);
+            }
+        }
     }
 
     int dev = 0;
@@ -267,7 +283,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     const uint32_t stride = half ? (K3 + 7u) / 8u * 8u : (K3 + 3u) / 4u * 4u;
     vgr_status st = VGR_OK;
     auto cleanup = [&]() { dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
-                           if (h->sh) cudaFree(h->sh); delete h; };
+                           dfree(h->box); if (h->sh) cudaFree(h->sh); delete h; };
 #define VGR_TRY(x)                 \
     do {                           \
         st = (x);                  \
@@ -282,6 +298,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     VGR_TRY(dalloc(&h->covA, N, &h->bytes));
     VGR_TRY(dalloc(&h->covB, N, &h->bytes));
     VGR_TRY(dalloc(&h->lmax, N, &h->bytes));
+    if (d->bbox) VGR_TRY(dalloc(&h->box, 3 * (size_t)N, &h->bytes));
     {
         const size_t shb = (size_t)N * stride * (half ? 2 : 4);
         cudaError_t e = cudaMalloc(&h->sh, shb);
@@ -325,6 +342,14 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
         }
         if (ce == cudaSuccess) ce = cudaMemcpy(h->child + b, u, cnt * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(h->parent + b, d->parent + b, cnt * 4, cudaMemcpyHostToDevice);
+        if (d->bbox) {
+            float2* f2 = (float2*)pin;  // (lo, hi) per axis
+            for (uint32_t i = 0; i < cnt; ++i) {
+                const float* bb = d->bbox + 6 * (size_t)(b + i);
+                for (int a = 0; a < 3; ++a) f2[3 * i + a] = make_float2(bb[a], bb[3 + a]);
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpy(h->box + 3 * (size_t)b, f2, (size_t)cnt * 24, cudaMemcpyHostToDevice);
+        }
         {
             // largest absolute row sum of the covariance >= its largest eigenvalue;
             // widened for the rounding of the stored (FP32 or BF16) covariance
@@ -389,6 +414,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     h->dev.covA = h->covA;
     h->dev.covB = h->covB;
     h->dev.lmax = h->lmax;
+    h->dev.box = h->box;
     h->dev.sh = h->sh;
     h->dev.n_nodes = N;
     h->dev.sh_degree = d->sh_degree;
@@ -402,6 +428,7 @@ vgr_status vgr_free_hierarchy(vgr_hierarchy* h) {
     if (!h) return fail(VGR_E_INVALID, "null hierarchy");
     cudaSetDevice(h->device);
     dfree(h->cr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
+    dfree(h->box);
     if (h->sh) cudaFree(h->sh);
     delete h;
     return VGR_OK;
@@ -601,6 +628,14 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     if (v->opts.lut_size == 0) v->opts.lut_size = 32;
     if (v->opts.lut_size > 256) { delete v; return fail(VGR_E_INVALID, "lut_size must be <= 256"); }
     if (v->opts.lod_budget == 0) v->opts.lod_budget = 4096;
+    if (v->opts.lod_frustum && !h->box) {
+        delete v;
+        return fail(VGR_E_INVALID, "lod_frustum needs node boxes (vgr_scene_desc.bbox)");
+    }
+    if (v->opts.lod_frustum && !(v->opts.lod_frustum_guard >= 0.f && v->opts.lod_frustum_guard <= 1e6f)) {
+        delete v;
+        return fail(VGR_E_INVALID, "lod_frustum_guard must be in [0, 1e6] pixels");
+    }
     const uint32_t N = h->n_nodes;
     vgr_status s = VGR_OK;
 #define VGR_VTRY(x)                 \
@@ -757,10 +792,10 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     if (scratch) {
         for (uint32_t level = 0; level <= v->h->max_depth; ++level)
             launch_lod_level((int)level, sc, v->frontier[level & 1], v->frontier[(level + 1) & 1], v->h->n_nodes,
-                             v->fp_dev, v->bitmap, v->front_bm, v->ctr, v->grid_wide, s);
+                             v->fp_dev, v->bitmap, v->front_bm, v->ctr, v->grid_wide, fh.lod_frustum != 0, s);
     } else {
         launch_lod_update(sc, v->cut[prev], &v->vstate->n_cut[prev], v->cap_cut, v->fp_dev, v->bitmap, v->front_bm,
-                          v->ctr, v->grid_wide, s);
+                          v->ctr, v->grid_wide, fh.lod_frustum != 0, s);
     }
     mark(VGR_STAGE_COMPACT);
     launch_cut_compact(v->bitmap, v->front_bm, v->n_words, v->cut[cur], v->front_list, v->cap_cut,
@@ -870,6 +905,38 @@ float* mapped_host(const vgr_view* v, float* host) {
     return static_cast<float*>(a.devicePointer);
 }
 
+// Planes of the frustum-aware granularity test.  Camera-space inward
+// normals a with camera-space offset o_c (near: a = (0, 0, 1), o_c = z_near;
+// the sides pass through the camera centre and the image edges moved out by
+// g pixels: left (fx, 0, cx + g), right (-fx, 0, W - cx + g), top
+// (0, fy, cy + g), bottom (0, -fy, H - cy + g), o_c = 0).  With p_cam =
+// R (x - pos) the world normal is w = R^T a and the offset o = w . pos + o_c:
+//   w_j = fl32(fma(R2j, a2, fma(R1j, a1, R0j a0)))   (FP64, correctly rounded fma)
+//   o   = fl32(fma(w2, pos2, fma(w1, pos1, w0 pos0)) + o_c)
+// Explicit fmas keep the values identical on every host compiler.
+void frustum_planes(const vgr_camera* cam, float guard, float out[5][4]) {
+    const double g = guard, fx = cam->fx, fy = cam->fy, cx = cam->cx, cy = cam->cy;
+    const double W = cam->width, H = cam->height;
+    const double a[5][4] = {{0.0, 0.0, 1.0, (double)cam->z_near},
+                            {fx, 0.0, cx + g, 0.0},
+                            {-fx, 0.0, (W - cx) + g, 0.0},
+                            {0.0, fy, cy + g, 0.0},
+                            {0.0, -fy, (H - cy) + g, 0.0}};
+    const float* R = cam->R;
+    for (int i = 0; i < 5; ++i) {
+        float w[3];
+        for (int j = 0; j < 3; ++j)
+            w[j] = (float)std::fma((double)R[6 + j], a[i][2],
+                                   std::fma((double)R[3 + j], a[i][1], (double)R[j] * a[i][0]));
+        const double o = std::fma((double)w[2], (double)cam->pos[2],
+                                  std::fma((double)w[1], (double)cam->pos[1], (double)w[0] * (double)cam->pos[0]));
+        out[i][0] = w[0];
+        out[i][1] = w[1];
+        out[i][2] = w[2];
+        out[i][3] = (float)(o + a[i][3]);
+    }
+}
+
 void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
     const uint32_t W = cam->width, H = cam->height;
     FrameParams& p = *v->fp_host;
@@ -891,6 +958,8 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
     p.max_depth = v->h->max_depth;
     p.host_image = host_dev;
     p.test_hooks = v->opts.test_hooks;
+    p.lod_frustum = v->opts.lod_frustum ? 1u : 0u;
+    if (p.lod_frustum) frustum_planes(cam, v->opts.lod_frustum_guard, p.frustum);
 }
 
 // Enqueue the frame (and the image copy to host_rgb, if given) and record the

@@ -58,6 +58,9 @@ struct FrameParams {
     uint32_t max_depth;
     uint32_t test_hooks;  // vgr_view_opts.test_hooks (0 in normal use)
     float* host_image;    // device-accessible pinned host image the blend also writes, or null
+    uint32_t lod_frustum; // frustum-aware expansion on (needs node boxes)
+    // its planes: world normal w (xyz) and offset o (w), inside iff w.x - o >= 0 (read as float4)
+    alignas(16) float frustum[5][4];
 };
 
 // Zeroed at the start of every frame.  Scalars first: the host reads back
@@ -92,6 +95,7 @@ struct SceneDev {
     const float4* covA;        // xx xy xz yy
     const float4* covB;        // yz zz opacity ln(opacity)
     const float* lmax;         // upper bound of the covariance's largest eigenvalue (Gershgorin)
+    const float2* box;         // nested node boxes, 3 per node: (lo, hi) in x, y, z; null if not loaded
     const void* sh;            // FP32 or FP16, sh_stride elements per node
     uint32_t n_nodes;
     uint32_t sh_degree;
@@ -254,6 +258,38 @@ __device__ __forceinline__ bool lod_expand(float4 c, float px, float py, float p
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
     return __fmul_rn(d2, k) < c.w;
 }
+
+// Frustum-aware variant of the granularity test: node n also needs its box
+// to meet each of the five half-spaces {x : w.x - o >= 0} (near plane and the
+// four planes through the camera centre and the guard-widened image edges).
+// The box corner furthest along w is tested, single-rounded FP32 in a fixed
+// order; rounding is monotone, so a box inside another never scores higher
+// and nested boxes keep "child expands => parent expands".
+// (The planes are read from the frame parameters at each test, through L1,
+// rather than held in 20 registers.)
+struct LodFrustum {
+    const float4* planes;
+    const float2* box;
+    __device__ __forceinline__ void load(const FrameParams* fp, const float2* b) {
+        planes = reinterpret_cast<const float4*>(fp->frustum);
+        box = b;
+    }
+    __device__ __forceinline__ bool meets(uint32_t n) const {
+        const float2 bx = box[3 * (size_t)n], by = box[3 * (size_t)n + 1], bz = box[3 * (size_t)n + 2];
+        bool in = true;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float4 w = __ldg(planes + i);
+            const float X = w.x >= 0.f ? bx.y : bx.x;
+            const float Y = w.y >= 0.f ? by.y : by.x;
+            const float Z = w.z >= 0.f ? bz.y : bz.x;
+            const float s = __fsub_rn(__fadd_rn(__fadd_rn(__fmul_rn(w.x, X), __fmul_rn(w.y, Y)), __fmul_rn(w.z, Z)),
+                                      w.w);
+            in = in && s >= 0.f;
+        }
+        return in;
+    }
+};
 
 __device__ __forceinline__ void bitmap_set(uint32_t* bm, uint32_t n) { atomicOr(&bm[n >> 5], 1u << (n & 31u)); }
 

@@ -81,6 +81,8 @@ def _load():
             lib.sg_tree_depth.restype = ctypes.c_uint32
             lib.sg_tree_fill.argtypes = [P, ctypes.c_int] + [P] * 13
             lib.sg_tree_fill.restype = ctypes.c_int
+            lib.sg_tree_boxes.argtypes = [ctypes.c_uint64, P, P, P, P, P]
+            lib.sg_tree_boxes.restype = ctypes.c_int
             lib.sg_tree_free.argtypes = [P]
             lib.sg_tree_free.restype = None
             _lib = lib
@@ -170,7 +172,24 @@ def build_tree(leaves: dict) -> dict:
     finally:
         lib.sg_tree_free(t)
     sc.update(sh_degree=leaves["sh_degree"], n_nodes=N, n_leaves=n, max_depth=depth)
+    sc["bbox"] = tree_boxes(sc)
     return sc
+
+
+def tree_boxes(sc: dict) -> np.ndarray:
+    """Nested axis-aligned node boxes (N, 6: lo xyz, hi xyz), FP32 rounded
+    outward: a node's box holds mu +- 3.34 sqrt(diag Sigma) of its own
+    Gaussian and its children's boxes."""
+    lib = _load()
+    N = int(sc["n_nodes"])
+    box = np.empty((N, 6), np.float32)
+    fc = np.ascontiguousarray(sc["first_child"], np.uint32)
+    nc = np.ascontiguousarray(sc["n_child"], np.uint8)
+    mean = np.ascontiguousarray(sc["mean"], np.float32)
+    cov = np.ascontiguousarray(sc["cov6"], np.float32)
+    if lib.sg_tree_boxes(N, _ptr(fc), _ptr(nc), _ptr(mean), _ptr(cov), _ptr(box)) != 0:
+        raise RuntimeError("sg_tree_boxes failed")
+    return box
 
 
 def single_node_scene(mean, cov6, opacity, sh, sh_degree: int = 0) -> dict:

@@ -32,6 +32,11 @@
  * to FP32.  This nesting keeps "child expands => parent expands" true for a
  * distance/size granularity test whenever tau <= focal length.
  *
+ * Node boxes (for the frustum-aware variant of the granularity test): the
+ * axis-aligned box of a node holds its own Gaussian's extent mu_j +- 3.34
+ * sqrt(Sigma_jj) (FP64 from the stored FP32 values, rounded outward to FP32)
+ * and the boxes of its children, so boxes nest exactly.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (no fast-math, so
  * x86-64 and aarch64 builds give the same numbers up to libm last-ulp).
  */
@@ -87,6 +92,12 @@ typedef struct {
 static float sg_round_up_f32(double x) {
     float f = (float)x;
     if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+static float sg_round_down_f32(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
     return f;
 }
 
@@ -406,6 +417,34 @@ int sg_tree_fill(const sg_tree* t, int sh_dim, const float* lmean, const float* 
             }
             R *= 1.0 + 0x1p-12;
             radius2[q] = sg_round_up_f32(R * R);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Nested axis-aligned node boxes, box[6 n ..] = lo x, y, z, hi x, y, z.
+ * Children have larger ids than their parent, so one pass over descending
+ * ids sees every child box before its parent's.
+ */
+int sg_tree_boxes(uint64_t n_nodes, const uint32_t* first_child, const uint8_t* n_child, const float* mean,
+                  const float* cov6, float* box) {
+    static const int diag[3] = {0, 3, 5};
+    for (int64_t q = (int64_t)n_nodes - 1; q >= 0; --q) {
+        float* b = box + 6 * (size_t)q;
+        for (int a = 0; a < 3; ++a) {
+            double v = (double)cov6[6 * (size_t)q + diag[a]];
+            double h = 3.34 * sqrt(v > 0.0 ? v : 0.0);
+            double m = (double)mean[3 * (size_t)q + a];
+            b[a] = sg_round_down_f32(m - h);
+            b[3 + a] = sg_round_up_f32(m + h);
+        }
+        for (uint32_t k = 0; k < n_child[q]; ++k) {
+            const float* c = box + 6 * (size_t)(first_child[q] + k);
+            for (int a = 0; a < 3; ++a) {
+                if (c[a] < b[a]) b[a] = c[a];
+                if (c[3 + a] > b[3 + a]) b[3 + a] = c[3 + a];
+            }
         }
     }
     return 0;

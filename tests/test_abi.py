@@ -26,6 +26,7 @@ def test_default_opts(lib):
     o = _abi.ViewOpts()
     lib.vgr_default_view_opts(ctypes.byref(o))
     assert o.filter == _abi.FILTER_PREEMPTIVE and o.temporal == 1 and o.lut_size == 32 and o.lod_budget == 4096
+    assert o.lod_frustum == 0 and o.lod_frustum_guard == 2.0
 
 
 def _desc(sc, **over):
@@ -33,9 +34,10 @@ def _desc(sc, **over):
             ("parent", "first_child", "n_child", "mean", "cov6", "opacity", "sh", "radius2")}
     keep.update(over)
     p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    box = keep.get("bbox")
     d = _abi.SceneDesc(int(sc["n_nodes"]), int(sc["sh_degree"]), p(keep["parent"]), p(keep["first_child"]),
                        p(keep["n_child"]), p(keep["mean"]), p(keep["cov6"]), p(keep["opacity"]), p(keep["sh"]),
-                       p(keep["radius2"]), 0)
+                       p(keep["radius2"]), 0, p(box) if box is not None else None)
     return d, keep
 
 
@@ -67,6 +69,15 @@ def test_rejects_malformed_trees(lib, tiny_scene):
     nch = sc["n_child"].copy()
     nch[0] = 9
     assert _load_status(lib, sc, n_child=nch)[0] == _abi.VGR_E_INVALID
+    box = sc["bbox"].copy()
+    c = int(sc["first_child"][0])
+    box[c, 3] = box[0, 3] + 1.0  # a child's box pokes out of the root's
+    st, msg = _load_status(lib, sc, bbox=box)
+    assert st == _abi.VGR_E_INVALID and "box" in msg and "nesting" in msg
+    box = sc["bbox"].copy()
+    box[c, 0], box[c, 3] = box[c, 3], box[c, 0]  # lo > hi
+    st, msg = _load_status(lib, sc, bbox=box)
+    assert st == _abi.VGR_E_INVALID and "box" in msg
 
 
 def test_null_arguments(lib):
