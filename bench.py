@@ -369,6 +369,36 @@ def run_ours(args) -> dict:
         vft.close()
         vd.close()
 
+    # ---- parent-child weight interpolation of the cut's Gaussians: the same
+    # walk, timed like the headline
+    weight_interp = None
+    if not args.no_interp:
+        vi = vgr.View(h, stream=stream.cuda_stream, use_graph=not args.no_graph, lod_interp=True)
+        msi, _, sti, _ = timed(vi)
+        vi.close()
+        vit = vgr.View(h, stream=stream.cuda_stream, timing=True, lod_interp=True)
+        vd = vgr.View(h, stream=stream.cuda_stream)
+        for i in range(args.warmup):
+            vit.render(cams[i], tau)
+        st_ms, n_st = np.zeros(2), min(args.steps, 50)
+        for i in range(args.warmup, args.warmup + n_st):
+            r_i = vit.render(cams[i], tau)
+            st_ms += np.array([r_i.stats["stage_ms"][k] for k in ("preprocess", "color")])
+        st_ms /= n_st
+        i1 = args.warmup + n_st - 1
+        vd.render(cams[i1 - 1], tau)
+        r_d = vd.render(cams[i1], tau)
+        img_i, img_d = r_i.image().double(), r_d.image().double()
+        mse = float(((img_i - img_d) ** 2).mean())
+        weight_interp = dict(value=round(frames / (msi / 1e3), 2), unit="frames/s",
+                             ms_per_step=round(msi / args.steps, 4),
+                             front=round(float(np.mean([x["front_count"] for x in sti])), 1),
+                             visible=round(float(np.mean([x["visible_count"] for x in sti])), 1),
+                             stage_ms=dict(preprocess=round(st_ms[0], 4), color=round(st_ms[1], 4)),
+                             psnr_vs_plain_db=round(10 * math.log10(1.0 / mse), 2) if mse > 0 else None)
+        vit.close()
+        vd.close()
+
     # ---- end to end through the host-buffer entry point
     host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
     hp = host_img.data_ptr()
@@ -439,6 +469,7 @@ def run_ours(args) -> dict:
                lod_reuse=lod_reuse,
                half_store=half_store,
                frustum_lod=frustum_lod,
+               weight_interp=weight_interp,
                setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
     view.close()
     if args.config == "city" and not args.leaves and not args.no_served:
@@ -652,6 +683,7 @@ def main():
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16-store run of the walk")
     ap.add_argument("--no-lod-reuse", action="store_true", help="skip the cut-reuse statistics")
     ap.add_argument("--no-frustum", action="store_true", help="skip the frustum-aware LoD run of the walk")
+    ap.add_argument("--no-interp", action="store_true", help="skip the weight-interpolation run of the walk")
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)

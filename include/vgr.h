@@ -129,6 +129,8 @@ typedef struct {
     uint32_t lod_frustum;    /* 1: frustum-aware granularity test (needs bbox; default 0), see
                                 vgr_render_frame */
     float lod_frustum_guard; /* pixels the frustum test adds beyond each image edge (default 2) */
+    uint32_t lod_interp;     /* 1: parent-child weight interpolation of the cut's Gaussians (default 0),
+                                see vgr_render_frame */
 } vgr_view_opts;
 
 enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1 };
@@ -220,6 +222,15 @@ vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes);
  * corner X furthest along w (hi where w_j >= 0, else lo) and require
  * fl(fl(fl(w0 X0) + fl(w1 X1)) + fl(w2 X2)) - o >= 0 (single-rounded FP32).
  * Nested boxes keep this monotone, so the temporal update stays exact.
+ * With lod_interp set, each cut node n with parent p is rendered as a
+ * Gaussian interpolated towards p's (Sec. 3.1 "Weight Interpolation"; the
+ * paper gives no formula, this is the one used): with t = fl(tau / f) and
+ * a = fl(sqrt(fl(radius2 / d2))) a node's size ratio (single-rounded FP32,
+ * d2 as above), w = clamp(fl(fl(t - a_n) / fl(a_p - a_n)), 0, 1) if a_p > a_n,
+ * else 0 (and 0 at the root); mean_j = fl(mean_n + fl(w fl(mean_p - mean_n)));
+ * covariance, SH coefficients and opacity move by w towards the parent's,
+ * the parent's opacity taken as 1 - (1 - opacity_p)^(1 / n_child[p]) (its
+ * share among the siblings).  The cut itself does not change.
  * Between frames with equal tau and f the cut is updated from the previous
  * one (Sec. 4.1, Algorithm 1); the result equals the top-down cut.
  * Requires 0 <= tau <= f, width, height in [1, 16384], z_near > 0.

@@ -95,7 +95,10 @@ def _load():
             lib.orc_rho_max_rect.argtypes = [P] + [ctypes.c_double] * 6
             lib.orc_rho_max_rect.restype = ctypes.c_double
             lib.orc_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_float,
-                                       P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_float]
+                                       P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_float,
+                                       ctypes.c_int]
+            lib.orc_interp_weight.argtypes = [ctypes.POINTER(_Scene), ctypes.c_uint32, P, ctypes.c_float]
+            lib.orc_interp_weight.restype = ctypes.c_float
             lib.orc_render.restype = ctypes.POINTER(_Frame)
             lib.orc_frame_free.argtypes = [ctypes.POINTER(_Frame)]
             lib.orc_frame_free.restype = None
@@ -201,6 +204,14 @@ def cut(sc: dict, cam_pos, k, bruteforce: bool = False, planes=None) -> np.ndarr
     return out[:n].copy()
 
 
+def interp_weight(sc: dict, node: int, cam_pos, t) -> np.float32:
+    """Parent weight of cut node ``node`` in the interpolated Gaussian
+    (FP32), with t = fl(tau / f)."""
+    ref = _SceneRef(sc)
+    p = np.ascontiguousarray(cam_pos, np.float32)
+    return np.float32(_load().orc_interp_weight(ctypes.byref(ref.s), int(node), _ptr(p), float(np.float32(t))))
+
+
 def sh_basis(degree: int, d) -> np.ndarray:
     """Real orthonormal SH basis values (index l*l + l + m) at unit vector d."""
     d = np.ascontiguousarray(d, np.float64)
@@ -223,7 +234,7 @@ def _arr(ptr, dtype, n):
 
 
 def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-3, t_flag: float = 0.05,
-           exhaustive: bool = False, frustum_guard: float | None = None) -> dict:
+           exhaustive: bool = False, frustum_guard: float | None = None, interp: bool = False) -> dict:
     """Render one frame; returns the cut, per-cut projection, pairs and image.
 
     ``tile_mask`` (bool per tile, row-major) restricts binning and blending
@@ -232,7 +243,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     >= ``t_flag``: there an FP32 renderer may take the other side of the
     alpha >= alpha* test and move the pixel by up to ~alpha* T max(rgb).
     ``frustum_guard`` (pixels; needs ``sc["bbox"]``) selects the
-    frustum-aware cut.
+    frustum-aware cut; ``interp`` renders the cut's Gaussians interpolated
+    with their parents.
     """
     lib = _load()
     ref = _SceneRef(sc)
@@ -244,7 +256,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
         mask = np.ascontiguousarray(np.asarray(tile_mask, bool).reshape(TW * TH).astype(np.uint8))
     fp = lib.orc_render(ctypes.byref(ref.s), ctypes.byref(c), float(np.float32(tau)),
                         _ptr(mask) if mask is not None else None, float(band), float(t_flag),
-                        int(bool(exhaustive)), float(-1.0 if frustum_guard is None else frustum_guard))
+                        int(bool(exhaustive)), float(-1.0 if frustum_guard is None else frustum_guard),
+                        int(bool(interp)))
     if not fp:
         raise MemoryError("oracle render")
     try:

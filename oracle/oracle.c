@@ -30,6 +30,20 @@
  *     FP32, then o = fma(w2, C2, fma(w1, C1, w0 C0)) + o_c rounded to FP32.
  *     The box corner X furthest along w (hi where w_j >= 0, else lo) is
  *     tested: fl(fl(fl(w0 X0) + fl(w1 X1)) + fl(w2 X2)) - o >= 0.
+ *  1c. Weight interpolation (Sec. 3.1 "Weight Interpolation": each cut
+ *     Gaussian is interpolated with its parent; the paper gives no formula,
+ *     this is the reading used).  With t = fl(tau / f) and a node's size
+ *     ratio a = fl(sqrt(fl(radius2 / d2))) (d2 as in step 1, IEEE division
+ *     and square root in FP32), the parent weight of cut node n with parent p
+ *     is w = clamp(fl(fl(t - a_n) / fl(a_p - a_n)), 0, 1) when a_p > a_n and
+ *     0 otherwise (and at the root): 0 where n is about to expand (a_n = t),
+ *     1 where p is about to collapse (a_p = t).  The rendered Gaussian has the
+ *     FP32 mean fl(m_n + fl(w fl(m_p - m_n))) per component (it decides the
+ *     depth key, so both sides round it alike), and in FP64 the covariance
+ *     S_n + w (S_p - S_n), the SH coefficients likewise, and the opacity
+ *     theta_n + w (s_p - theta_n) with s_p = 1 - (1 - theta_p)^(1/k), k the
+ *     number of children of p: the share of the parent's opacity that makes
+ *     k coincident copies as opaque as the parent.
  *  2. Cut = { n : every strict ancestor expands and n does not }, found by a
  *     plain top-down traversal from the root.  A brute-force form (walk the
  *     ancestor chain of every node) is provided as a cross-check.
@@ -107,6 +121,9 @@ float orc_lod_k(float tau, float f) {
     float t = tau / f;
     return t * t;
 }
+
+/* t = fl(tau / f), the size ratio of the granularity threshold */
+static float orc_lod_k_t(float tau, float f) { return tau / f; }
 
 /* 1b: the five planes as (w0, w1, w2, o) in planes[4 i ..] */
 void orc_frustum_planes(const orc_camera* cam, float guard, float planes[20]) {
@@ -266,10 +283,55 @@ typedef struct {
     int32_t ntile;       /* kept tiles */
 } orc_proj;
 
-static void orc_project_one(const orc_scene* s, const orc_camera* cam, uint32_t n, orc_proj* P) {
+/* 1c: a node's size ratio R / d in FP32 */
+static float orc_size_ratio(const orc_scene* s, uint32_t n, const float cam[3]) {
+    float dx = cam[0] - s->mean[3 * (size_t)n + 0];
+    float dy = cam[1] - s->mean[3 * (size_t)n + 1];
+    float dz = cam[2] - s->mean[3 * (size_t)n + 2];
+    float d2 = (dx * dx + dy * dy) + dz * dz;
+    float q = s->radius2[n] / d2;
+    return sqrtf(q);
+}
+
+/* 1c: parent weight of cut node n (0 at the root) */
+float orc_interp_weight(const orc_scene* s, uint32_t n, const float cam[3], float t) {
+    uint32_t p = s->parent[n];
+    if (p == 0xFFFFFFFFu) return 0.0f;
+    float an = orc_size_ratio(s, n, cam), ap = orc_size_ratio(s, p, cam);
+    if (!(ap > an)) return 0.0f;
+    float num = t - an, den = ap - an;
+    float w = num / den;
+    return fminf(1.0f, fmaxf(0.0f, w));
+}
+
+/* interp_t < 0: the node's own Gaussian; else step 1c with t = interp_t */
+static void orc_project_one(const orc_scene* s, const orc_camera* cam, uint32_t n, orc_proj* P, float interp_t) {
     memset(P, 0, sizeof(*P));
     P->rect[0] = 0; P->rect[1] = 0; P->rect[2] = -1; P->rect[3] = -1;
-    const float* mf = &s->mean[3 * (size_t)n];
+    int deg = (int)s->sh_degree;
+    int K = (deg + 1) * (deg + 1);
+    float mf[3];
+    double c6[6], theta_n, shn[48];
+    for (int j = 0; j < 3; ++j) mf[j] = s->mean[3 * (size_t)n + j];
+    for (int j = 0; j < 6; ++j) c6[j] = s->cov6[6 * (size_t)n + j];
+    theta_n = s->opacity[n];
+    for (int j = 0; j < 3 * K; ++j) shn[j] = s->sh[(size_t)n * K * 3 + j];
+    if (interp_t >= 0.0f) {
+        float w = orc_interp_weight(s, n, cam->pos, interp_t);
+        if (w > 0.0f) {
+            uint32_t p = s->parent[n];
+            for (int j = 0; j < 3; ++j) {
+                float dm = s->mean[3 * (size_t)p + j] - mf[j];
+                float wd = w * dm;
+                mf[j] = mf[j] + wd;
+            }
+            double wd = w;
+            for (int j = 0; j < 6; ++j) c6[j] += wd * ((double)s->cov6[6 * (size_t)p + j] - c6[j]);
+            double share = -expm1(log1p(-(double)s->opacity[p]) / (double)s->n_child[p]);
+            theta_n += wd * (share - theta_n);
+            for (int j = 0; j < 3 * K; ++j) shn[j] += wd * ((double)s->sh[(size_t)p * K * 3 + j] - shn[j]);
+        }
+    }
     /* depth key: the renderer's FP32 expression */
     float dxf = mf[0] - cam->pos[0], dyf = mf[1] - cam->pos[1], dzf = mf[2] - cam->pos[2];
     float zk = (cam->R[6] * dxf + cam->R[7] * dyf) + cam->R[8] * dzf;
@@ -287,7 +349,6 @@ static void orc_project_one(const orc_scene* s, const orc_camera* cam, uint32_t 
     P->u = fx * p[0] / z + cam->cx;
     P->v = fy * p[1] / z + cam->cy;
 
-    const float* c6 = &s->cov6[6 * (size_t)n];
     double S[9] = {c6[0], c6[1], c6[2], c6[1], c6[3], c6[4], c6[2], c6[4], c6[5]};
     double RS[9], Sc[9];
     for (int r = 0; r < 3; ++r)
@@ -331,20 +392,17 @@ static void orc_project_one(const orc_scene* s, const orc_camera* cam, uint32_t 
     P->valid = 1;
 
     /* colour */
-    int deg = (int)s->sh_degree;
-    int K = (deg + 1) * (deg + 1);
     double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double dir[3] = {d[0] / nd, d[1] / nd, d[2] / nd};
     double Y[16];
     orc_sh_basis(deg, dir, Y);
-    const float* shn = &s->sh[(size_t)n * K * 3];
     for (int ch = 0; ch < 3; ++ch) {
         double acc = 0.0;
-        for (int k = 0; k < K; ++k) acc += (double)shn[3 * k + ch] * Y[k];
+        for (int k = 0; k < K; ++k) acc += shn[3 * k + ch] * Y[k];
         acc += 0.5;
         P->rgb[ch] = acc > 0.0 ? acc : 0.0;
     }
-    P->theta = s->opacity[n];
+    P->theta = theta_n;
     P->thr = log(ORC_ALPHA_MIN) - log(P->theta > 0.0 ? P->theta : 1e-300);
 }
 
@@ -486,10 +544,11 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
  * Render one frame.  tile_mask (optional, n_tiles bytes) restricts binning
  * and blending to the flagged tiles.  band and t_flag parameterise the
  * ambiguity flag (see orc_blend_pixel).  exhaustive != 0 selects mode 7.
- * frustum_guard >= 0 (with s->bbox) selects the frustum-aware cut (1b).
+ * frustum_guard >= 0 (with s->bbox) selects the frustum-aware cut (1b);
+ * interp != 0 renders the cut's Gaussians interpolated with their parents (1c).
  */
 orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, const uint8_t* tile_mask,
-                      double band, double t_flag, int exhaustive, float frustum_guard) {
+                      double band, double t_flag, int exhaustive, float frustum_guard, int interp) {
     orc_frame* F = (orc_frame*)calloc(1, sizeof(orc_frame));
     if (!F) return NULL;
     float f = cam->fx > cam->fy ? cam->fx : cam->fy;
@@ -507,7 +566,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
     int64_t i;
 #pragma omp parallel for schedule(dynamic, 256)
     for (i = 0; i < nc; ++i) {
-        orc_project_one(s, cam, F->cut[i], &F->proj[i]);
+        orc_project_one(s, cam, F->cut[i], &F->proj[i], interp ? orc_lod_k_t(tau, f) : -1.0f);
         orc_candidates(cam, &F->proj[i]);
     }
     const int W = (int)cam->width, H = (int)cam->height;

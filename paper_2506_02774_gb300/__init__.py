@@ -153,7 +153,7 @@ class View:
                  lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
                  cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, grid_wide: int = 0,
                  grid_scan: int = 0, test_hooks: int = 0, lod_frustum: bool = False,
-                 lod_frustum_guard: float = 2.0, stream=None):
+                 lod_frustum_guard: float = 2.0, lod_interp: bool = False, stream=None):
         lib = _abi.load()
         o = _abi.ViewOpts()
         lib.vgr_default_view_opts(ctypes.byref(o))
@@ -165,6 +165,7 @@ class View:
         o.grid_wide, o.grid_scan = int(grid_wide), int(grid_scan)
         o.test_hooks = int(test_hooks)
         o.lod_frustum, o.lod_frustum_guard = int(lod_frustum), float(lod_frustum_guard)
+        o.lod_interp = int(lod_interp)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(stream))
         v = ctypes.c_void_p()

@@ -33,7 +33,8 @@ class ViewOpts(ctypes.Structure):
     _fields_ = [("stream", c_vp), ("filter", c_u32), ("exp_mode", c_u32), ("lut_size", c_u32),
                 ("temporal", c_u32), ("timing", c_u32), ("use_graph", c_u32), ("cut_capacity", c_u64),
                 ("pair_capacity", c_u64), ("lod_budget", c_u32), ("grid_wide", c_u32), ("grid_scan", c_u32),
-                ("test_hooks", c_u32), ("lod_frustum", c_u32), ("lod_frustum_guard", c_f32)]
+                ("test_hooks", c_u32), ("lod_frustum", c_u32), ("lod_frustum_guard", c_f32),
+                ("lod_interp", c_u32)]
 
 
 class FrameStats(ctypes.Structure):

@@ -64,12 +64,14 @@ struct CutOut {
     float R0, R1, R2, R3, R4, R5, R6, R7, R8, Cx, Cy, Cz, z_near;
     float fx, fy, cx, cy, kx, ky, umax, vmax;
     bool canonical;
+    bool all_front;  // weight interpolation: the rendered Gaussian is not the node's own, list every cut node
     __device__ __forceinline__ void add(uint32_t n, float4 c) const {
         bitmap_set(cut_bm, n);
         if (in_front(c, lmax[n])) bitmap_set(front_bm, n);
     }
     // may node (centre c, lm = lmax[n]) reach the image in front of the near plane?
     __device__ __forceinline__ bool in_front(float4 c, float lm) const {
+        if (all_front) return true;
         const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
         const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
         if (!(z > z_near)) return false;
@@ -108,6 +110,7 @@ __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const Scen
     o.umax = (float)(TILE * fp->tiles_x) - 0.5f;
     o.vmax = (float)(TILE * fp->tiles_y) - 0.5f;
     o.canonical = fp->filter == VGR_FILTER_CANONICAL;
+    o.all_front = fp->lod_interp != 0;
     return o;
 }
 

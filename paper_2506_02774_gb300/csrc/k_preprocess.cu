@@ -120,7 +120,7 @@ struct Store<VGR_STORE_HALF> {
     }
 };
 
-template <int STORE>
+template <int STORE, bool INTERP>
 __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
                                                             const uint32_t* __restrict__ n_front_p, uint32_t cap,
                                                             const FrameParams* __restrict__ fp, VisBuffers vis,
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
     const float limx = fp->limx, limy = fp->limy, Wf = fp->width_f, Hf = fp->height_f;
     const int TW = (int)fp->tiles_x, TH = (int)fp->tiles_y;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
+    const float lod_t = fp->lod_t;
     uint32_t n_visible = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     // uniform trip count per warp so the visible count can use a ballot
@@ -148,12 +149,36 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
         bool v = i < n_front;
         uint32_t node = node_next, zbits = 0xFFFFFFFFu;
         node_next = i + stride < n_front ? front[i + stride] : 0u;
-        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f;
+        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f, lw = 0.f;
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
-            const float4 m = sc.cr[node];
+            float4 m = sc.cr[node];
             float S[6], lnth = 0.f;
             Store<STORE>::cov(sc, node, S, theta, lnth);  // in flight together with the centre
+            if constexpr (INTERP) {
+                // the rendered Gaussian moves towards the parent's by the weight w:
+                // mean (single-rounded), covariance and opacity; the parent's
+                // opacity is shared among its k children, 1 - (1 - theta_p)^(1/k),
+                // so that k coincident copies have the parent's peak opacity
+                const uint32_t p = sc.parent[node];
+                if (p != NONE) {
+                    const float4 mp = sc.cr[p];
+                    lw = lod_interp_weight(lod_size_ratio(m, Cx, Cy, Cz), lod_size_ratio(mp, Cx, Cy, Cz), lod_t);
+                    if (lw > 0.f) {
+                        float Sp[6], thp, lnp;
+                        Store<STORE>::cov(sc, p, Sp, thp, lnp);
+                        const float kp = (float)(sc.child[p] >> CHILD_SHIFT);
+                        m.x = lod_lerp_rn(m.x, mp.x, lw);
+                        m.y = lod_lerp_rn(m.y, mp.y, lw);
+                        m.z = lod_lerp_rn(m.z, mp.z, lw);
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) S[j] = fmaf(lw, Sp[j] - S[j], S[j]);
+                        const float share = -expm1f(log1pf(-thp) / kp);
+                        theta = fmaf(lw, share - theta, theta);
+                        lnth = logf(theta);
+                    }
+                }
+            }
             const float dx = __fsub_rn(m.x, Cx), dy = __fsub_rn(m.y, Cy), dz = __fsub_rn(m.z, Cz);
             const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
             v = z > z_near;  // always true for the in-front list; kept as the definition
@@ -232,6 +257,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
             vis.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
             vis.recA[i] = make_float4(u, vv, -0.5f * ca, -cb);
             vis.recB[i] = make_float4(-0.5f * cc, thr, theta, half_h);
+            if (INTERP) vis.lw[i] = lw;
         }
     }
     if (lane_id() == 0 && n_visible) atomicAdd(&ctr->n_vis, n_visible);
@@ -245,9 +271,10 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
 // Colour of the visible Gaussians (dense, no barriers), in visible order,
 // i.e. ascending node id, so consecutive threads read neighbouring SH rows:
 // rgb = sum_lm c_lm Y_lm(d) + 0.5, clamped at 0, d = (mu - C)/|mu - C|.
-template <int DEG, int STORE>
+template <int DEG, int STORE, bool INTERP>
 __global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __restrict__ vis_node,
-                                               const uint32_t* __restrict__ vis_ntile, uint32_t cap,
+                                               const uint32_t* __restrict__ vis_ntile,
+                                               const float* __restrict__ vis_lw, uint32_t cap,
                                                const FrameParams* __restrict__ fp, const Counters* __restrict__ ctr,
                                                float4* __restrict__ rgb_out) {
     pdl_wait();
@@ -265,7 +292,21 @@ __global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __re
         if (nt == 0u) continue;  // culled
         float shc[((3 * K + 7) / 8) * 8];
         Store<STORE>::template sh<K>(sc, node, shc);
-        const float4 m = sc.cr[node];
+        float4 m = sc.cr[node];
+        if constexpr (INTERP) {  // coefficients and mean towards the parent's (weight from preprocess)
+            const float lw = vis_lw[r];
+            if (lw > 0.f) {
+                const uint32_t p = sc.parent[node];
+                float shp[((3 * K + 7) / 8) * 8];
+                Store<STORE>::template sh<K>(sc, p, shp);
+                const float4 mp = sc.cr[p];
+#pragma unroll
+                for (int j = 0; j < 3 * K; ++j) shc[j] = fmaf(lw, shp[j] - shc[j], shc[j]);
+                m.x = lod_lerp_rn(m.x, mp.x, lw);
+                m.y = lod_lerp_rn(m.y, mp.y, lw);
+                m.z = lod_lerp_rn(m.z, mp.z, lw);
+            }
+        }
         const float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
         float Y[K];
         const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
@@ -299,20 +340,32 @@ void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
 }
 
 void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
-                       const FrameParams* fp, VisBuffers vis, Counters* ctr, int grid, cudaStream_t s) {
-    if (sc.storage == VGR_STORE_HALF)
-        launch_k(k_preprocess<VGR_STORE_HALF>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
-    else
-        launch_k(k_preprocess<VGR_STORE_FP32>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
+                       const FrameParams* fp, VisBuffers vis, Counters* ctr, bool interp, int grid, cudaStream_t s) {
+    const bool half = sc.storage == VGR_STORE_HALF;
+    if (interp) {
+        if (half) launch_k(k_preprocess<VGR_STORE_HALF, true>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
+        else launch_k(k_preprocess<VGR_STORE_FP32, true>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
+    } else {
+        if (half) launch_k(k_preprocess<VGR_STORE_HALF, false>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
+        else launch_k(k_preprocess<VGR_STORE_FP32, false>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
+    }
 }
 
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, uint32_t cap,
-                  const FrameParams* fp, const Counters* ctr, float4* rgb, int grid, cudaStream_t s) {
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, const float* vis_lw,
+                  uint32_t cap, const FrameParams* fp, const Counters* ctr, float4* rgb, bool interp, int grid,
+                  cudaStream_t s) {
     const bool half = sc.storage == VGR_STORE_HALF;
-#define VGR_COLOR_CASE(D)                                                                                   \
-    case D:                                                                                                 \
-        if (half) launch_k(k_color<D, VGR_STORE_HALF>, grid, 256, s, sc, vis_node, vis_ntile, cap, fp, ctr, rgb); \
-        else launch_k(k_color<D, VGR_STORE_FP32>, grid, 256, s, sc, vis_node, vis_ntile, cap, fp, ctr, rgb);      \
+#define VGR_COLOR_LAUNCH(D, ST, IN) \
+    launch_k(k_color<D, ST, IN>, grid, 256, s, sc, vis_node, vis_ntile, vis_lw, cap, fp, ctr, rgb)
+#define VGR_COLOR_CASE(D)                                            \
+    case D:                                                          \
+        if (interp) {                                                \
+            if (half) VGR_COLOR_LAUNCH(D, VGR_STORE_HALF, true);     \
+            else VGR_COLOR_LAUNCH(D, VGR_STORE_FP32, true);          \
+        } else {                                                     \
+            if (half) VGR_COLOR_LAUNCH(D, VGR_STORE_HALF, false);    \
+            else VGR_COLOR_LAUNCH(D, VGR_STORE_FP32, false);         \
+        }                                                            \
         break;
     switch (sc.sh_degree) {
         VGR_COLOR_CASE(0)
@@ -322,6 +375,7 @@ void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* 
         default: break;
     }
 #undef VGR_COLOR_CASE
+#undef VGR_COLOR_LAUNCH
 }
 
 uint32_t preprocess_tile() { return PRE_THREADS; }

@@ -107,7 +107,7 @@ struct vgr_hierarchy {
 // A submitted frame, kept until vgr_finish_frame.
 struct PendingFrame {
     vgr_camera cam{};
-    float tau = 0.f, f = 0.f, k = 0.f;
+    float tau = 0.f, f = 0.f, t = 0.f, k = 0.f;
     bool scratch = false;
     int tile_passes = 1;
     uint32_t kernels = 0;
@@ -195,6 +195,7 @@ void vgr_default_view_opts(vgr_view_opts* o) {
     o->lod_budget = 4096;
     o->lod_frustum = 0;
     o->lod_frustum_guard = 2.0f;
+    o->lod_interp = 0;
 }
 
 // ------------------------------------------------------------- hierarchy
@@ -332,7 +333,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
         for (uint32_t i = 0; i < cnt; ++i) {
             const uint32_t n = b + i;
             const float* m = d->mean + 3 * (size_t)n;
-            f4[i] = make_float4(m[0], m[1], m[2], d->n_child[n] ? d->radius2[n] : 0.f);
+            f4[i] = make_float4(m[0], m[1], m[2], d->n_child[n] ? d->radius2[n] : -d->radius2[n]);
         }
         ce = cudaMemcpy(h->cr + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
         uint32_t* u = (uint32_t*)pin;
@@ -484,7 +485,7 @@ void drop_graphs(vgr_view* v) {
 void free_vis(vgr_view* v) {
     drop_graphs(v);
     dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
-    dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb);
+    dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb); dfree(v->vis.lw);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
     v->vis_bytes = 0;
 }
@@ -496,7 +497,7 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
     if ((s = dalloc(&v->vis.node, cap, &b)) || (s = dalloc(&v->vis.depth, cap, &b)) ||
         (s = dalloc(&v->vis.ntile, cap, &b)) || (s = dalloc(&v->vis.rect, cap, &b)) ||
         (s = dalloc(&v->vis.recA, cap, &b)) || (s = dalloc(&v->vis.recB, cap, &b)) ||
-        (s = dalloc(&v->vis.rgb, cap, &b)) ||
+        (s = dalloc(&v->vis.rgb, cap, &b)) || (s = dalloc(&v->vis.lw, cap, &b)) ||
         (s = dalloc(&v->sortK[0], cap, &b)) ||
         (s = dalloc(&v->sortK[1], cap, &b)) || (s = dalloc(&v->sortV[0], cap, &b)) ||
         (s = dalloc(&v->sortV[1], cap, &b))) {
@@ -734,7 +735,7 @@ vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* 
     const uint64_t cap_pairs = o.pair_capacity ? o.pair_capacity : 2 * cap_vis;
     const uint64_t TW = cut_compact_tile_words();
     const uint64_t n_words = ((N + 31) / 32 + TW - 1) / TW * TW;
-    const uint64_t per_vis = 3 * sizeof(uint32_t) + sizeof(uint2) + 3 * sizeof(float4) /* visible SoA */ +
+    const uint64_t per_vis = 3 * sizeof(uint32_t) + sizeof(uint2) + 3 * sizeof(float4) + sizeof(float) /* visible SoA */ +
                              4 * sizeof(uint32_t) /* depth-sort ping-pong */ + 3 * sizeof(float4) /* rank records */;
     const uint64_t RT = radix_tile();
     const uint64_t status_words = 2 * (cut_compact_tiles((uint32_t)n_words) + 1) + ceil_div(cap_vis, emit_tile()) + 1 +
@@ -802,7 +803,8 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
                        &v->vstate->n_cut[cur], v->status + v->st_compact, v->status + v->st_front, v->ctr, v->fp_dev,
                        v->grid_scan, s);
     mark(VGR_STAGE_PREPROCESS);
-    launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, v->grid_wide, s);
+    launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, fh.lod_interp != 0,
+                      v->grid_wide, s);
     mark(VGR_STAGE_DEPTH_SORT);
     // every potentially visible entry is sorted; culled ones carry the key
     // 0xFFFFFFFF and land last (the digit histograms come from preprocess)
@@ -815,7 +817,8 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
     mark(VGR_STAGE_COLOR);
-    launch_color(sc, v->vis.node, v->vis.ntile, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, v->grid_wide, s);
+    launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, fh.lod_interp != 0,
+                 v->grid_wide, s);
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
@@ -937,7 +940,7 @@ void frustum_planes(const vgr_camera* cam, float guard, float out[5][4]) {
     }
 }
 
-void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
+void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* host_dev) {
     const uint32_t W = cam->width, H = cam->height;
     FrameParams& p = *v->fp_host;
     memcpy(p.R, cam->R, sizeof(p.R));
@@ -959,6 +962,8 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float k, float* host_dev) {
     p.host_image = host_dev;
     p.test_hooks = v->opts.test_hooks;
     p.lod_frustum = v->opts.lod_frustum ? 1u : 0u;
+    p.lod_interp = v->opts.lod_interp ? 1u : 0u;
+    p.lod_t = t;
     if (p.lod_frustum) frustum_planes(cam, v->opts.lod_frustum_guard, p.frustum);
 }
 
@@ -985,10 +990,11 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
     volatile float t = tau / f;
     volatile float k = t * t;
     q.f = f;
+    q.t = t;
     q.k = k;
     q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
     q.host_dev = mapped_host(v, host_rgb);
-    fill_params(v, cam, q.k, q.host_dev);
+    fill_params(v, cam, q.t, q.k, q.host_dev);
     return VGR_OK;
 }
 
@@ -1141,7 +1147,7 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         if (!again) break;
         if (attempt >= 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt + 1);
         ++replays;
-        fill_params(v, &q.cam, q.k, q.host_dev);
+        fill_params(v, &q.cam, q.t, q.k, q.host_dev);
         if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
         if (q.host && !q.host_dev)
             VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,

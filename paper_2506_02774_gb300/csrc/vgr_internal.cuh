@@ -59,6 +59,8 @@ struct FrameParams {
     uint32_t test_hooks;  // vgr_view_opts.test_hooks (0 in normal use)
     float* host_image;    // device-accessible pinned host image the blend also writes, or null
     uint32_t lod_frustum; // frustum-aware expansion on (needs node boxes)
+    uint32_t lod_interp;  // parent-child weight interpolation on
+    float lod_t;          // fl(tau / f), the size ratio the interpolation weight is measured against
     // its planes: world normal w (xyz) and offset o (w), inside iff w.x - o >= 0 (read as float4)
     alignas(16) float frustum[5][4];
 };
@@ -89,7 +91,7 @@ struct ViewState {
 
 // Device view of the hierarchy.
 struct SceneDev {
-    const float4* cr;          // mean xyz, w = radius2 (internal) or 0 (leaf)
+    const float4* cr;          // mean xyz, w = radius2 (internal) or -radius2 (leaf: never expands)
     const uint32_t* parent;
     const uint32_t* child;     // first_child | n_child << 28
     const float4* covA;        // xx xy xz yy
@@ -252,7 +254,7 @@ __device__ __forceinline__ float depth_key(float4 m, float R6, float R7, float R
 }
 
 // The granularity test, single-rounded FP32 (no contraction): expand iff
-// fl(((dx dx + dy dy) + dz dz) k) < radius2; cr.w is 0 for leaves.
+// fl(((dx dx + dy dy) + dz dz) k) < radius2; cr.w is -radius2 <= 0 for leaves.
 __device__ __forceinline__ bool lod_expand(float4 c, float px, float py, float pz, float k) {
     float dx = __fsub_rn(px, c.x), dy = __fsub_rn(py, c.y), dz = __fsub_rn(pz, c.z);
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -290,6 +292,28 @@ struct LodFrustum {
         return in;
     }
 };
+
+// Weight of the parent in the interpolated Gaussian of cut node n (Sec. 3.1
+// 'Weight Interpolation'): with a = sqrt(R^2 / d^2) the size ratio R / d of a
+// node (its projected size over f) and t = tau / f,
+//   w = clamp((t - a_n) / (a_p - a_n), 0, 1)  when a_p > a_n, else 0,
+// single-rounded FP32 (IEEE division and square root), d^2 as in the
+// granularity test.  w runs from 0 where n is about to expand (a_n = t) to 1
+// where its parent is about to collapse (a_p = t).
+__device__ __forceinline__ float lod_size_ratio(float4 c, float px, float py, float pz) {
+    const float dx = __fsub_rn(px, c.x), dy = __fsub_rn(py, c.y), dz = __fsub_rn(pz, c.z);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return __fsqrt_rn(__fdiv_rn(fabsf(c.w), d2));
+}
+__device__ __forceinline__ float lod_interp_weight(float an, float ap, float t) {
+    if (!(ap > an)) return 0.f;
+    const float w = __fdiv_rn(__fsub_rn(t, an), __fsub_rn(ap, an));
+    return fminf(1.f, fmaxf(0.f, w));
+}
+// The interpolated mean, single-rounded per component: mn + w (mp - mn).
+__device__ __forceinline__ float lod_lerp_rn(float a, float b, float w) {
+    return __fadd_rn(a, __fmul_rn(w, __fsub_rn(b, a)));
+}
 
 __device__ __forceinline__ void bitmap_set(uint32_t* bm, uint32_t n) { atomicOr(&bm[n >> 5], 1u << (n & 31u)); }
 

@@ -63,12 +63,14 @@ struct VisBuffers {
     float4* recA;   // u v A B   (rho = A dx^2 + B dx dy + C dy^2)
     float4* recB;   // C thr theta half-height of the footprint box
     float4* rgb;    // r g b 0
+    float* lw;      // parent weight of the interpolated Gaussian (weight interpolation only)
 };
 void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
-                       const FrameParams* fp, VisBuffers vis, Counters* ctr, int grid, cudaStream_t s);
+                       const FrameParams* fp, VisBuffers vis, Counters* ctr, bool interp, int grid, cudaStream_t s);
 uint32_t preprocess_tile();
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, uint32_t cap,
-                  const FrameParams* fp, const Counters* ctr, float4* rgb, int grid, cudaStream_t s);
+void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, const float* vis_lw,
+                  uint32_t cap, const FrameParams* fp, const Counters* ctr, float4* rgb, bool interp, int grid,
+                  cudaStream_t s);
 void prepare_scene(float4* covB, uint32_t n, cudaStream_t s);
 void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s);
 
