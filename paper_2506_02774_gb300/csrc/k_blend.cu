@@ -27,6 +27,8 @@
 //   alpha = min(0.99, theta e^rho)         (Eq. 3)
 //   T'    = T (1 - alpha); stop when T' < 1e-4 (this Gaussian excluded)
 //   C    += alpha T rgb; T = T'
+// (the exact mode takes the same test and alpha in base 2 with ln theta
+// folded into the exponent, see blend_prepare).
 // CTAs take tiles heaviest first (k_tile_order).  Modes: canonical (every
 // record at every pixel of the tile, alpha first, then the alpha* test; for
 // the filtered-vs-unfiltered comparison; its row masks are all ones) and the
@@ -47,18 +49,42 @@ struct BlendPixel {
     uint32_t evals = 0, contribs = 0;
 };
 
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LOG2_ALPHA_MIN = -7.9943534368588578f;  // log2(1/255)
+
 // A staged record, rewritten for the warp's two pixel rows (dy0, dy1 the
 // offsets of the mean from their centres):
 //   X = (u, A, thr, theta),  R = (B dy0, C dy0^2, B dy1, C dy1^2)
 // so that at a pixel of row r, dx = u - x:  rho = (A dx + B dy_r) dx + C dy_r^2,
-// one subtraction and two FMAs (A = -a/2, B = -b, C = -c/2).
+// one subtraction and two FMAs (A = -a/2, B = -b, C = -c/2).  The exact mode
+// works in base 2 with the opacity folded in: A, B, C scaled by log2 e and
+// log2 theta added to the constant term, so that
+//   rho' = (A' dx + B' dy_r) dx + (C' dy_r^2 + log2 theta) = log2(theta e^rho),
+// Eq. 4 becomes rho' >= log2 alpha* (one constant) and Eq. 3 alpha =
+// min(0.99, 2^rho'): X = (u, A', -, -).
+template <int MODE>
 __device__ __forceinline__ void blend_prepare(float4& a, float4& b, float row0) {
     const float dy0 = a.y - row0, dy1 = a.y - (row0 + 1.0f);
-    const float Bc = a.w, Cc = b.x;
-    const float4 X = make_float4(a.x, a.z, b.y, b.z);
-    const float4 R = make_float4(Bc * dy0, (Cc * dy0) * dy0, Bc * dy1, (Cc * dy1) * dy1);
-    a = X;
-    b = R;
+    if (MODE == 0) {
+        const float Bc = a.w * LOG2E, Cc = b.x * LOG2E;
+        const float l2th = (LN_ALPHA_MIN - b.y) * LOG2E;  // b.y = ln alpha* - ln theta
+        const float4 X = make_float4(a.x, a.z * LOG2E, 0.f, 0.f);
+        const float4 R = make_float4(Bc * dy0, fmaf(Cc * dy0, dy0, l2th), Bc * dy1, fmaf(Cc * dy1, dy1, l2th));
+        a = X;
+        b = R;
+    } else {
+        const float Bc = a.w, Cc = b.x;
+        const float4 X = make_float4(a.x, a.z, b.y, b.z);
+        const float4 R = make_float4(Bc * dy0, (Cc * dy0) * dy0, Bc * dy1, (Cc * dy1) * dy1);
+        a = X;
+        b = R;
+    }
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // One record at one pixel; returns false once the pixel has stopped.
@@ -66,17 +92,17 @@ template <int MODE>
 __device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& X, const float4* __restrict__ sC, uint32_t k,
                                            float rho, const float* s_lut, uint32_t m, float lut_scale) {
     float alpha;
-    if (MODE == 1) {  // canonical: Eq. 3, then the alpha* test
+    if (MODE == 0) {  // base 2, opacity folded in (see blend_prepare)
+        if (rho < LOG2_ALPHA_MIN) return true;
+        alpha = fminf(ALPHA_MAX, ex2_approx(rho));
+    } else if (MODE == 1) {  // canonical: Eq. 3, then the alpha* test
         alpha = fminf(ALPHA_MAX, X.w * __expf(rho));
         if (alpha < ALPHA_MIN) return true;
     } else {
         if (rho < X.z) return true;  // Eq. 4 before Eq. 3
-        if (MODE == 0) {
-            alpha = fminf(ALPHA_MAX, X.w * __expf(rho));
-        } else {  // Eq. 5: nearest of m intervals over [-5.55, 0]
-            const uint32_t idx = min(m, (uint32_t)__float2int_rn(rho * lut_scale));
-            alpha = fminf(ALPHA_MAX, X.w * s_lut[idx]);
-        }
+        // Eq. 5: nearest of m intervals over [-5.55, 0]
+        const uint32_t idx = min(m, (uint32_t)__float2int_rn(rho * lut_scale));
+        alpha = fminf(ALPHA_MAX, X.w * s_lut[idx]);
     }
     const float Tn = p.T * (1.f - alpha);
     if (Tn < T_MIN) { p.done = true; return false; }
@@ -88,6 +114,16 @@ __device__ __forceinline__ bool blend_step(BlendPixel& p, const float4& X, const
     p.T = Tn;
     ++p.contribs;
     return true;
+}
+
+// The staged X of slot i: only (u, A') in the exact mode.
+template <int MODE>
+__device__ __forceinline__ float4 load_x(const float4* wA, uint32_t i) {
+    if (MODE == 0) {
+        const float2 x = reinterpret_cast<const float2*>(wA)[2 * i];
+        return make_float4(x.x, x.y, 0.f, 0.f);
+    }
+    return wA[i];
 }
 
 __device__ __forceinline__ float blend_rho(const BlendPixel& p, const float4& X, const float2& R) {
@@ -167,21 +203,21 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
         float4* wB = sbuf[buf][1][warp];
         const float4* wC = sbuf[buf][2][warp];
         const uint32_t nh = __popc(hits_cur);
-        if (lane < nh) blend_prepare(wA[lane], wB[lane], rlo);  // each lane its own slot
+        if (lane < nh) blend_prepare<MODE>(wA[lane], wB[lane], rlo);  // each lane its own slot
         __syncwarp();
         if (!p.done) {
             // rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31): each reads its half of R
             const float2* wR = reinterpret_cast<const float2*>(wB) + (lane >> 4);
             uint32_t i = 0, ev = nh;
             for (; i + 2 <= nh; i += 2) {
-                const float4 X0 = wA[i], X1 = wA[i + 1];
+                const float4 X0 = load_x<MODE>(wA, i), X1 = load_x<MODE>(wA, i + 1);
                 const float2 R0 = wR[2 * i], R1 = wR[2 * i + 2];
                 const float r0 = blend_rho(p, X0, R0), r1 = blend_rho(p, X1, R1);
                 if (!blend_step<MODE>(p, X0, wC, i, r0, s_lut, m, lut_scale)) { ev = i + 1; break; }
                 if (!blend_step<MODE>(p, X1, wC, i + 1, r1, s_lut, m, lut_scale)) { ev = i + 2; break; }
             }
             if (!p.done && i < nh) {
-                const float4 X0 = wA[i];
+                const float4 X0 = load_x<MODE>(wA, i);
                 if (!blend_step<MODE>(p, X0, wC, i, blend_rho(p, X0, wR[2 * i]), s_lut, m, lut_scale)) ev = i + 1;
             }
             p.evals += ev;
