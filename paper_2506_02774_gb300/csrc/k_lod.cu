@@ -57,21 +57,73 @@ __device__ __forceinline__ void warp_bitmap_set(uint32_t* bm, uint32_t n, bool p
     if (pred && (lane == 0u || wprev != w)) atomicOr(&bm[w], bits);
 }
 
+// With weight interpolation the rendered Gaussian of a cut node n is not n's
+// own: its mean lies on the segment from n's centre to its parent's and its
+// covariance is a convex combination of theirs, so its largest eigenvalue is
+// at most max(L_n, L_p).  When both centres are beyond the near plane the
+// whole segment is, its projection is the segment between the two projected
+// centres and its depth is at least the smaller of theirs: the union of the
+// two boxes, widened for max(L_n, L_p) at that depth, bounds the footprint.
+// A segment across the near plane is kept; one wholly behind it is dropped.
 struct CutOut {
     uint32_t* cut_bm;
     uint32_t* front_bm;
     const float* lmax;
+    const float4* cr;
+    const uint32_t* parent;
     float R0, R1, R2, R3, R4, R5, R6, R7, R8, Cx, Cy, Cz, z_near;
     float fx, fy, cx, cy, kx, ky, umax, vmax;
     bool canonical;
-    bool all_front;  // weight interpolation: the rendered Gaussian is not the node's own, list every cut node
+    bool interp;  // weight interpolation: bound the interpolated Gaussian, not the node's own
     __device__ __forceinline__ void add(uint32_t n, float4 c) const {
         bitmap_set(cut_bm, n);
-        if (in_front(c, lmax[n])) bitmap_set(front_bm, n);
+        if (visible(n, c, lmax[n])) bitmap_set(front_bm, n);
+    }
+    // may the Gaussian rendered for cut node n (centre c, lm = lmax[n]) reach the image?
+    __device__ __forceinline__ bool visible(uint32_t n, float4 c, float lm) const {
+        if (!interp) return in_front(c, lm);
+        const uint32_t p = parent[n];
+        if (p == NONE) return in_front(c, lm);
+        return in_front_segment(c, lm, cr[p], lmax[p]);
+    }
+    __device__ __forceinline__ float depth(float4 c) const {
+        const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
+        return __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
+    }
+    __device__ __forceinline__ void project(float4 c, float z, float& u, float& v) const {
+        const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
+        const float x = fmaf(R0, dx, fmaf(R1, dy, R2 * dz));
+        const float y = fmaf(R3, dx, fmaf(R4, dy, R5 * dz));
+        const float iz = 1.0f / z;
+        u = fmaf(fx, x * iz, cx);
+        v = fmaf(fy, y * iz, cy);
+    }
+    __device__ __forceinline__ void half_box(float lm, float z, float& bx, float& by) const {
+        const float iz = 1.0f / z;
+        const float t = lm * iz * iz;
+        if (!canonical) {
+            bx = 3.34f * sqrtf(fmaf(t, kx, 0.3f)) + 0.01f;
+            by = 3.34f * sqrtf(fmaf(t, ky, 0.3f)) + 0.01f;
+        } else {
+            bx = by = 3.01f * sqrtf(fmaf(t, kx + ky, 1.0f)) + 1.01f;
+        }
+    }
+    __device__ __forceinline__ bool in_front_segment(float4 cn, float lmn, float4 cp, float lmp) const {
+        const float zn = depth(cn), zp = depth(cp);
+        const float zeps = 1e-2f;  // far above the FP32 error of the interpolated mean's depth
+        if (zn <= z_near - zeps && zp <= z_near - zeps) return false;
+        if (!(zn > z_near + zeps) || !(zp > z_near + zeps)) return true;
+        float un, vn, up, vp, bx, by;
+        project(cn, zn, un, vn);
+        project(cp, zp, up, vp);
+        half_box(fmaxf(lmn, lmp), fminf(zn, zp), bx, by);
+        const float ulo = fminf(un, up), uhi = fmaxf(un, up), vlo = fminf(vn, vp), vhi = fmaxf(vn, vp);
+        const float su = 1e-5f * fmaxf(fabsf(ulo), fabsf(uhi)) + 1e-2f;
+        const float sv = 1e-5f * fmaxf(fabsf(vlo), fabsf(vhi)) + 1e-2f;
+        return !(uhi + bx < 0.5f - su || ulo - bx > umax + su || vhi + by < 0.5f - sv || vlo - by > vmax + sv);
     }
     // may node (centre c, lm = lmax[n]) reach the image in front of the near plane?
     __device__ __forceinline__ bool in_front(float4 c, float lm) const {
-        if (all_front) return true;
         const float dx = __fsub_rn(c.x, Cx), dy = __fsub_rn(c.y, Cy), dz = __fsub_rn(c.z, Cz);
         const float z = __fadd_rn(__fadd_rn(__fmul_rn(R6, dx), __fmul_rn(R7, dy)), __fmul_rn(R8, dz));
         if (!(z > z_near)) return false;
@@ -93,12 +145,15 @@ struct CutOut {
     }
 };
 
+template <bool IP>
 __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const SceneDev& sc, uint32_t* cut_bm,
                                                uint32_t* front_bm) {
     CutOut o;
     o.cut_bm = cut_bm;
     o.front_bm = front_bm;
     o.lmax = sc.lmax;
+    o.cr = sc.cr;
+    o.parent = sc.parent;
     o.R0 = fp->R[0]; o.R1 = fp->R[1]; o.R2 = fp->R[2];
     o.R3 = fp->R[3]; o.R4 = fp->R[4]; o.R5 = fp->R[5];
     o.R6 = fp->R[6]; o.R7 = fp->R[7]; o.R8 = fp->R[8];
@@ -110,13 +165,13 @@ __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const Scen
     o.umax = (float)(TILE * fp->tiles_x) - 0.5f;
     o.vmax = (float)(TILE * fp->tiles_y) - 0.5f;
     o.canonical = fp->filter == VGR_FILTER_CANONICAL;
-    o.all_front = fp->lod_interp != 0;
+    o.interp = IP;  // a compile-time constant: the other form's code is not generated
     return o;
 }
 
 constexpr int LOD_UNROLL = 2;  // previous-cut nodes per thread and round
 
-template <bool FR>
+template <bool FR, bool IP>
 __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__ prev_cut,
                                                     const uint32_t* __restrict__ n_prev_p, uint32_t cap_prev,
                                                     SceneDev sc, const FrameParams* __restrict__ fp,
@@ -126,7 +181,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     const uint32_t n_prev = min(*n_prev_p, cap_prev);
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
     const uint32_t budget = fp->lod_budget, max_depth = fp->max_depth;
-    const CutOut out = make_cut_out(fp, sc, bitmap, front);
+    const CutOut out = make_cut_out<IP>(fp, sc, bitmap, front);
     LodFrustum fr;
     if (FR) fr.load(fp, sc.box);
     // the granularity test, and in the frustum-aware variant the box test
@@ -224,7 +279,12 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
         for (int u = 0; u < LOD_UNROLL; ++u) {
             const bool stay = ok[u] && visit(nn[u], cc[u], pp[u], qq[u]);
             warp_bitmap_set(bitmap, nn[u], stay);
-            warp_bitmap_set(front, nn[u], stay && out.in_front(cc[u], ll[u]));
+            bool vis = false;
+            if (stay) {
+                if (!out.interp || pp[u] == NONE) vis = out.in_front(cc[u], ll[u]);
+                else vis = out.in_front_segment(cc[u], ll[u], qq[u], sc.lmax[pp[u]]);
+            }
+            warp_bitmap_set(front, nn[u], vis);
         }
     }
     // one atomic per warp for the statistics
@@ -237,7 +297,7 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
 }
 
 // One level of the top-down traversal.  Level 0 starts from the root.
-template <bool FR>
+template <bool FR, bool IP>
 __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __restrict__ fin,
                                                    uint32_t* __restrict__ fout, uint32_t cap, SceneDev sc,
                                                    const FrameParams* __restrict__ fp,
@@ -247,7 +307,7 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
     const uint32_t n_in = level == 0 ? 1u : min(ctr->frontier_n[level], cap);
     uint32_t* n_out = &ctr->frontier_n[level + 1];
     const float px = fp->pos[0], py = fp->pos[1], pz = fp->pos[2], k = fp->k;
-    const CutOut out = make_cut_out(fp, sc, bitmap, front);
+    const CutOut out = make_cut_out<IP>(fp, sc, bitmap, front);
     LodFrustum fr;
     if (FR) fr.load(fp, sc.box);
     const uint32_t lane = lane_id();
@@ -269,7 +329,7 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
                 cnt = c >> CHILD_SHIFT;
             } else {
                 is_cut = true;
-                in_front = out.in_front(cn, lm);
+                in_front = out.visible(n, cn, lm);
             }
         }
         // one atomic per bitmap word and warp (a node's siblings are neighbours)
@@ -373,16 +433,32 @@ __global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitm
 // ------------------------------------------------------------ launchers
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
                        const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                       bool frustum, cudaStream_t s) {
-    if (frustum) launch_k(k_lod_update<true>, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
-    else launch_k(k_lod_update<false>, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr);
+                       bool frustum, bool interp, cudaStream_t s) {
+#define VGR_LOD_UPDATE(FR, IP) \
+    launch_k(k_lod_update<FR, IP>, grid, 256, s, prev_cut, n_prev, cap_prev, sc, fp, bitmap, front, ctr)
+    if (frustum) {
+        if (interp) VGR_LOD_UPDATE(true, true);
+        else VGR_LOD_UPDATE(true, false);
+    } else {
+        if (interp) VGR_LOD_UPDATE(false, true);
+        else VGR_LOD_UPDATE(false, false);
+    }
+#undef VGR_LOD_UPDATE
 }
 
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                      bool frustum, cudaStream_t s) {
-    if (frustum) launch_k(k_lod_level<true>, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
-    else launch_k(k_lod_level<false>, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr);
+                      bool frustum, bool interp, cudaStream_t s) {
+#define VGR_LOD_LEVEL(FR, IP) \
+    launch_k(k_lod_level<FR, IP>, grid, 256, s, level, fin, fout, cap, sc, fp, bitmap, front, ctr)
+    if (frustum) {
+        if (interp) VGR_LOD_LEVEL(true, true);
+        else VGR_LOD_LEVEL(true, false);
+    } else {
+        if (interp) VGR_LOD_LEVEL(false, true);
+        else VGR_LOD_LEVEL(false, false);
+    }
+#undef VGR_LOD_LEVEL
 }
 
 void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,

@@ -793,10 +793,11 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     if (scratch) {
         for (uint32_t level = 0; level <= v->h->max_depth; ++level)
             launch_lod_level((int)level, sc, v->frontier[level & 1], v->frontier[(level + 1) & 1], v->h->n_nodes,
-                             v->fp_dev, v->bitmap, v->front_bm, v->ctr, v->grid_wide, fh.lod_frustum != 0, s);
+                             v->fp_dev, v->bitmap, v->front_bm, v->ctr, v->grid_wide, fh.lod_frustum != 0,
+                             fh.lod_interp != 0, s);
     } else {
         launch_lod_update(sc, v->cut[prev], &v->vstate->n_cut[prev], v->cap_cut, v->fp_dev, v->bitmap, v->front_bm,
-                          v->ctr, v->grid_wide, fh.lod_frustum != 0, s);
+                          v->ctr, v->grid_wide, fh.lod_frustum != 0, fh.lod_interp != 0, s);
     }
     mark(VGR_STAGE_COMPACT);
     launch_cut_compact(v->bitmap, v->front_bm, v->n_words, v->cut[cur], v->front_list, v->cap_cut,

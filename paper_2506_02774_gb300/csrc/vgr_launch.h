@@ -43,10 +43,10 @@ struct Counters;
 // k_lod.cu
 void launch_lod_update(const SceneDev& sc, const uint32_t* prev_cut, const uint32_t* n_prev, uint32_t cap_prev,
                        const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                       bool frustum, cudaStream_t s);
+                       bool frustum, bool interp, cudaStream_t s);
 void launch_lod_level(int level, const SceneDev& sc, const uint32_t* fin, uint32_t* fout, uint32_t cap,
                       const FrameParams* fp, uint32_t* bitmap, uint32_t* front, Counters* ctr, int grid,
-                      bool frustum, cudaStream_t s);
+                      bool frustum, bool interp, cudaStream_t s);
 void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uint32_t* cut, uint32_t* front_list,
                         uint32_t cap, uint32_t* n_cut_out, unsigned long long* status,
                         unsigned long long* status_front, Counters* ctr, const FrameParams* fp, int grid,
