@@ -159,3 +159,26 @@ def test_whole_batch_graph_equals_individual(small_sh3_scene, h_small):
             assert res[1].stats["replays"] >= 1  # the small pair buffer grew
     for v in batch + solo:
         v.close()
+
+
+def test_batch_with_variant_views(small_sh3_scene, h_small):
+    """Views with the frustum-aware test, weight interpolation or both, in
+    one captured batch graph: each frame equals the view rendered alone, and
+    the combined variant matches the oracle."""
+    n = len(SIZES)
+    kinds = [dict(lod_frustum=True), dict(lod_interp=True), dict(lod_frustum=True, lod_interp=True), dict()]
+    batch = [vgr.View(h_small, use_graph=True, **kinds[i]) for i in range(n)]
+    solo = [vgr.View(h_small, **kinds[i]) for i in range(n)]
+    walks = [_cams(i, 3, SIZES[i]) for i in range(n)]
+    for k in range(3):
+        cams = [walks[i][k] for i in range(n)]
+        res = vgr.render_batch(batch, cams, [3.0] * n)
+        for i in range(n):
+            r = solo[i].render(cams[i], 3.0)
+            np.testing.assert_array_equal(res[i].cut().cpu().numpy(), r.cut().cpu().numpy())
+            assert np.array_equal(res[i].image().cpu().numpy(), r.image().cpu().numpy())
+        ref = oracle.render(small_sh3_scene, cams[2], 3.0, frustum_guard=2.0, interp=True)
+        np.testing.assert_array_equal(res[2].cut().cpu().numpy().view(np.uint32), ref["cut"])
+        check_image(res[2].image().cpu().numpy(), ref)
+    for v in batch + solo:
+        v.close()
