@@ -40,6 +40,8 @@ namespace vgr {
 
 constexpr int BL_THREADS = TILE * TILE;  // 256, one pixel each
 constexpr int BL_WARPS = BL_THREADS / 32;
+constexpr int BL_SCAN = 128;   // pair values scanned per batch (4 per lane, loaded one batch ahead)
+constexpr int BL_RING = 256;   // queue capacity per warp: < 32 queued + BL_SCAN appended never exceeds it
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 struct BlendPixel {
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     pdl_wait();
     // [buffer][record part A, B, C][warp][slot]
     __shared__ __align__(16) float4 sbuf[2][3][BL_WARPS][32];
+    __shared__ uint32_t s_ring[BL_WARPS][BL_RING];  // per-warp queue of hit pair values
     __shared__ float s_lut[260];
     const uint32_t W = fp->width, H = fp->height, TW = fp->tiles_x;
     float* const host_image = fp->host_image;
@@ -176,33 +179,65 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
     p.fxp = (float)px + 0.5f;
     p.fyp = (float)py + 0.5f;
     p.done = !inside;
-    // stage the records of the pairs in [b, b + 32) that reach this warp's rows
-    auto issue = [&](uint32_t v, int buf) -> uint32_t {
-        const bool hit = (v & wbit) != 0u;  // entries past the range hold 0
-        const uint32_t hits = __ballot_sync(FULL, hit);
-        if (hit) {
-            const uint32_t slot = __popc(hits & lanemask_lt()), gi = v >> 8;
-            cp_async16(&sbuf[buf][0][warp][slot], recA + gi);
-            cp_async16(&sbuf[buf][1][warp][slot], recB + gi);
-            cp_async16(&sbuf[buf][2][warp][slot], rgb + gi);
+    // The warp's pairs (those whose row mask names it, in depth order) pass
+    // through a ring of pair values: the range is scanned BL_SCAN values at a
+    // time (loaded one batch ahead), hits are appended, and records are
+    // staged 32 hits at a time, so staging and the walk run on full chunks
+    // however sparse the warp's hits are among the tile's pairs.
+    uint32_t* ring = s_ring[warp];
+    uint32_t head = 0, tail = 0;
+    uint32_t bp = rg.x;  // first pair value of the pending batch
+    uint32_t pend[BL_SCAN / 32];
+#pragma unroll
+    for (int g = 0; g < BL_SCAN / 32; ++g) {
+        const uint32_t j = bp + 32u * g + lane;
+        pend[g] = j < rg.y ? pair_val[j] : 0u;
+    }
+    auto refill = [&]() {
+        while (tail - head < 32u && bp < rg.y) {
+#pragma unroll
+            for (int g = 0; g < BL_SCAN / 32; ++g) {
+                const uint32_t v = pend[g];
+                const bool hit = (v & wbit) != 0u;  // entries past the range hold 0
+                const uint32_t hits = __ballot_sync(FULL, hit);
+                if (hit) ring[(tail + __popc(hits & lanemask_lt())) & (BL_RING - 1)] = v;
+                tail += __popc(hits);
+            }
+            bp += BL_SCAN;
+#pragma unroll
+            for (int g = 0; g < BL_SCAN / 32; ++g) {
+                const uint32_t j = bp + 32u * g + lane;
+                pend[g] = j < rg.y ? pair_val[j] : 0u;
+            }
+        }
+        __syncwarp();
+    };
+    // stage up to 32 queued hits into buffer buf; returns their number
+    auto issue = [&](int buf) -> uint32_t {
+        const uint32_t nh = min(32u, tail - head);
+        if (lane < nh) {
+            const uint32_t gi = ring[(head + lane) & (BL_RING - 1)] >> 8;
+            cp_async16(&sbuf[buf][0][warp][lane], recA + gi);
+            cp_async16(&sbuf[buf][1][warp][lane], recB + gi);
+            cp_async16(&sbuf[buf][2][warp][lane], rgb + gi);
         }
         cp_async_commit();
-        return hits;
+        head += nh;
+        return nh;
     };
-    uint32_t b = rg.x;
-    uint32_t hits_cur = issue(b + lane < rg.y ? pair_val[b + lane] : 0u, 0);
-    uint32_t v_next = b + 32 + lane < rg.y ? pair_val[b + 32 + lane] : 0u;
+    refill();
+    uint32_t nh_cur = issue(0);
     int buf = 0;
-    for (; b < rg.y; b += 32) {
+    while (nh_cur > 0) {
         if (__all_sync(FULL, p.done)) break;
-        const uint32_t hits_next = issue(v_next, buf ^ 1);  // next 32 pairs in flight during this walk
-        v_next = b + 64 + lane < rg.y ? pair_val[b + 64 + lane] : 0u;
+        refill();
+        const uint32_t nh_next = issue(buf ^ 1);  // the next chunk in flight during this walk
         cp_async_wait<1>();  // this chunk's copies (all but the newest group)
         __syncwarp();
         float4* wA = sbuf[buf][0][warp];
         float4* wB = sbuf[buf][1][warp];
         const float4* wC = sbuf[buf][2][warp];
-        const uint32_t nh = __popc(hits_cur);
+        const uint32_t nh = nh_cur;
         if (lane < nh) blend_prepare<MODE>(wA[lane], wB[lane], rlo);  // each lane its own slot
         __syncwarp();
         if (!p.done) {
@@ -224,7 +259,7 @@ __global__ void __launch_bounds__(BL_THREADS) k_blend(const uint32_t* __restrict
         }
         __syncwarp();  // the walk is done with this buffer before it is refilled
         buf ^= 1;
-        hits_cur = hits_next;
+        nh_cur = nh_next;
     }
     cp_async_wait<0>();
     if (inside) {
