@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 //     counter returns the count of earlier keys, shuffled to the peers;
 //  2. the tile's digit counts are published to the look-back words at once,
 //     so later tiles rarely wait for this one;
-//  3. keys and values are placed digit-sorted in shared memory;
+//  3. keys and values are placed digit-sorted in shared memory (one 8-byte
+//     store per element);
 //  4. the look-back over earlier tiles gives each digit its global start;
 //  5. every thread writes consecutive staged elements, so each digit's run
 //     is stored contiguously (coalesced).
@@ -82,8 +83,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
     __shared__ uint32_t s_gbase[RS_BINS];         // global start of each digit (all tiles)
     __shared__ uint32_t s_lstart[RS_BINS];        // start of each digit's run in the staged tile
     __shared__ uint32_t s_gofs[RS_BINS];          // global index minus staged index, per digit
-    __shared__ uint32_t s_key[RS_TILE];
-    __shared__ uint32_t s_val[RS_TILE];
+    __shared__ uint2 s_kv[RS_TILE];               // the tile staged digit-sorted: (key, value)
     __shared__ uint32_t s_scan[RS_WARPS + 1];
     __shared__ uint32_t s_tile;
     uint64_t n64v = n32 ? (uint64_t)*n32 : (uint64_t)*n64;
@@ -150,8 +150,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
             if (idx < n) {
                 const uint32_t dd = (key[it] >> shift) & 255u;
                 const uint32_t pos = s_lstart[dd] + s_wc[warp][dd] + rank[it];
-                s_key[pos] = key[it];
-                s_val[pos] = val[it];
+                s_kv[pos] = make_uint2(key[it], val[it]);
             }
         }
         // 4. look-back for digit d over earlier tiles (aggregate already
@@ -197,11 +196,11 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
         // 5. coalesced write of the staged tile
         const uint32_t tile_n = min((uint32_t)RS_TILE, n - tile * RS_TILE);
         for (uint32_t j = threadIdx.x; j < tile_n; j += RS_THREADS) {
-            const uint32_t k = s_key[j];
-            const uint32_t pos = s_gofs[(k >> shift) & 255u] + j;
+            const uint2 kv = s_kv[j];
+            const uint32_t pos = s_gofs[(kv.x >> shift) & 255u] + j;
             if (pos < n) {
-                keys_out[pos] = k;
-                vals_out[pos] = s_val[j];
+                keys_out[pos] = kv.x;
+                vals_out[pos] = kv.y;
             }
         }
         __syncthreads();
