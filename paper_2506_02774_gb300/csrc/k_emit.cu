@@ -183,39 +183,22 @@ void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32
                                        tile_passes, sentinel, status, ctr, fp);
 }
 
-// [start, end) of each tile in the sorted list; sentinel keys (>= n_tiles)
-// sort last and are skipped.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const Counters* __restrict__ ctr, uint64_t cap,
-                         uint32_t n_tiles, uint2* __restrict__ ranges) {
-    pdl_wait();
-    uint64_t n64 = ctr->n_pairs;
-    if (n64 > cap) n64 = cap;
-    const uint32_t n = (uint32_t)n64;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if (t >= n_tiles) continue;
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
-    }
-}
-
-void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
-                   int grid, cudaStream_t s) {
-    launch_k(k_ranges, grid, 256, s, keys, ctr, cap_pairs, n_tiles, ranges);
-}
-
 // Blend order: tiles by descending pair count (buckets of floor(log2(count+1)),
 // heaviest bucket first), so the long tiles start in the first wave and the
 // short ones fill in behind them.  One CTA; the order inside a bucket does
-// not matter (tiles are independent).
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, uint32_t n_tiles,
+// not matter (tiles are independent).  It also finishes the ranges the last
+// tile-sort pass recorded as (start, ~end) by atomic minima from all ones:
+// each becomes [start, end), or [0, 0) for a tile without pairs.
+__global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges, uint32_t n_tiles,
                                                      uint32_t* __restrict__ order) {
     pdl_wait();
     __shared__ uint32_t s_cnt[33], s_start[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const uint2 r = ranges[t];
+        uint2 r = ranges[t];
+        r = r.x == 0xFFFFFFFFu ? make_uint2(0u, 0u) : make_uint2(r.x, ~r.y);
+        ranges[t] = r;  // read back below by this same thread
         atomicAdd(&s_cnt[32 - __clz(r.y - r.x + 1u)], 1u);
     }
     __syncthreads();
@@ -230,7 +213,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
     }
 }
 
-void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {
+void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {
     launch_k(k_tile_order, 1, 1024, s, ranges, n_tiles, order);
 }
 

@@ -64,6 +64,12 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 //  4. the look-back over earlier tiles gives each digit its global start;
 //  5. every thread writes consecutive staged elements, so each digit's run
 //     is stored contiguously (coalesced).
+// The last pass of the tile sort also records each tile's range: a CTA's
+// staged elements are in final key order and each key's run is one
+// contiguous stretch of global positions, so the first and last element of
+// every run it holds give atomicMin / atomicMax updates of [start, end) (the
+// end kept as its complement, so both start from all ones and take a min).
+// Keys >= n_ranges (dropped slots) have no range.
 constexpr int LB_BATCH = 8;  // look-back words read per round trip
 
 template <bool HW_MATCH>
@@ -77,7 +83,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
                                                            unsigned long long* __restrict__ status,
                                                            uint32_t* __restrict__ ticket,
                                                            const FrameParams* __restrict__ fp,
-                                                           Counters* __restrict__ ctr) {
+                                                           Counters* __restrict__ ctr, uint2* __restrict__ ranges,
+                                                           uint32_t n_ranges) {
     pdl_wait();
     __shared__ uint32_t s_wc[RS_WARPS][RS_BINS];  // per-warp digit counts, then per-warp run offsets
     __shared__ uint32_t s_gbase[RS_BINS];         // global start of each digit (all tiles)
@@ -201,6 +208,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
             if (pos < n) {
                 keys_out[pos] = kv.x;
                 vals_out[pos] = kv.y;
+                if (ranges && kv.x < n_ranges) {
+                    if (j == 0 || s_kv[j - 1].x != kv.x) atomicMin(&ranges[kv.x].x, pos);
+                    if (j + 1 == tile_n || s_kv[j + 1].x != kv.x) atomicMin(&ranges[kv.x].y, ~(pos + 1u));
+                }
             }
         }
         __syncthreads();
@@ -215,13 +226,13 @@ void launch_radix_hist(const uint32_t* keys, const uint32_t* n32, const unsigned
 void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                        const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
                        const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
-                       Counters* ctr, int grid, cudaStream_t s, int hw_match) {
+                       Counters* ctr, int grid, cudaStream_t s, int hw_match, uint2* ranges, uint32_t n_ranges) {
     if (hw_match)
         launch_k(k_radix_pass<true>, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32,
-                  n64, cap, shift, hist, status, ticket, fp, ctr);
+                  n64, cap, shift, hist, status, ticket, fp, ctr, ranges, n_ranges);
     else
         launch_k(k_radix_pass<false>, grid, RS_THREADS, s, keys_in, vals_in, keys_out, vals_out, n32,
-                  n64, cap, shift, hist, status, ticket, fp, ctr);
+                  n64, cap, shift, hist, status, ticket, fp, ctr, ranges, n_ranges);
 }
 
 }  // namespace vgr

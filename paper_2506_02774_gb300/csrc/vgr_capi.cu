@@ -773,7 +773,7 @@ constexpr int EMIT_GRID_NUM = 5;
 uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
     return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
-           1u /*emit*/ + (uint32_t)tile_passes + 2u /*ranges, tile order*/ + 1u /*blend*/;
+           1u /*emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
 }
 
 // Enqueue one frame.  'scratch' selects the top-down cut.  Returns the
@@ -787,7 +787,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t n_tiles = fh.tiles_x * fh.tiles_y;
     cudaMemcpyAsync(v->fp_dev, v->fp_host, sizeof(FrameParams), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(v->ctr, 0, sizeof(Counters), s);
-    cudaMemsetAsync(v->ranges, 0, (size_t)n_tiles * sizeof(uint2), s);
+    cudaMemsetAsync(v->ranges, 0xFF, (size_t)n_tiles * sizeof(uint2), s);  // (start, ~end): both all ones
     const int prev = v->parity, cur = v->parity ^ 1;
     mark(VGR_STAGE_LOD);
     if (scratch) {
@@ -825,16 +825,17 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
                 tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan * EMIT_GRID_NUM / 4, s);
     mark(VGR_STAGE_TILE_SORT);
+    // (the last pass also records each tile's range)
     for (int p = 0; p < tile_passes; ++p) {
+        const bool last = p + 1 == tile_passes;
         launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
                           &v->ctr->n_cand, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
                           v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
-                          v->fp_dev, v->ctr, v->grid_scan, s, 1);
+                          v->fp_dev, v->ctr, v->grid_scan, s, 1, last ? v->ranges : nullptr, n_tiles);
     }
     const int fb = tile_passes & 1;
     v->last_tile_buf = fb;
     mark(VGR_STAGE_RANGES);
-    launch_ranges(v->pairK[fb], v->ctr, v->cap_pairs, n_tiles, v->ranges, v->grid_wide, s);
     launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
     mark(VGR_STAGE_BLEND);
     launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->vis.recA, v->vis.recB, v->vis.rgb, v->fp_dev, v->lut, v->image, v->ctr,

@@ -81,15 +81,14 @@ void launch_radix_hist(const uint32_t* keys, const uint32_t* n32, const unsigned
 void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                        const uint32_t* n32, const unsigned long long* n64, uint64_t cap, int shift,
                        const uint32_t* hist, unsigned long long* status, uint32_t* ticket, const FrameParams* fp,
-                       Counters* ctr, int grid, cudaStream_t s, int hw_match = 0);
+                       Counters* ctr, int grid, cudaStream_t s, int hw_match = 0, uint2* ranges = nullptr,
+                       uint32_t n_ranges = 0);
 
 // k_emit.cu
 void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
                  unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
 uint32_t emit_tile();
-void launch_ranges(const uint32_t* keys, const Counters* ctr, uint64_t cap_pairs, uint32_t n_tiles, uint2* ranges,
-                   int grid, cudaStream_t s);
-void launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
+void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
 
 // k_blend.cu
 void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
