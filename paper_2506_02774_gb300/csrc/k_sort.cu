@@ -202,15 +202,22 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
         __syncthreads();
         // 5. coalesced write of the staged tile
         const uint32_t tile_n = min((uint32_t)RS_TILE, n - tile * RS_TILE);
-        for (uint32_t j = threadIdx.x; j < tile_n; j += RS_THREADS) {
-            const uint2 kv = s_kv[j];
+        for (uint32_t j0 = threadIdx.x & ~31u; j0 < tile_n; j0 += RS_THREADS) {  // warp-uniform trips
+            const uint32_t j = j0 + lane;
+            const bool valid = j < tile_n;
+            const uint2 kv = valid ? s_kv[j] : make_uint2(0xFFFFFFFFu, 0u);
             const uint32_t pos = s_gofs[(kv.x >> shift) & 255u] + j;
-            if (pos < n) {
+            if (valid && pos < n) {
                 keys_out[pos] = kv.x;
                 vals_out[pos] = kv.y;
-                if (ranges && kv.x < n_ranges) {
-                    if (j == 0 || s_kv[j - 1].x != kv.x) atomicMin(&ranges[kv.x].x, pos);
-                    if (j + 1 == tile_n || s_kv[j + 1].x != kv.x) atomicMin(&ranges[kv.x].y, ~(pos + 1u));
+            }
+            if (ranges) {  // neighbours' keys from the adjacent lanes, across warps from shared memory
+                uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, kv.x, 1), kn = __shfl_down_sync(0xFFFFFFFFu, kv.x, 1);
+                if (lane == 0) kp = j > 0 ? s_kv[j - 1].x : ~kv.x;
+                if (lane == 31) kn = j + 1 < tile_n ? s_kv[j + 1].x : ~kv.x;
+                if (valid && pos < n && kv.x < n_ranges) {
+                    if (kp != kv.x) atomicMin(&ranges[kv.x].x, pos);
+                    if (kn != kv.x) atomicMin(&ranges[kv.x].y, ~(pos + 1u));
                 }
             }
         }
