@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
             const uint2 kv = valid ? s_kv[j] : make_uint2(0xFFFFFFFFu, 0u);
             const uint32_t pos = s_gofs[(kv.x >> shift) & 255u] + j;
             if (valid && pos < n) {
-                keys_out[pos] = kv.x;
+                if (keys_out) keys_out[pos] = kv.x;  // null: only the permutation is wanted
                 vals_out[pos] = kv.y;
             }
             if (ranges) {  // neighbours' keys from the adjacent lanes, across warps from shared memory

@@ -812,7 +812,9 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     for (int p = 0; p < 4; ++p) {
         const uint32_t* kin = p == 0 ? v->vis.depth : v->sortK[(p + 1) & 1];
         const uint32_t* vin = p == 0 ? nullptr : v->sortV[(p + 1) & 1];
-        launch_radix_pass(kin, vin, v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_front, nullptr, v->cap_vis, 8 * p,
+        // the last pass writes only the permutation (the sorted keys are not read)
+        launch_radix_pass(kin, vin, p == 3 ? nullptr : v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_front, nullptr,
+                          v->cap_vis, 8 * p,
                           v->ctr->depth_hist[p], v->status + v->st_depth + p * v->st_depth_stride,
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
     }
