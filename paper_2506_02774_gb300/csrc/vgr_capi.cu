@@ -63,7 +63,12 @@ vgr_status dalloc(T** p, size_t count, uint64_t* acct) {
         return fail(e == cudaErrorMemoryAllocation ? VGR_E_NOMEM : VGR_E_CUDA, "cudaMalloc of %zu bytes: %s",
                     count * sizeof(T), cudaGetErrorString(e));
     }
+    // The zero fill runs on the legacy default stream, which does not order
+    // with the views' non-blocking streams: wait for it here, or a frame
+    // already running on such a stream could see the fill land on top of its
+    // own writes (a range table reset to zero, look-back words cleared).
     VGR_CK(cudaMemset(*p, 0, count * sizeof(T)));
+    VGR_CK(cudaStreamSynchronize(cudaStreamLegacy));
     if (acct) *acct += count * sizeof(T);
     return VGR_OK;
 }
@@ -86,6 +91,11 @@ bool vgr::pdl_enabled() {
         return !(e && e[0] == '0');
     }();
     return on;
+}
+
+vgr::PdlState& vgr::pdl_state() {
+    static thread_local PdlState st;
+    return st;
 }
 
 struct vgr_hierarchy {
@@ -171,6 +181,7 @@ struct vgr_view {
     uint32_t graph_tiles = 0;
     // frame in flight between submit and finish
     bool pending = false;
+    bool broken = false;  // a buffer could not be grown: its memory is gone, no further frames
     PendingFrame pend;
     cudaEvent_t done_ev = nullptr;
     cudaEvent_t join_ev = nullptr;  // end of this view's branch in a captured batch
@@ -700,6 +711,7 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
         const uint32_t m = v->opts.lut_size;
         for (uint32_t i = 0; i <= m; ++i) host_lut[i] = (float)std::exp(-5.55 * (double)i / (double)m);
         cudaError_t ce = cudaMemcpy(v->lut, host_lut, sizeof(host_lut), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(cudaStreamLegacy);  // see dalloc
         if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "lut: %s", cudaGetErrorString(ce)); }
     }
 #undef VGR_VTRY
@@ -788,6 +800,9 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     cudaMemcpyAsync(v->fp_dev, v->fp_host, sizeof(FrameParams), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(v->ctr, 0, sizeof(Counters), s);
     cudaMemsetAsync(v->ranges, 0xFF, (size_t)n_tiles * sizeof(uint2), s);  // (start, ~end): both all ones
+    // the first kernel waits for the copies above in plain stream order; with
+    // stage events between the kernels none of them is launched early
+    PdlScope pdl(!timing);
     const int prev = v->parity, cur = v->parity ^ 1;
     mark(VGR_STAGE_LOD);
     if (scratch) {
@@ -978,6 +993,7 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* ho
 vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
     if (!v) return fail(VGR_E_INVALID, "null view");
     if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is already in flight");
+    if (v->broken) return fail(VGR_E_NOMEM, "a buffer of this view could not be grown; destroy the view");
     vgr_status s = check_camera(cam, tau);
     if (s != VGR_OK) return s;
     VGR_CK(cudaSetDevice(v->h->device));
@@ -1138,14 +1154,19 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
             return fail(VGR_E_TIMEOUT, "top-down cut exceeded the tree depth");
         } else if (flags & F_OVF_CUT) {
             const uint32_t nc = (uint32_t)std::min<uint64_t>(v->h->n_nodes, (uint64_t)n_cut + n_cut / 4 + 1024);
-            if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_vis(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK)
+            if ((s = alloc_cut(v, nc)) != VGR_OK || (s = alloc_vis(v, nc)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) {
+                v->broken = true;
                 return s;
+            }
             q.scratch = true;  // the previous cut lived in the old buffers
             again = true;
         } else if (flags & F_OVF_PAIRS) {
             const uint64_t np = ch->n_cand + ch->n_cand / 4 + 4096;
             if (np >= 0xFFFFFFFFull) return fail(VGR_E_OVERFLOW, "more than 2^32 pairs");
-            if ((s = alloc_pairs(v, np)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) return s;
+            if ((s = alloc_pairs(v, np)) != VGR_OK || (s = alloc_status(v)) != VGR_OK) {
+                v->broken = true;
+                return s;
+            }
             again = true;
         }
         if (!again) break;

@@ -13,9 +13,25 @@ void set_last_error(const char* msg);
 // a kernel's CTAs may be scheduled while the previous kernel drains, and each
 // kernel waits (griddepcontrol.wait, its first statement) until the previous
 // one has completed and its writes are visible, so ordering is unchanged and
-// only the launch latency overlaps.  VGR_PDL=0 in the environment turns it
-// off (plain stream order).
+// only the launch latency overlaps.  That wait covers a preceding kernel only:
+// a kernel that follows copies, memsets or event records in the stream is
+// launched in plain stream order (PdlScope), so it cannot start before them.
+// VGR_PDL=0 in the environment turns it off everywhere.
 bool pdl_enabled();
+struct PdlState {
+    bool on = true;          // frame kernels may use it (off while stage events sit between kernels)
+    bool plain_next = false; // the next launch follows a non-kernel operation
+};
+PdlState& pdl_state();  // per host thread
+// For the kernels of one frame: the first launch in plain order, PDL for the
+// rest unless 'on' is false; restores the defaults when it ends.
+struct PdlScope {
+    explicit PdlScope(bool on) {
+        pdl_state().on = on;
+        pdl_state().plain_next = true;
+    }
+    ~PdlScope() { pdl_state() = PdlState{}; }
+};
 template <typename... KArgs, typename... Args>
 inline void launch_ks(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                       Args... args) {
@@ -28,7 +44,9 @@ inline void launch_ks(void (*kernel)(KArgs...), unsigned grid, unsigned block, s
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    PdlState& st = pdl_state();
+    cfg.numAttrs = pdl_enabled() && st.on && !st.plain_next ? 1 : 0;
+    st.plain_next = false;
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 template <typename... KArgs, typename... Args>

@@ -107,7 +107,8 @@ extern "C" vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* va
         if ((e = cudaMalloc(&c.fp, sizeof(FrameParams))) != cudaSuccess ||
             (e = cudaMemset(c.fp, 0, sizeof(FrameParams))) != cudaSuccess ||
             (e = cudaMalloc(&c.ctr, sizeof(Counters))) != cudaSuccess ||
-            (e = cudaMemset(c.ctr, 0, sizeof(Counters))) != cudaSuccess)
+            (e = cudaMemset(c.ctr, 0, sizeof(Counters))) != cudaSuccess ||
+            (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess)  // the fills before any use on 's'
             return sort_fail(VGR_E_NOMEM, "sort scratch", e);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -120,7 +121,8 @@ extern "C" vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* va
         c.status = nullptr;
         c.status_words = 0;
         if ((e = cudaMalloc(&c.status, words * sizeof(unsigned long long))) != cudaSuccess ||
-            (e = cudaMemset(c.status, 0, words * sizeof(unsigned long long))) != cudaSuccess)
+            (e = cudaMemset(c.status, 0, words * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess)
             return sort_fail(VGR_E_NOMEM, "sort look-back words", e);
         c.status_words = words;
     }

@@ -182,3 +182,29 @@ def test_batch_with_variant_views(small_sh3_scene, h_small):
         check_image(res[2].image().cpu().numpy(), ref)
     for v in batch + solo:
         v.close()
+
+
+def test_busy_first_frames_equal_solo():
+    """Many clients admitted at once on a busy GPU (1M leaves at 1080p and
+    720p, every first frame in flight together, buffers growing): each
+    client's first frame equals the same camera rendered alone.  New views'
+    buffers are zero-filled before any of their frames may run, whatever the
+    other streams are doing."""
+    sc = scenegen.make_scene("m1")
+    h = vgr.Hierarchy(sc)
+    C = 12
+    sizes = [(1920, 1080) if c % 2 else (1280, 720) for c in range(C)]
+    cams = [scenegen.camera((20.0 + 7.0 * c, 100.0 - 3.0 * c, 10.0), 0.3 * c, W, H, 1100.0 * W / 1920.0)
+            for c, (W, H) in enumerate(sizes)]
+    for round_ in range(2):  # the second server reuses the first one's freed memory
+        sv = vgr.Server(h, C, max_inflight=0, host_images=True)
+        res = sv.serve([dict(client=c, arrival_s=0.0, tau=3.0, cam=cams[c]) for c in range(C)])
+        assert (res["status"] == 0).all(), res
+        for c in range(C):
+            v = vgr.View(h)
+            r = v.render(cams[c], 3.0)
+            W, H = sizes[c]
+            assert np.array_equal(sv.client_host_image(c, H, W), r.image().cpu().numpy()), (round_, c)
+            v.close()
+        sv.close()
+    h.close()
