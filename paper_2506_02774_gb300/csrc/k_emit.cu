@@ -34,7 +34,7 @@ constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
 
 uint32_t emit_tile() { return EM_TILE; }
 
-__global__ void __launch_bounds__(EM_THREADS) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
+__global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
                                                      VisBuffers vis,
                                                      uint32_t* __restrict__ pair_key,
                                                      uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,

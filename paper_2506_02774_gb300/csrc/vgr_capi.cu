@@ -779,8 +779,8 @@ int tile_passes_for(uint32_t n_tiles) {
 }
 
 // The emission's grid relative to the look-back kernels' (x/4): it keeps
-// five CTAs resident per SM, the radix passes four.
-constexpr int EMIT_GRID_NUM = 5;
+// six CTAs resident per SM (40 registers a thread), the radix passes four.
+constexpr int EMIT_GRID_NUM = 6;
 
 uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
