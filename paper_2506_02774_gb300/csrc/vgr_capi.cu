@@ -185,6 +185,9 @@ struct vgr_view {
     PendingFrame pend;
     cudaEvent_t done_ev = nullptr;
     cudaEvent_t join_ev = nullptr;  // end of this view's branch in a captured batch
+    // the colour pass runs beside the sorts and the emission on a second stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     uint64_t uid = 0;               // unique per view ever created (batch graph keys)
     uint64_t gen = 0;               // bumped whenever the view's buffers change (graphs invalid)
     uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
@@ -616,6 +619,9 @@ void destroy_view(vgr_view* v) {
         if (e) cudaEventDestroy(e);
     if (v->done_ev) cudaEventDestroy(v->done_ev);
     if (v->join_ev) cudaEventDestroy(v->join_ev);
+    if (v->side_fork) cudaEventDestroy(v->side_fork);
+    if (v->side_join) cudaEventDestroy(v->side_join);
+    if (v->side) cudaStreamDestroy(v->side);
     forget_batches(v->uid);
     if (v->own_stream && v->stream) cudaStreamDestroy(v->stream);
     delete v;
@@ -701,6 +707,9 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     {
         cudaError_t ce = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->join_ev, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->side_fork, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->side_join, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking);
         if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
         static std::atomic<uint64_t> next_uid{1};
         v->uid = next_uid.fetch_add(1);
@@ -821,6 +830,17 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_PREPROCESS);
     launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, fh.lod_interp != 0,
                       v->grid_wide, s);
+    if (!timing) {
+        // colour (bandwidth-bound) on the side stream, beside the depth sort,
+        // emission and tile sort (latency-bound); joined before the blend
+        cudaEventRecord(v->side_fork, s);
+        cudaStreamWaitEvent(v->side, v->side_fork, 0);
+        pdl_state().plain_next = true;
+        launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb,
+                     fh.lod_interp != 0, v->grid_wide, v->side);
+        cudaEventRecord(v->side_join, v->side);
+        pdl_state().plain_next = true;  // the depth sort follows an event record on s
+    }
     mark(VGR_STAGE_DEPTH_SORT);
     // every potentially visible entry is sorted; culled ones carry the key
     // 0xFFFFFFFF and land last (the digit histograms come from preprocess)
@@ -834,9 +854,11 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
-    mark(VGR_STAGE_COLOR);
-    launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb, fh.lod_interp != 0,
-                 v->grid_wide, s);
+    if (timing) {  // stage by stage
+        mark(VGR_STAGE_COLOR);
+        launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb,
+                     fh.lod_interp != 0, v->grid_wide, s);
+    }
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
@@ -855,6 +877,10 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_RANGES);
     launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
     mark(VGR_STAGE_BLEND);
+    if (!timing) {
+        cudaStreamWaitEvent(s, v->side_join, 0);
+        pdl_state().plain_next = true;
+    }
     launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->vis.recA, v->vis.recB, v->vis.rgb, v->fp_dev, v->lut, v->image, v->ctr,
                  v->opts.filter, v->opts.exp_mode, s);
     mark(VGR_N_STAGES);
