@@ -797,12 +797,15 @@ uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
            1u /*emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
 }
 
-// Enqueue one frame.  'scratch' selects the top-down cut.  Returns the
-// number of kernels launched.
-uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
+// Enqueue one frame.  'scratch' selects the top-down cut; 'captured': the
+// frame is being captured into a graph, where the colour pass runs on the
+// side stream (launched one by one, the extra stream calls cost more host
+// time than the overlap saves).  Returns the number of kernels launched.
+uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured) {
     const SceneDev& sc = v->h->dev;
     cudaStream_t s = v->stream;
     const bool timing = v->opts.timing != 0;
+    const bool side = captured && !timing;
     auto mark = [&](int i) { if (timing) cudaEventRecord(v->ev[i], s); };
     const FrameParams& fh = *v->fp_host;
     const uint32_t n_tiles = fh.tiles_x * fh.tiles_y;
@@ -830,7 +833,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_PREPROCESS);
     launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, fh.lod_interp != 0,
                       v->grid_wide, s);
-    if (!timing) {
+    if (side) {
         // colour (bandwidth-bound) on the side stream, beside the depth sort,
         // emission and tile sort (latency-bound); joined before the blend
         cudaEventRecord(v->side_fork, s);
@@ -854,7 +857,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
-    if (timing) {  // stage by stage
+    if (!side) {
         mark(VGR_STAGE_COLOR);
         launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb,
                      fh.lod_interp != 0, v->grid_wide, s);
@@ -877,7 +880,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
     mark(VGR_STAGE_RANGES);
     launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
     mark(VGR_STAGE_BLEND);
-    if (!timing) {
+    if (side) {
         cudaStreamWaitEvent(s, v->side_join, 0);
         pdl_state().plain_next = true;
     }
@@ -894,7 +897,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes) {
 // (top-down?, parity) pair, captured on first use.
 vgr_status run_frame(vgr_view* v, bool scratch, int tile_passes, uint32_t n_tiles, uint32_t* kernels) {
     if (!v->opts.use_graph || v->opts.timing) {
-        *kernels += enqueue_frame(v, scratch, tile_passes);
+        *kernels += enqueue_frame(v, scratch, tile_passes, false);
         VGR_CK(cudaGetLastError());
         return VGR_OK;
     }
@@ -905,7 +908,7 @@ vgr_status run_frame(vgr_view* v, bool scratch, int tile_passes, uint32_t n_tile
     cudaGraphExec_t& ge = v->graph[scratch ? 1 : 0][v->parity];
     if (!ge) {
         VGR_CK(cudaStreamBeginCapture(v->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_frame(v, scratch, tile_passes);
+        enqueue_frame(v, scratch, tile_passes, true);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(v->stream, &g);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1110,7 +1113,7 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
             vgr_view* v = views[i];
             e = cudaStreamWaitEvent(v->stream, bs.fork, 0);
             if (e != cudaSuccess) break;
-            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes);
+            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, true);
             e = cudaEventRecord(v->join_ev, v->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
         }
