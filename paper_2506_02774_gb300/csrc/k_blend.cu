@@ -9,12 +9,13 @@
 // footprint box: outside the box rho < ln alpha* - ln theta holds with a
 // margin, so a pair whose box misses the warp's two rows would fail the
 // Eq. 4 test at every one of its pixels); within a tile the pairs are in
-// depth order.  The warp reads 32 pair values at a time (coalesced), keeps
-// those with its row bit, and copies their 48-byte records (mean, conic,
-// threshold, opacity, colour) with cp.async into its own double-buffered
-// slice of shared memory; the copies of the next 32 pairs are in flight
-// while the current ones are walked, two at a time for instruction-level
-// parallelism.  Before the walk each lane rewrites its staged record for the
+// depth order.  The warp scans the pair values (coalesced, a batch ahead),
+// queues those with its row bit in a ring, and copies the 48-byte records
+// (mean, conic, threshold, opacity, colour) of 32 queued hits at a time with
+// cp.async into its own double-buffered slice of shared memory; the copies
+// of the next 32 hits are in flight while the current ones are walked, two
+// at a time for instruction-level parallelism.  Before the walk each lane
+// rewrites its staged record for the
 // warp's two rows (the row offsets of the mean folded into the conic
 // terms), so a pixel evaluates rho with one subtraction and two FMAs.
 // Records are read only for the pairs a warp needs, and the eight warps of
