@@ -1,6 +1,6 @@
 // k_emit.cu -- emission of (tile, Gaussian) pairs in depth order with the
-// tile-level preemptive alpha test, and the per-tile ranges of the sorted
-// pair list.
+// tile-level preemptive alpha test, and the blend's tile order (which also
+// finishes the per-tile ranges the last tile-sort pass records).
 //
 // Visible Gaussians are visited in depth order (the output of the depth
 // sort), 512 per CTA tile (2 per thread).  Each one owns as many pair slots as it has
