@@ -1,9 +1,11 @@
 // vgr_capi.cu -- the C ABI (include/vgr.h): hierarchy upload and validation,
 // per-view buffers, and the per-frame launch sequence
 //   LoD (temporal update or top-down levels) -> cut compaction ->
-//   preprocess -> depth sort -> colour -> emission -> tile sort -> ranges
-//   and blend order -> blend
-// all enqueued on the view's stream (or replayed as one captured graph).
+//   preprocess -> depth sort -> colour -> emission -> tile sort (its last
+//   pass records the tile ranges) -> blend order -> blend
+// all enqueued on the view's stream (or replayed as one captured graph, in
+// which the colour pass runs on a second stream beside the depth sort, the
+// emission and the tile sort).
 // Counts stay on the device (every kernel reads its element count from
 // device memory), so a frame needs no host round trip until its end, where
 // a 56-byte status block and the cut sizes are read back: buffer overflows
