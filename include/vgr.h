@@ -114,7 +114,8 @@ typedef struct {
     uint32_t timing;         /* 1: record per-stage device times into vgr_frame_stats */
     uint32_t use_graph;      /* 1: replay each frame as one captured CUDA graph (captured on first use per
                                 cut mode and buffer parity; re-captured after a buffer grows or the image
-                                size changes); ignored while timing is set.  Default 0. */
+                                size changes; inside it the colour pass runs on a second stream the view
+                                owns, beside the sorts); ignored while timing is set.  Default 0. */
     uint64_t cut_capacity;   /* initial capacities; 0 = automatic.  Grown on demand. */
     uint64_t pair_capacity;
     uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
