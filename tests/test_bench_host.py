@@ -1,0 +1,48 @@
+"""Host-side helpers of bench.py (CPU): the code hash that keys the committed
+DRAM-traffic record, and the rule that a record taken on other code is not
+reported."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_code_hash_ignores_comments_and_spacing(tmp_path):
+    a = tmp_path / "a.cu"
+    a.write_text("int f(int x) {\n    return x + 1;  // one more\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("// a new header line\nint f(int  x) {\n\n        return x + 1;\n}  // end\n")
+    c = tmp_path / "c.cu"
+    c.write_text("int f(int x) {\n    return x + 2;\n}\n")
+    assert bench.code_sha256(str(a)) == bench.code_sha256(str(b))
+    assert bench.code_sha256(str(a)) != bench.code_sha256(str(c))
+
+
+def test_traffic_record_only_for_the_code_it_was_taken_on(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2506_02774_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = csrc / "k_blend.cu"
+    src.write_text("__global__ void k() {}\n")
+    rec = {"k_blend": {"code_sha256": bench.code_sha256(str(src)), "dram_bytes_per_launch": 123456}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic("k_blend", "k_blend.cu", 1.0) == 123456
+    src.write_text("// comment only\n__global__ void k() {}\n")
+    assert bench._traffic("k_blend", "k_blend.cu", 1.0) == 123456
+    src.write_text("__global__ void k() { int x = 0; }\n")
+    assert bench._traffic("k_blend", "k_blend.cu", 1.0) is None
+    assert bench._traffic("k_emit", "k_emit.cu", 1.0) is None
+
+
+def test_committed_traffic_record_matches_the_blend():
+    """The committed record was taken on the blend as it is in the tree."""
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["k_blend"]
+    src = os.path.join(ROOT, "paper_2506_02774_gb300", "csrc", "k_blend.cu")
+    assert rec["code_sha256"] == bench.code_sha256(src)
+    assert rec["dram_bytes_per_launch"] > 0
