@@ -82,3 +82,44 @@ def test_deterministic_across_thread_counts():
         env = dict(os.environ, OMP_NUM_THREADS=nt, PYTHONPATH=root)
         outs.append(subprocess.check_output([sys.executable, "-c", code], env=env, cwd=root).strip())
     assert outs[0] == outs[1]
+
+
+def _yaw(cam):
+    # camera forward axis (third row of R) in the z-up world
+    f = np.asarray(cam["R"], np.float64).reshape(3, 3)[2]
+    return np.arctan2(f[1], f[0])
+
+
+def test_walks_follow_the_stated_motion():
+    """Each workload's walk moves at its speed on its height and keeps the yaw
+    rate within 2 pi A / period (18.9 deg/s for the 1M box and the city)."""
+    for name in ("tiny", "m1", "city"):
+        c = scenegen.CONFIGS[name]
+        cams = [scenegen.trajectory(name, f) for f in range(0, min(c["frames"], 120))]
+        pos = np.array([np.asarray(x["pos"], np.float64) for x in cams])
+        step = np.linalg.norm(np.diff(pos, axis=0), axis=1)
+        np.testing.assert_allclose(step, c["speed"] / c["fps"], rtol=1e-3)
+        np.testing.assert_allclose(pos[:, 2], c["start"][2], atol=1e-5)
+        yaw = np.unwrap([_yaw(x) for x in cams])
+        rate = np.abs(np.diff(yaw)) * c["fps"]
+        bound = 2 * np.pi * np.radians(c["yaw_amp_deg"]) / c["yaw_period"]
+        assert rate.max() <= bound * 1.001
+        assert cams[0]["width"] == c["width"] and cams[0]["fx"] == np.float32(c["focal"])
+
+
+def test_street_walks_stay_on_streets():
+    """The per-view and per-client walks run along a street of the 40 m grid
+    (one coordinate fixed at 40 k, k in 1..36) at the city's height, with the
+    focal length scaled with the image width."""
+    c = scenegen.CONFIGS["city"]
+    for seed in (200, 201, 237, 300, 331):
+        for (W, H) in scenegen.RESOLUTIONS.values():
+            cams = [scenegen.street_trajectory("city", seed, f, W, H) for f in (0, 150, 300)]
+            pos = np.array([np.asarray(x["pos"], np.float64) for x in cams])
+            fixed = [np.allclose(pos[:, a], pos[0, a], atol=1e-3) for a in (0, 1)]
+            assert sum(fixed) == 1
+            a = fixed.index(True)
+            k = pos[0, a] / 40.0
+            assert abs(k - round(k)) < 1e-4 and 1 <= round(k) <= 36
+            np.testing.assert_allclose(pos[:, 2], c["start"][2], atol=1e-5)
+            assert cams[0]["width"] == W and np.isclose(cams[0]["fx"], c["focal"] * W / c["width"])
