@@ -7,7 +7,10 @@ tile binning, sort and front-to-back blending (Sec. 3.1 'Rasterization').
   (brute-force scan);
 * rho_max over a tile rectangle bounds rho at every pixel and is attained;
 * single- and multi-Gaussian images are checked against hand-computed
-  values, including the T < 1e-4 termination rule.
+  values, including the T < 1e-4 termination rule and the 0.99 alpha cap;
+* every candidate's margin is the maximum of rho over its tile's pixel-centre
+  hull (found by a bounded solver), Gaussians below alpha* get no tile, and
+  equal depth keys blend in node-id order.
 """
 import math
 
@@ -195,3 +198,81 @@ def test_sorted_pairs_are_ordered(tiny_scene):
     assert ts[0] == 0 and ts[-1] == len(t)
     for tile in range(0, r["n_tiles"], 5):
         assert np.all(t[ts[tile]:ts[tile + 1]] == tile)
+
+
+def test_alpha_is_capped_at_0_99():
+    """An opaque Gaussian (theta = 1) centred on a pixel centre: alpha is
+    capped at 0.99 there, so the pixel is 0.99 rgb and T ends at 0.01 (an
+    uncapped alpha of 1 would take T to 0 < 1e-4 and stop before adding)."""
+    cam = _cam(f=100.0, W=64, H=48, cx=32.5, cy=24.5)
+    rgb = (0.8, 0.3, 0.6)
+    sc = _flat_scene([(0, 0, 3.0)], [[0.04, 0, 0, 0.04, 0, 0.04]], [1.0], [_dc_for(rgb)])
+    r = oracle.render(sc, cam, 0.0)
+    rgbf = np.array([0.5 + C0 * np.float64(np.float32(d)) for d in _dc_for(rgb)])
+    np.testing.assert_allclose(r["image"][24, 32], 0.99 * rgbf, rtol=1e-12)
+    assert r["n_contrib"][24, 32] == 1
+
+
+def test_gaussian_level_filter_drops_faint_gaussians():
+    """alpha <= theta everywhere, so a Gaussian with theta < alpha* = 1/255
+    can never contribute and gets no candidate tile at all; just above
+    alpha* it gets the tiles around its centre, and the tile holding the
+    centre is kept (rho_max = 0 >= ln alpha* - ln theta)."""
+    cam = _cam(f=100.0, W=64, H=48)
+    for theta, has in ((0.0035, False), (0.0045, True)):
+        sc = _flat_scene([(0.05, 0.02, 3.0)], [[0.04, 0, 0, 0.04, 0, 0.04]], [theta], [_dc_for((1, 1, 1))])
+        r = oracle.render(sc, cam, 0.0)
+        assert (r["n_cand"] > 0) == has
+        assert (r["n_pairs"] > 0) == has
+        assert r["n_visible"] == int(has)
+
+
+def test_equal_depth_ties_go_to_the_lower_node_id():
+    """Two coincident Gaussians with the same FP32 depth key: the pair order
+    is (tile, depth key, node id), so the lower node id is blended first."""
+    cam = _cam(f=100.0, W=64, H=48, cx=32.5, cy=24.5)
+    red, green = (0.9, 0.1, 0.1), (0.1, 0.9, 0.1)
+    a = np.float64(np.float32(0.9))
+    for first, second in ((red, green), (green, red)):
+        sc = _flat_scene([(0, 0, 3.0), (0, 0, 3.0)], [[0.04, 0, 0, 0.04, 0, 0.04]] * 2, [0.9, 0.9],
+                         [_dc_for(first), _dc_for(second)])
+        r = oracle.render(sc, cam, 0.0)
+        f1 = np.array([0.5 + C0 * np.float64(np.float32(d)) for d in _dc_for(first)])
+        f2 = np.array([0.5 + C0 * np.float64(np.float32(d)) for d in _dc_for(second)])
+        np.testing.assert_allclose(r["image"][24, 32], a * f1 + a * (1 - a) * f2, rtol=1e-12)
+
+
+def test_tile_margin_is_the_max_over_the_pixel_centre_hull(tiny_scene):
+    """For every candidate pair, margin + (ln alpha* - ln theta) is the maximum
+    of rho over the convex hull of the tile's pixel centres, clipped to the
+    image (the ragged last column and row included).  rho is concave, so a
+    bounded quasi-Newton solve finds that maximum independently."""
+    opt = pytest.importorskip("scipy.optimize")
+    cam = scenegen.camera((2.0, 10.0, 2.5), 0.1, 88, 56, 60.0)
+    r = oracle.render(tiny_scene, cam, 3.0)
+    TW, TH = r["tiles"]
+    W, H = cam["width"], cam["height"]
+    rng = np.random.default_rng(3)
+    cands = np.arange(len(r["cand_tile"]))
+    edge = cands[(r["cand_tile"] % TW == TW - 1) | (r["cand_tile"] // TW == TH - 1)]
+    assert len(edge) > 20
+    pick = np.concatenate([rng.choice(cands, 150, replace=False), rng.choice(edge, 50, replace=False)])
+    for c in pick:
+        p = r["proj"][r["cand_idx"][c]]
+        t = int(r["cand_tile"][c])
+        tx, ty = t % TW, t // TW
+        lo = (16 * tx + 0.5, 16 * ty + 0.5)
+        hi = (min(16 * tx + 15.5, W - 0.5), min(16 * ty + 15.5, H - 0.5))
+        a, b, cc = p["conic"]
+
+        def neg(x):
+            dx, dy = x[0] - p["u"], x[1] - p["v"]
+            val = 0.5 * (a * dx * dx + cc * dy * dy) + b * dx * dy
+            return val, np.array([a * dx + b * dy, cc * dy + b * dx])
+
+        x0 = np.clip([p["u"], p["v"]], lo, hi)
+        res = opt.minimize(neg, x0, jac=True, method="L-BFGS-B", bounds=list(zip(lo, hi)),
+                           options=dict(ftol=1e-15, gtol=1e-12, maxiter=200))
+        want = -res.fun
+        got = r["cand_margin"][c] + p["thr"]
+        assert got == pytest.approx(want, rel=1e-7, abs=1e-7), (c, tx, ty)

@@ -121,3 +121,23 @@ def test_lod_k_is_fp32():
     # tau / f and its square are single-rounded FP32 operations
     t = np.float32(np.float32(3.0) / np.float32(1100.0))
     assert oracle.lod_k(3.0, 1100.0) == np.float32(t * t)
+
+
+def test_granularity_boundary_is_strict():
+    """A node is refined only while its projected size R f / d is above tau,
+    i.e. d^2 (tau / f)^2 < R^2; at equality it stays in the cut.  With tau = f
+    (k = 1) and d = 2 the boundary is R^2 = 4, exactly representable."""
+    sc = dict(parent=np.array([0xFFFFFFFF, 0, 0], np.uint32), first_child=np.array([1, 0, 0], np.uint32),
+              n_child=np.array([2, 0, 0], np.uint8),
+              mean=np.array([[0, 0, 2], [0, 0.5, 2], [0, -0.5, 2]], np.float32),
+              cov6=np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (3, 1)),
+              opacity=np.full(3, 0.5, np.float32), sh=np.zeros((3, 1, 3), np.float32),
+              radius2=np.array([4.0, 1.0, 1.0], np.float32), sh_degree=0, n_nodes=3)
+    cam = np.zeros(3, np.float32)
+    k = oracle.lod_k(100.0, 100.0)
+    assert k == np.float32(1.0)
+    assert not oracle.expand(sc, 0, cam, k)
+    assert oracle.cut(sc, cam, k).tolist() == [0]
+    sc["radius2"] = np.array([np.nextafter(np.float32(4.0), np.float32(5.0)), 1.0, 1.0], np.float32)
+    assert oracle.expand(sc, 0, cam, k)
+    assert oracle.cut(sc, cam, k).tolist() == [1, 2]

@@ -178,3 +178,32 @@ def test_sh_matches_scipy():
                 c = complex(sp.sph_harm_y(l, abs(m), theta, phi))  # includes the Condon-Shortley phase
                 want = c.real if m == 0 else math.sqrt(2) * (c.real if m > 0 else c.imag)
                 assert Y[l * l + l + m] == pytest.approx(want, abs=1e-12)
+
+
+def test_near_plane_boundary_is_strict():
+    # kept iff the FP32 depth key is above z_near: a mean exactly on the plane is culled
+    cov = [0.01, 0, 0, 0.01, 0, 0.01]
+    zn = np.float32(0.2)
+    assert oracle.render(_one((0, 0, zn), cov), _cam(), 0.0)["proj"][0]["valid"] == 0
+    above = np.nextafter(zn, np.float32(1.0))
+    assert oracle.render(_one((0, 0, above), cov), _cam(), 0.0)["proj"][0]["valid"] == 1
+
+
+def test_sh_view_direction_is_camera_to_mean():
+    """Degree-1 colour at a mean seen along d = (0.6, 0, 0.8) from the camera:
+    the Y_10 (c1 z) coefficient in red and the Y_11 (-c1 x) coefficient in
+    green give 0.5 + 0.8 c1 and 0.5 - 0.6 c1; the opposite direction would
+    swap the signs."""
+    sh = np.zeros((4, 3), np.float32)
+    sh[2, 0] = 1.0
+    sh[3, 1] = 1.0
+    sc = scenegen.single_node_scene((0.75, 0.0, 1.0), [0.01, 0, 0, 0.01, 0, 0.01], 0.8, sh, sh_degree=1)
+    p = oracle.render(sc, _cam(f=40.0), 0.0)["proj"][0]
+    assert p["valid"] == 1
+    c1 = math.sqrt(3 / (4 * math.pi))
+    np.testing.assert_allclose(p["rgb"], [0.5 + 0.8 * c1, 0.5 - 0.6 * c1, 0.5], rtol=1e-12)
+    # seen from the far side of the mean, the odd band changes sign
+    cam = _cam(f=40.0, pos=(1.5, 0.0, 2.0), R=np.diag([-1.0, 1.0, -1.0]))
+    q = oracle.render(sc, cam, 0.0)["proj"][0]
+    assert q["valid"] == 1
+    np.testing.assert_allclose(q["rgb"], [0.5 - 0.8 * c1, 0.5 + 0.6 * c1, 0.5], rtol=1e-12)
