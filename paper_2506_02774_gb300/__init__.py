@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (EXP_EXACT, EXP_LUT, FILTER_CANONICAL, FILTER_PREEMPTIVE, STAGES, STORE_FP32, STORE_HALF,
                    VgrError)
 
-__all__ = ["Hierarchy", "View", "FrameResult", "Server", "render_batch", "camera_struct", "sort_pairs", "VgrError",
+__all__ = ["Renderer", "Hierarchy", "View", "FrameResult", "Server", "render_batch", "camera_struct", "sort_pairs", "VgrError",
            "load_library", "STORE_FP32",
            "STORE_HALF", "FILTER_PREEMPTIVE", "FILTER_CANONICAL", "EXP_EXACT", "EXP_LUT", "STAGES"]
 
@@ -290,6 +290,41 @@ def render_batch(views, cams, taus, host_outs=None):
     frs = (_abi.Frame * n)()
     _abi.check(_abi.load().vgr_render_batch(hv, cs, ts, hp, n, frs))
     return [FrameResult(frs[i]) for i in range(n)]
+
+
+class Renderer:
+    """One scene and one view in a single object: ``vgr_load_hierarchy``,
+    then ``vgr_create_view`` with the given view options (the keyword
+    arguments of :class:`View`), then ``vgr_render_frame`` per call.  Frames
+    rendered in sequence reuse the previous cut (the temporal update)."""
+
+    def __init__(self, scene: dict, storage: int = STORE_FP32, **view_opts):
+        self.hierarchy = Hierarchy(scene, storage)
+        try:
+            self.view = View(self.hierarchy, **view_opts)
+        except BaseException:
+            self.hierarchy.close()
+            raise
+
+    def render(self, cam: dict, tau: float) -> FrameResult:
+        return self.view.render(cam, tau)
+
+    def render_host(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
+        return self.view.render_host(cam, tau, out)
+
+    def reset(self):
+        self.view.reset()
+
+    def close(self):
+        self.view.close()
+        self.hierarchy.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 class Server:

@@ -128,3 +128,14 @@ def test_async_and_server_argument_errors(lib):
     assert lib.vgr_create_server(None, ctypes.byref(o), ctypes.byref(s)) == _abi.VGR_E_INVALID
     assert lib.vgr_destroy_server(None) == _abi.VGR_E_INVALID
     assert lib.vgr_serve_trace(None, None, 0, None) == _abi.VGR_E_INVALID
+
+
+def test_renderer_fails_loudly_without_a_gpu(tiny_scene):
+    """No CPU fallback: on a machine without a CUDA device the library
+    validates the scene, then reports the missing device as an error."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_2506_02774_gb300 as vgr
+    with pytest.raises(vgr.VgrError):
+        vgr.Renderer(tiny_scene)

@@ -65,3 +65,15 @@ def test_graph_growth_fallback_and_resize(small_sh3_scene):
             np.testing.assert_array_equal(a.cut().cpu().numpy().view(np.uint32), ref["cut"])
             check_image(a.image().cpu().numpy(), ref)
     vg.close(); vp.close(); h.close()
+
+
+def test_renderer_equals_hierarchy_and_view(tiny_scene):
+    tau = scenegen.CONFIGS["tiny"]["tau"]
+    h = vgr.Hierarchy(tiny_scene)
+    v = vgr.View(h, use_graph=True)
+    with vgr.Renderer(tiny_scene, use_graph=True) as r:
+        for fr in range(4):
+            cam = scenegen.trajectory("tiny", fr)
+            _same(r.render(cam, tau), v.render(cam, tau))
+    v.close()
+    h.close()
