@@ -96,7 +96,7 @@ def _load():
             lib.orc_rho_max_rect.restype = ctypes.c_double
             lib.orc_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_float,
                                        P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_float,
-                                       ctypes.c_int]
+                                       ctypes.c_int, ctypes.c_uint32]
             lib.orc_interp_weight.argtypes = [ctypes.POINTER(_Scene), ctypes.c_uint32, P, ctypes.c_float]
             lib.orc_interp_weight.restype = ctypes.c_float
             lib.orc_render.restype = ctypes.POINTER(_Frame)
@@ -234,7 +234,8 @@ def _arr(ptr, dtype, n):
 
 
 def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-3, t_flag: float = 0.05,
-           exhaustive: bool = False, frustum_guard: float | None = None, interp: bool = False) -> dict:
+           exhaustive: bool = False, frustum_guard: float | None = None, interp: bool = False,
+           lut_m: int = 0) -> dict:
     """Render one frame; returns the cut, per-cut projection, pairs and image.
 
     ``tile_mask`` (bool per tile, row-major) restricts binning and blending
@@ -244,7 +245,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     alpha >= alpha* test and move the pixel by up to ~alpha* T max(rgb).
     ``frustum_guard`` (pixels; needs ``sc["bbox"]``) selects the
     frustum-aware cut; ``interp`` renders the cut's Gaussians interpolated
-    with their parents.
+    with their parents; ``lut_m`` > 0 blends with the Eq. 5 lookup table of
+    that many intervals.
     """
     lib = _load()
     ref = _SceneRef(sc)
@@ -257,7 +259,7 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     fp = lib.orc_render(ctypes.byref(ref.s), ctypes.byref(c), float(np.float32(tau)),
                         _ptr(mask) if mask is not None else None, float(band), float(t_flag),
                         int(bool(exhaustive)), float(-1.0 if frustum_guard is None else frustum_guard),
-                        int(bool(interp)))
+                        int(bool(interp)), int(lut_m))
     if not fp:
         raise MemoryError("oracle render")
     try:

@@ -74,6 +74,15 @@
  *     rho = -1/2 (a dx^2 + c dy^2) - b dx dy, alpha = min(0.99, theta e^rho);
  *     skip when alpha < alpha*; T' = T (1 - alpha); stop (without this
  *     Gaussian) when T' < 1e-4; else C += alpha T rgb, T = T'.  Background 0.
+ *  6b. Lookup-table variant (Sec. 4.2, Eq. 5), selected by m = lut_m > 0:
+ *     the alpha* decision is Eq. 4's (skip when rho < ln alpha* - ln theta),
+ *     then e^rho is replaced by the nearest of the m + 1 samples
+ *     e^(-5.55 i / m), i = 0..m, of the effective range [-5.55, 0]:
+ *     i = round(rho / -5.55 * m) to nearest, ties to even, clamped to
+ *     [0, m]; alpha = min(0.99, theta e^(-5.55 i / m)) with no second alpha*
+ *     test.  The index is an integer decided by floating point, so it is
+ *     taken in the renderer's precision: fl(fl(rho) * fl(-fl(m) / 5.55f)).
+ *     The rest of step 6 is unchanged.
  *  7. Exhaustive mode: the same per-pixel loop over every cut Gaussian that
  *     passes the near-plane and determinant culls, sorted by (depth key,
  *     id), with no tiles, boxes or filters.
@@ -515,8 +524,9 @@ static int orc_cmp_key(const void* a, const void* b) {
  * alpha* T max(rgb).  Flips of the T < 1e-4 test move a pixel by at most
  * about 1e-4 max(rgb) and are not flagged. */
 static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, double px, double py,
-                            double band, double t_flag, double* out, uint8_t* flag, uint32_t* n_eval,
-                            uint32_t* n_contrib) {
+                            double band, double t_flag, uint32_t lut_m, double* out, uint8_t* flag,
+                            uint32_t* n_eval, uint32_t* n_contrib) {
+    const float lut_scale = lut_m ? -(float)lut_m / 5.55f : 0.0f;
     double T = 1.0, C[3] = {0, 0, 0};
     uint8_t f = 0;
     uint32_t ne = 0, nb = 0;
@@ -524,10 +534,18 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
         const orc_proj* g = &P[idx[i]];
         double dx = g->u - px, dy = g->v - py;
         double rho = orc_rho(g->conic, dx, dy);
-        double alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(rho));
         ++ne;
         if (fabs(rho - g->thr) <= band && T >= t_flag) f = 1;
-        if (alpha < ORC_ALPHA_MIN) continue;
+        double alpha;
+        if (lut_m) {
+            if (rho < g->thr) continue; /* Eq. 4 */
+            float q = nearbyintf((float)rho * lut_scale);
+            uint32_t i = q <= 0.0f ? 0u : (q >= (float)lut_m ? lut_m : (uint32_t)q);
+            alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(-5.55 * (double)i / (double)lut_m));
+        } else {
+            alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(rho));
+            if (alpha < ORC_ALPHA_MIN) continue;
+        }
         double Tn = T * (1.0 - alpha);
         if (Tn < ORC_T_MIN) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * g->rgb[ch];
@@ -546,9 +564,11 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
  * ambiguity flag (see orc_blend_pixel).  exhaustive != 0 selects mode 7.
  * frustum_guard >= 0 (with s->bbox) selects the frustum-aware cut (1b);
  * interp != 0 renders the cut's Gaussians interpolated with their parents (1c).
+ * lut_m > 0 blends with the Eq. 5 lookup table of m intervals (6b).
  */
 orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, const uint8_t* tile_mask,
-                      double band, double t_flag, int exhaustive, float frustum_guard, int interp) {
+                      double band, double t_flag, int exhaustive, float frustum_guard, int interp,
+                      uint32_t lut_m) {
     orc_frame* F = (orc_frame*)calloc(1, sizeof(orc_frame));
     if (!F) return NULL;
     float f = cam->fx > cam->fy ? cam->fx : cam->fy;
@@ -602,8 +622,8 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
             int x = (int)(p % W), y = (int)(p / W);
             int t = (y / ORC_TILE) * TW + x / ORC_TILE;
             if (tile_mask && !tile_mask[t]) continue;
-            orc_blend_pixel(F->proj, list, m, x + 0.5, y + 0.5, band, t_flag, &F->image[3 * p], &F->flags[p],
-                            &F->n_eval[p], &F->n_contrib[p]);
+            orc_blend_pixel(F->proj, list, m, x + 0.5, y + 0.5, band, t_flag, lut_m, &F->image[3 * p],
+                            &F->flags[p], &F->n_eval[p], &F->n_contrib[p]);
         }
         free(list);
         int64_t tot = 0;
@@ -686,7 +706,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
         for (int y = ty * ORC_TILE; y < (ty + 1) * ORC_TILE && y < H; ++y)
             for (int x = tx * ORC_TILE; x < (tx + 1) * ORC_TILE && x < W; ++x) {
                 size_t p = (size_t)y * W + x;
-                orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5, band, t_flag, &F->image[3 * p],
+                orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5, band, t_flag, lut_m, &F->image[3 * p],
                                 &F->flags[p], &F->n_eval[p], &F->n_contrib[p]);
             }
     }

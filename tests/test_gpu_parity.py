@@ -235,14 +235,25 @@ def test_half_storage_error(small_sh3_scene):
 
 
 def test_lut_mode_error(small_sh3_scene):
-    """Eq. 5 lookup table (m = 32): error against the exact oracle, reported."""
+    """Eq. 5 lookup table (m = 8, 32, 128): the error against the exact
+    oracle, and the agreement with the oracle's own table mode, which takes
+    the same table index wherever the FP32 rho does not sit on an index
+    boundary.  A table index flip moves a pixel by up to e^(5.55/m) - 1 of a
+    contribution, so agreement is judged by PSNR: at least 50 dB, and 6 dB
+    above the agreement with the exact oracle.  (On the CPU, the table-mode
+    oracle of this scene with every covariance entry perturbed by 1e-3,
+    10^4 times the FP32 rounding, still meets both: 53 / 59 / 65 dB against
+    31.6 / 43.7 / 55.8 dB.)"""
     h = vgr.Hierarchy(small_sh3_scene)
     cam = scenegen.camera((2.0, 15.0, 3.0), 0.2, 328, 250, 260.0)
     ref = oracle.render(small_sh3_scene, cam, 3.0)
     for m in (8, 32, 128):
         v = vgr.View(h, exp_mode=vgr.EXP_LUT, lut_size=m)
-        r = image_report(_img(v.render(cam, 3.0)), ref)
-        print("LUT m=%d:" % m, r)
+        img = _img(v.render(cam, 3.0))
+        r = image_report(img, ref)
+        rl = image_report(img, oracle.render(small_sh3_scene, cam, 3.0, lut_m=m))
+        print("LUT m=%d: vs exact oracle %s; vs table-mode oracle %s" % (m, r, rl))
         assert r["psnr"] > 20.0
+        assert rl["psnr"] >= max(50.0, r["psnr"] + 6.0), (m, r, rl)
         v.close()
     h.close()
