@@ -39,3 +39,16 @@ def test_traffic_record_only_for_the_code_it_was_taken_on(tmp_path, monkeypatch)
     assert bench._traffic("k_blend", "k_blend.cu", 1.0) is None
     assert bench._traffic("k_emit", "k_emit.cu", 1.0) is None
 
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread(tiny_scene):
+    import oracle
+    import scenegen
+    n = oracle.num_threads()
+    cams = [scenegen.trajectory("tiny", f) for f in range(3)]
+    r = bench.cpu_baseline(tiny_scene, cams, 3.0, budget_s=0.05)
+    assert r["kind"] == "oracle" and r["unit"] == "frames/s" and r["cores"] == n and r["value"] > 0
+    st = r["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and st["unit"] == "frames/s"
+    assert oracle.num_threads() == n  # the thread count is restored
+    assert "single_thread" not in bench.cpu_baseline(tiny_scene, cams, 3.0, budget_s=0.05, single_thread=False)
