@@ -181,6 +181,18 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
     )
 
 
+def frame_roofline(fb: dict, stage_ms: dict, frame_ms: float, hbm_gbs: float) -> dict:
+    """HBM roofline of the whole frame: the algorithmic bytes of every stage
+    at the measured copy bandwidth, as a share of the measured frame time,
+    and each stage's achieved bandwidth as a share of that peak."""
+    total = float(sum(fb.values()))
+    roof_ms = total / (hbm_gbs * 1e9) * 1e3
+    per_stage = {k: round(fb[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm_gbs, 4)
+                 for k in fb if stage_ms.get(k, 0.0) > 0}
+    return dict(algorithmic_bytes=int(total), hbm_roofline_ms=round(roof_ms, 4), frame_ms=round(frame_ms, 4),
+                frac=round(roof_ms / frame_ms, 4), stage_frac=per_stage)
+
+
 def run_ours(args) -> dict:
     import torch
 
@@ -465,6 +477,7 @@ def run_ours(args) -> dict:
                                      p99=round(1e3 * float(np.percentile(lat, 99)), 4)),
                stage_ms={k: round(v, 4) for k, v in shares.items()},
                stage_gbs={k: round(v, 1) for k, v in hbm_stages.items()},
+               frame_hbm=frame_roofline(fb, shares, ms / args.steps, peaks["hbm_gbs"]),
                counts={k: round(v, 1) for k, v in mean.items()},
                lod_reuse=lod_reuse,
                half_store=half_store,

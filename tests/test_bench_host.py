@@ -52,3 +52,13 @@ def test_cpu_baseline_reports_all_cores_and_one_thread(tiny_scene):
     assert st["cores"] == 1 and st["value"] > 0 and st["unit"] == "frames/s"
     assert oracle.num_threads() == n  # the thread count is restored
     assert "single_thread" not in bench.cpu_baseline(tiny_scene, cams, 3.0, budget_s=0.05, single_thread=False)
+
+
+def test_frame_roofline_arithmetic():
+    fb = {"lod": 2e8, "blend": 6e8, "emit": 2e8}
+    ms = {"lod": 0.1, "blend": 0.3, "emit": 0.0}
+    r = bench.frame_roofline(fb, ms, 1.0, 8000.0)
+    assert r["algorithmic_bytes"] == 10 ** 9
+    assert r["hbm_roofline_ms"] == 0.125            # 1 GB at 8 TB/s
+    assert r["frac"] == 0.125                       # of a 1 ms frame
+    assert r["stage_frac"] == {"lod": 0.25, "blend": 0.25}  # 2 GB/ms = 2 TB/s of 8; emit untimed
