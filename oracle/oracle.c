@@ -593,7 +593,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
     const int TW = (W + ORC_TILE - 1) / ORC_TILE, TH = (H + ORC_TILE - 1) / ORC_TILE;
     F->n_tiles = (int64_t)TW * TH;
     size_t npx = (size_t)W * H;
-    F->image = (double*)calloc(npx * 3 ? npx * 3 : 1, sizeof(double));
+    F->image = (double*)calloc(npx ? npx * 3 : 1, sizeof(double));
     F->flags = (uint8_t*)calloc(npx ? npx : 1, 1);
     F->n_eval = (uint32_t*)calloc(npx ? npx : 1, sizeof(uint32_t));
     F->n_contrib = (uint32_t*)calloc(npx ? npx : 1, sizeof(uint32_t));
