@@ -26,8 +26,21 @@ def load_library(build: bool = True):
     return _abi.load(build)
 
 
+def _require(ok: bool, msg: str, exc=ValueError):
+    """Argument check that survives python -O (unlike assert)."""
+    if not ok:
+        raise exc(msg)
+
+
+def _host_image_ok(a, cam, what: str):
+    _require(isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"],
+             "%s must be a C-contiguous float32 numpy array" % what, TypeError)
+    _require(a.shape == (int(cam["height"]), int(cam["width"]), 3),
+             "%s has shape %s, the camera needs (%d, %d, 3)" % (what, a.shape, int(cam["height"]), int(cam["width"])))
+
+
 def _ptr(a: np.ndarray):
-    assert a.flags["C_CONTIGUOUS"]
+    _require(a.flags["C_CONTIGUOUS"], "array must be C-contiguous")
     return ctypes.c_void_p(a.ctypes.data)
 
 
@@ -69,8 +82,10 @@ def sort_pairs(keys, vals, key_bits: int = 32, stream=None):
     """Stable radix sort of int32 CUDA tensors (u32 bit patterns) via
     vgr_sort_pairs; returns new (keys, values) tensors."""
     import torch
-    assert keys.is_cuda and vals.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32
-    assert keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel()
+    _require(keys.is_cuda and vals.is_cuda and keys.dtype == torch.int32 and vals.dtype == torch.int32,
+             "keys and values must be int32 CUDA tensors", TypeError)
+    _require(keys.is_contiguous() and vals.is_contiguous() and keys.numel() == vals.numel(),
+             "keys and values must be contiguous and of equal length")
     ko, vo = torch.empty_like(keys), torch.empty_like(vals)
     s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
     _abi.check(_abi.load().vgr_sort_pairs(keys.data_ptr(), vals.data_ptr(), ko.data_ptr(), vo.data_ptr(),
@@ -86,13 +101,14 @@ class Hierarchy:
         self._keep = [np.ascontiguousarray(scene[k]) for k in
                       ("parent", "first_child", "n_child", "mean", "cov6", "opacity", "sh", "radius2")]
         a = self._keep
-        assert a[0].dtype == np.uint32 and a[1].dtype == np.uint32 and a[2].dtype == np.uint8
-        for x in a[3:]:
-            assert x.dtype == np.float32
+        _require(a[0].dtype == np.uint32 and a[1].dtype == np.uint32 and a[2].dtype == np.uint8,
+                 "parent and first_child must be uint32, n_child uint8", TypeError)
+        for name, x in zip(("mean", "cov6", "opacity", "sh", "radius2"), a[3:]):
+            _require(x.dtype == np.float32, "%s must be float32" % name, TypeError)
         box = scene.get("bbox")
         if box is not None:
             box = np.ascontiguousarray(box, np.float32)
-            assert box.shape == (int(scene["n_nodes"]), 6)
+            _require(box.shape == (int(scene["n_nodes"]), 6), "bbox must have shape (n_nodes, 6)")
             self._keep.append(box)
         d = _abi.SceneDesc(int(scene["n_nodes"]), int(scene["sh_degree"]), *[_ptr(x) for x in a[:8]], int(storage),
                            _ptr(box) if box is not None else None)
@@ -181,8 +197,7 @@ class View:
 
     def render_host(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
         """Render and copy the image into the float32 H x W x 3 host array ``out``."""
-        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
-        assert out.shape == (int(cam["height"]), int(cam["width"]), 3)
+        _host_image_ok(out, cam, "out")
         fr = _abi.Frame()
         c = camera_struct(cam)
         _abi.check(_abi.load().vgr_render_frame_host(self.handle, ctypes.byref(c), float(tau),
@@ -200,8 +215,7 @@ class View:
         c = camera_struct(cam)
         ptr = None
         if host_out is not None:
-            assert host_out.dtype == np.float32 and host_out.flags["C_CONTIGUOUS"]
-            assert host_out.shape == (int(cam["height"]), int(cam["width"]), 3)
+            _host_image_ok(host_out, cam, "host_out")
             ptr = ctypes.c_void_p(host_out.ctypes.data)
         self._pending_host = host_out
         _abi.check(_abi.load().vgr_submit_frame(self.handle, ctypes.byref(c), float(tau), ptr))
@@ -274,7 +288,7 @@ def render_batch(views, cams, taus, host_outs=None):
     """One frame on each of several distinct views (``vgr_render_batch``):
     all submitted, then all finished.  Returns one FrameResult per view."""
     n = len(views)
-    assert len(cams) == n and len(taus) == n
+    _require(len(cams) == n and len(taus) == n, "views, cams and taus must have the same length")
     if n == 0:
         return []
     hv = (ctypes.c_void_p * n)(*[v.handle.value for v in views])
@@ -284,8 +298,7 @@ def render_batch(views, cams, taus, host_outs=None):
     if host_outs is not None:
         for a, c in zip(host_outs, cams):
             if a is not None:
-                assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
-                assert a.shape == (int(c["height"]), int(c["width"]), 3)
+                _host_image_ok(a, c, "host_outs[i]")
         hp = (ctypes.c_void_p * n)(*[(a.ctypes.data if a is not None else None) for a in host_outs])
     frs = (_abi.Frame * n)()
     _abi.check(_abi.load().vgr_render_batch(hv, cs, ts, hp, n, frs))

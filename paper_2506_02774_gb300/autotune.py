@@ -66,7 +66,8 @@ def tune(hier, cams, tau: float, *, cache_path: str | None = None, warmup: int =
     Returns {"grid_wide", "grid_scan", "ms", "default_ms", "candidates"}."""
     import torch
     W, H = int(cams[0]["width"]), int(cams[0]["height"])
-    assert all(int(c["width"]) == W and int(c["height"]) == H for c in cams)
+    if not all(int(c["width"]) == W and int(c["height"]) == H for c in cams):
+        raise ValueError("every camera of a tuning walk must have the same image size")
     key = cache_key(hier, W, H)
     cache = load_cache(cache_path)
     if key in cache and not force:

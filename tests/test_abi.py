@@ -139,3 +139,29 @@ def test_renderer_fails_loudly_without_a_gpu(tiny_scene):
     import paper_2506_02774_gb300 as vgr
     with pytest.raises(vgr.VgrError):
         vgr.Renderer(tiny_scene)
+
+
+def test_binding_argument_checks_survive_optimised_python(tiny_scene):
+    """The binding's own checks raise real exceptions (not asserts, which
+    python -O removes) before anything reaches the library."""
+    import paper_2506_02774_gb300 as vgr
+    bad = dict(tiny_scene)
+    bad["parent"] = tiny_scene["parent"].astype(np.int64)
+    with pytest.raises(TypeError, match="uint32"):
+        vgr.Hierarchy(bad)
+    bad = dict(tiny_scene)
+    bad["opacity"] = tiny_scene["opacity"].astype(np.float64)
+    with pytest.raises(TypeError, match="opacity"):
+        vgr.Hierarchy(bad)
+    bad = dict(tiny_scene)
+    bad["bbox"] = tiny_scene["bbox"][:-1]
+    with pytest.raises(ValueError, match="bbox"):
+        vgr.Hierarchy(bad)
+    cam = scenegen.trajectory("tiny", 0)
+    with pytest.raises(ValueError, match="same length"):
+        vgr.render_batch([object()], [cam, cam], [3.0])
+    with pytest.raises(TypeError, match="float32"):
+        vgr._host_image_ok(np.zeros((128, 128, 3)), cam, "out")
+    with pytest.raises(ValueError, match="shape"):
+        vgr._host_image_ok(np.zeros((64, 128, 3), np.float32), cam, "out")
+    vgr._host_image_ok(np.zeros((128, 128, 3), np.float32), cam, "out")
