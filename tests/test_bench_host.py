@@ -1,9 +1,12 @@
 """Host-side helpers of bench.py (CPU): the code hash that keys the committed
-DRAM-traffic record, and the rule that a record taken on other code is not
-reported."""
+DRAM-traffic record, the rule that a record taken on other code is not
+reported, the CPU baseline's two timings, the whole-frame roofline
+arithmetic and the serving leg's request trace."""
 import json
 import os
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -62,3 +65,28 @@ def test_frame_roofline_arithmetic():
     assert r["hbm_roofline_ms"] == 0.125            # 1 GB at 8 TB/s
     assert r["frac"] == 0.125                       # of a 1 ms frame
     assert r["stage_frac"] == {"lod": 0.25, "blend": 0.25}  # 2 GB/ms = 2 TB/s of 8; emit untimed
+
+
+def test_serving_trace_is_the_poisson_recipe():
+    """32 clients at 8 req/s each for 10 s: arrivals sorted inside the window,
+    about 2560 requests in all (Poisson, 3 sigma), each client's requests
+    walking consecutive frames of its own street at its own image size, and
+    the same trace for the same seed."""
+    import scenegen
+    names = ["720p", "1080p", "1440p"]
+    pick = [names[i % 3] for i in range(32)]
+    tr = bench._serve_trace(32, 8.0, 10.0, 5, pick, 2)
+    t = np.array([r["arrival_s"] for r in tr])
+    assert np.all(np.diff(t) >= 0) and t[0] > 0 and t[-1] <= 10.0
+    assert abs(len(tr) - 2560) <= 3 * np.sqrt(2560)
+    for c in (0, 7, 31):
+        mine = [r for r in tr if r["client"] == c]
+        W, H = scenegen.RESOLUTIONS[pick[c]]
+        assert all(r["cam"]["width"] == W and r["cam"]["height"] == H for r in mine)
+        ref = [scenegen.street_trajectory("city", 300 + c, 2 + k, W, H)["pos"] for k in range(len(mine))]
+        np.testing.assert_array_equal(np.array([r["cam"]["pos"] for r in mine]), np.array(ref))
+    # gaps are exponential with mean 1/8 s (mean within 5 %)
+    gaps = np.concatenate([np.diff([0.0] + [r["arrival_s"] for r in tr if r["client"] == c]) for c in range(32)])
+    assert abs(gaps.mean() - 0.125) < 0.00625
+    tr2 = bench._serve_trace(32, 8.0, 10.0, 5, pick, 2)
+    assert [r["arrival_s"] for r in tr2] == list(t)
