@@ -76,3 +76,14 @@ def test_table_alpha_is_capped():
     lt = oracle.render(_one(theta=1.0), _cam(), 0.0, lut_m=32)
     rgb = 0.5 + C0 * np.float64(np.float32(1.0))
     assert lt["image"][40, 48, 0] == pytest.approx(0.99 * rgb, rel=1e-12)
+
+
+def test_tiled_equals_exhaustive_with_the_table(tiny_scene):
+    """Eq. 4 still decides which pixels a Gaussian reaches, so the tile filter
+    stays exact under the table: binned and exhaustive images are equal."""
+    for fr in (0, 9):
+        cam = scenegen.trajectory("tiny", fr)
+        a = oracle.render(tiny_scene, cam, 3.0, lut_m=32)
+        b = oracle.render(tiny_scene, cam, 3.0, lut_m=32, exhaustive=True)
+        assert np.array_equal(a["image"], b["image"])
+        assert a["image"].max() > 0.05
