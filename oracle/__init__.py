@@ -6,7 +6,9 @@ two meet only in the seeded inputs of ``scenegen``.
 
 ``oracle.c`` holds the arithmetic (each step cites the paper section it
 follows); this module compiles it with gcc on first use and returns numpy
-arrays.
+arrays.  The environment variable ``ORACLE_LIB`` names another build of
+``oracle.c`` to load instead (the planted-mistake test loads mutated copies
+this way).
 """
 from __future__ import annotations
 
@@ -77,7 +79,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
             P = ctypes.c_void_p
             lib.orc_lod_k.argtypes = [ctypes.c_float, ctypes.c_float]
             lib.orc_lod_k.restype = ctypes.c_float
