@@ -19,7 +19,7 @@ FRUSTUM, INTERP, LUT = "tests/test_oracle_frustum.py", "tests/test_oracle_interp
 MUTANTS = [
     ("granularity k = t, not t^2", CUT, "    return t * t;\n}", "    return t;\n}"),
     ("granularity boundary <=", CUT, "if (!(lhs < s->radius2[n])) return 0;", "if (!(lhs <= s->radius2[n])) return 0;"),
-    ("Jacobian sign", BLEND, "-fx * tx / z, 0.0", "fx * tx / z, 0.0"),
+    ("Jacobian sign", PROJ, "-fx * tx / z, 0.0", "fx * tx / z, 0.0"),
     ("conic off-diagonal sign", PROJ, "P->conic[1] = -s01 / det;", "P->conic[1] = s01 / det;"),
     ("no dilation", PROJ, "double s00 = C2[0] + ORC_DILATE, s01 = 0.5 * (C2[1] + C2[2]), s11 = C2[3] + ORC_DILATE;",
      "double s00 = C2[0], s01 = 0.5 * (C2[1] + C2[2]), s11 = C2[3];"),

@@ -207,3 +207,17 @@ def test_sh_view_direction_is_camera_to_mean():
     q = oracle.render(sc, cam, 0.0)["proj"][0]
     assert q["valid"] == 1
     np.testing.assert_allclose(q["rgb"], [0.5 - 0.8 * c1, 0.5 + 0.6 * c1, 0.5], rtol=1e-12)
+
+
+def test_off_axis_xz_covariance_closed_form():
+    """Mean at camera-space (x, 0, z) with an x-z covariance term: with t = x/z,
+    Sigma'_00 = f^2/z^2 (Sxx - 2 t Sxz + t^2 Szz) + 0.3 (the sign of J's
+    third column decides the middle term), Sigma'_11 = f^2/z^2 Syy + 0.3 and
+    Sigma'_01 = 0."""
+    f, x, z = 100.0, 0.5, 2.0
+    Sxx, Syy, Sxz, Szz = (float(np.float32(v)) for v in (0.04, 0.03, 0.01, 0.02))
+    p = oracle.render(_one((x, 0.0, z), [Sxx, 0.0, Sxz, Syy, 0.0, Szz]), _cam(f=f), 0.0)["proj"][0]
+    t = x / z
+    k = f * f / (z * z)
+    np.testing.assert_allclose(p["cov"], [k * (Sxx - 2 * t * Sxz + t * t * Szz) + 0.3, 0.0, k * Syy + 0.3],
+                               rtol=1e-12, atol=1e-12)
