@@ -2,6 +2,7 @@
 every function include/vgr.h declares, and rejects malformed hierarchies and
 arguments before touching the GPU."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -165,3 +166,24 @@ def test_binding_argument_checks_survive_optimised_python(tiny_scene):
     with pytest.raises(ValueError, match="shape"):
         vgr._host_image_ok(np.zeros((64, 128, 3), np.float32), cam, "out")
     vgr._host_image_ok(np.zeros((128, 128, 3), np.float32), cam, "out")
+
+
+def test_ctypes_prototypes_match_header_arity():
+    """Every function the binding declares to ctypes has the header's number
+    of parameters and a matching return kind (status, void or string)."""
+    import re
+    from paper_2506_02774_gb300 import _build
+    src = open(os.path.join(_build.INCLUDE, "vgr.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"(vgr_status|void|const char\s*\*)\s*(vgr_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        protos[name] = (ret.replace(" ", ""), n)
+    assert len(protos) >= 20
+    for name, (res, args) in _abi._PROTOS.items():
+        assert name in protos, name
+        ret, n = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        want = {"vgr_status": ctypes.c_int32, "void": None, "constchar*": ctypes.c_char_p}[ret]
+        assert res is want, (name, res, ret)
