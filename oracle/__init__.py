@@ -250,6 +250,8 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     with their parents; ``lut_m`` > 0 blends with the Eq. 5 lookup table of
     that many intervals.
     """
+    if int(lut_m) < 0:
+        raise ValueError("lut_m must be >= 0")
     lib = _load()
     ref = _SceneRef(sc)
     c = _camera(cam)
