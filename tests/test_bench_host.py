@@ -90,3 +90,23 @@ def test_serving_trace_is_the_poisson_recipe():
     assert abs(gaps.mean() - 0.125) < 0.00625
     tr2 = bench._serve_trace(32, 8.0, 10.0, 5, pick, 2)
     assert [r["arrival_s"] for r in tr2] == list(t)
+
+
+def test_autotune_cache_is_reused_and_sizes_must_agree(tmp_path, monkeypatch):
+    """A cached launch geometry is returned without timing anything; a
+    tuning walk of mixed image sizes is refused."""
+    import pytest
+    from paper_2506_02774_gb300 import autotune
+    path = str(tmp_path / "geom.json")
+    entry = {"grid_wide": 1216, "grid_scan": 608, "ms": 1.0, "default_ms": 1.1, "candidates": []}
+    autotune.save_cache(path, {"dev|64x32": entry})
+    assert autotune.load_cache(path) == {"dev|64x32": entry}
+    assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
+    monkeypatch.setattr(autotune, "cache_key", lambda h, W, H: "dev|%dx%d" % (W, H))
+    timed = []
+    monkeypatch.setattr(autotune, "_time_walk", lambda *a, **k: timed.append(k) or 1.0)
+    cams = [dict(width=64, height=32)] * 3
+    assert autotune.tune(None, cams, 3.0, cache_path=path) == entry
+    assert not timed
+    with pytest.raises(ValueError, match="same image size"):
+        autotune.tune(None, [dict(width=64, height=32), dict(width=32, height=32)], 3.0, cache_path=path)
