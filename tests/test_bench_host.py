@@ -1,7 +1,7 @@
 """Host-side helpers of bench.py (CPU): the code hash that keys the committed
 DRAM-traffic record, the rule that a record taken on other code is not
 reported, the CPU baseline's two timings, the whole-frame roofline
-arithmetic and the serving leg's request trace."""
+arithmetic, the serving leg's request trace and the autotuner's cache."""
 import json
 import os
 import sys
