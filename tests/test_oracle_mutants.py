@@ -45,6 +45,54 @@ MUTANTS = [
     ("table index floored", LUT, "float q = nearbyintf((float)rho * lut_scale);",
      "float q = floorf((float)rho * lut_scale);"),
     ("table without Eq. 4 first", LUT, "            if (rho < g->thr) continue; /* Eq. 4 */\n", ""),
+    ('distance without its z term', CUT, 'float d2 = (dx * dx + dy * dy) + dz * dz;\n    float lhs',
+     'float d2 = (dx * dx + dy * dy);\n    float lhs'),
+    ('Jacobian clamp at 1.0', PROJ, 'double limx = 1.3 * (0.5',
+     'double limx = 1.0 * (0.5'),
+    ('Jacobian not clamped', PROJ, 'double tx = fmin(limx, fmax(-limx, p[0] / z));',
+     'double tx = p[0] / z;'),
+    ('conic a and c swapped', PROJ, 'P->conic[0] = s11 / det;',
+     'P->conic[0] = s00 / det;'),
+    ('covariance rotated by R twice', PROJ, 'acc += RS[3 * r + k] * R[3 * c + k];',
+     'acc += RS[3 * r + k] * R[3 * k + c];'),
+    ('no principal point', PROJ, 'P->u = fx * p[0] / z + cam->cx;',
+     'P->u = fx * p[0] / z;'),
+    ('colour without +0.5', PROJ, '        acc += 0.5;\n',
+     ''),
+    ('colour not clamped at 0', PROJ, 'P->rgb[ch] = acc > 0.0 ? acc : 0.0;',
+     'P->rgb[ch] = acc;'),
+    ('SH sin for m > 0', PROJ, 'else if (m > 0) v = sqrt(2.0) * K * P * cos(m * phi);',
+     'else if (m > 0) v = sqrt(2.0) * K * P * sin(m * phi);'),
+    ('SH without sqrt 2', PROJ, 'else v = sqrt(2.0) * K * P * sin(am * phi);',
+     'else v = K * P * sin(am * phi);'),
+    ('no Condon-Shortley phase', PROJ, 'pmm *= -(2.0 * i - 1.0) * sx;',
+     'pmm *= (2.0 * i - 1.0) * sx;'),
+    ('depth key from a column of R', PROJ, 'float zk = (cam->R[6] * dxf + cam->R[7] * dyf) + cam->R[8] * dzf;',
+     'float zk = (cam->R[2] * dxf + cam->R[5] * dyf) + cam->R[8] * dzf;'),
+    ('threshold sign', BLEND, 'P->thr = log(ORC_ALPHA_MIN) - log(',
+     'P->thr = -log(ORC_ALPHA_MIN) + log('),
+    ('rho cross-term sign', BLEND, 'return -0.5 * (conic[0] * dx * dx + conic[2] * dy * dy) - conic[1] * dx * dy;',
+     'return -0.5 * (conic[0] * dx * dx + conic[2] * dy * dy) + conic[1] * dx * dy;'),
+    ('rho without 1/2', BLEND, 'return -0.5 * (conic[0]',
+     'return -1.0 * (conic[0]'),
+    ('tile rectangle not clipped to the image', BLEND, '*x1 = fmin(ORC_TILE * tx + ORC_TILE - 0.5, (double)cam->width - 0.5);',
+     '*x1 = ORC_TILE * tx + ORC_TILE - 0.5;'),
+    ('rho_max without the inside case', BLEND, 'if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.0;',
+     ''),
+    ('box radius without the factor 2', BLEND, 'double r2 = 2.0 * (log(P->theta)',
+     'double r2 = 1.0 * (log(P->theta)'),
+    ('box x extent from the y variance', BLEND, 'double bx = sqrt(r2 * P->cov[0])',
+     'double bx = sqrt(r2 * P->cov[2])'),
+    ('order without depth', BLEND, 'if (x->zkey != y->zkey) return x->zkey < y->zkey ? -1 : 1;',
+     ''),
+    ('back to front', BLEND, 'if (x->zkey != y->zkey) return x->zkey < y->zkey ? -1 : 1;',
+     'if (x->zkey != y->zkey) return x->zkey > y->zkey ? -1 : 1;'),
+    ('no alpha* skip', BLEND, '            if (alpha < ORC_ALPHA_MIN) continue;\n',
+     ''),
+    ('termination after adding', BLEND, '        if (Tn < ORC_T_MIN) break;\n        for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * g->rgb[ch];',
+     '        for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * g->rgb[ch];\n        if (Tn < ORC_T_MIN) break;'),
+    ('pixel corner, not centre', BLEND, 'orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5,',
+     'orc_blend_pixel(F->proj, list, n, x, y,'),
 ]
 
 
