@@ -93,6 +93,38 @@ MUTANTS = [
      '        for (int ch = 0; ch < 3; ++ch) C[ch] += alpha * T * g->rgb[ch];\n        if (Tn < ORC_T_MIN) break;'),
     ('pixel corner, not centre', BLEND, 'orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5,',
      'orc_blend_pixel(F->proj, list, n, x, y,'),
+    ('frustum normals from R, not R^T', FRUSTUM, 'double acc = (double)cam->R[0 * 3 + j] * a[i][0];\n            acc = fma((double)cam->R[1 * 3 + j], a[i][1], acc);\n            acc = fma((double)cam->R[2 * 3 + j], a[i][2], acc);',
+     'double acc = (double)cam->R[j * 3 + 0] * a[i][0];\n            acc = fma((double)cam->R[j * 3 + 1], a[i][1], acc);\n            acc = fma((double)cam->R[j * 3 + 2], a[i][2], acc);'),
+    ('right plane facing out', FRUSTUM, '{-(double)cam->fx, 0.0, (W - cam->cx) + g}',
+     '{(double)cam->fx, 0.0, (W - cam->cx) + g}'),
+    ('plane offset sign', FRUSTUM, 'planes[4 * i + 3] = (float)(o + oc[i]);',
+     'planes[4 * i + 3] = (float)(-o + oc[i]);'),
+    ('no near plane', FRUSTUM, 'double oc[5] = {cam->z_near, 0.0, 0.0, 0.0, 0.0};',
+     'double oc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};'),
+    ('bottom plane from cy, not H - cy', FRUSTUM, '{0.0, -(double)cam->fy, (H - cam->cy) + g}',
+     '{0.0, -(double)cam->fy, (double)cam->cy + g}'),
+    ('only the near plane tested', FRUSTUM, 'if (!(sd >= 0.0f)) return 0;',
+     'if (!(sd >= 0.0f) && i == 0) return 0;'),
+    ('size ratio without the square root', INTERP, 'return sqrtf(q);',
+     'return q;'),
+    ('node and parent swapped', INTERP, 'float an = orc_size_ratio(s, n, cam), ap = orc_size_ratio(s, p, cam);',
+     'float ap = orc_size_ratio(s, n, cam), an = orc_size_ratio(s, p, cam);'),
+    ('mean moved away from the parent', INTERP, 'mf[j] = mf[j] + wd;',
+     'mf[j] = mf[j] - wd;'),
+    ('SH not interpolated', INTERP, 'for (int j = 0; j < 3 * K; ++j) shn[j] += wd * ((double)s->sh[(size_t)p * K * 3 + j] - shn[j]);',
+     ''),
+    ('covariance not interpolated', INTERP, 'for (int j = 0; j < 6; ++j) c6[j] += wd * ((double)s->cov6[6 * (size_t)p + j] - c6[j]);',
+     ''),
+    ('table index rounded up', LUT, 'float q = nearbyintf((float)rho * lut_scale);',
+     'float q = ceilf((float)rho * lut_scale);'),
+    ('table scaled by ln 255, not 5.55', LUT, '-(float)lut_m / 5.55f',
+     '-(float)lut_m / 5.541f'),
+    ('table of m + 1 intervals', LUT, 'exp(-5.55 * (double)i / (double)lut_m)',
+     'exp(-5.55 * (double)i / (double)(lut_m + 1))'),
+    ('table with a second alpha* test', LUT, '            alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(-5.55 * (double)i / (double)lut_m));\n',
+     '            alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(-5.55 * (double)i / (double)lut_m));\n            if (alpha < ORC_ALPHA_MIN) continue;\n'),
+    ('table without the alpha cap', LUT, 'alpha = fmin(ORC_ALPHA_MAX, g->theta * exp(-5.55 * (double)i / (double)lut_m));',
+     'alpha = g->theta * exp(-5.55 * (double)i / (double)lut_m);'),
 ]
 
 
