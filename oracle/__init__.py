@@ -98,7 +98,7 @@ def _load():
             lib.orc_rho_max_rect.restype = ctypes.c_double
             lib.orc_render.argtypes = [ctypes.POINTER(_Scene), ctypes.POINTER(_Camera), ctypes.c_float,
                                        P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_float,
-                                       ctypes.c_int, ctypes.c_uint32]
+                                       ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32]
             lib.orc_interp_weight.argtypes = [ctypes.POINTER(_Scene), ctypes.c_uint32, P, ctypes.c_float]
             lib.orc_interp_weight.restype = ctypes.c_float
             lib.orc_render.restype = ctypes.POINTER(_Frame)
@@ -237,7 +237,7 @@ def _arr(ptr, dtype, n):
 
 def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-3, t_flag: float = 0.05,
            exhaustive: bool = False, frustum_guard: float | None = None, interp: bool = False,
-           lut_m: int = 0) -> dict:
+           lut_m: int = 0, tile: int = TILE) -> dict:
     """Render one frame; returns the cut, per-cut projection, pairs and image.
 
     ``tile_mask`` (bool per tile, row-major) restricts binning and blending
@@ -248,22 +248,25 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
     ``frustum_guard`` (pixels; needs ``sc["bbox"]``) selects the
     frustum-aware cut; ``interp`` renders the cut's Gaussians interpolated
     with their parents; ``lut_m`` > 0 blends with the Eq. 5 lookup table of
-    that many intervals.
+    that many intervals; ``tile`` is the side of a tile in pixels (binning,
+    pair lists and ``tile_mask`` are per tile of that size).
     """
     if int(lut_m) < 0:
         raise ValueError("lut_m must be >= 0")
+    if int(tile) < 1:
+        raise ValueError("tile must be >= 1")
     lib = _load()
     ref = _SceneRef(sc)
     c = _camera(cam)
     W, H = c.width, c.height
-    TW, TH = (W + TILE - 1) // TILE, (H + TILE - 1) // TILE
+    TW, TH = (W + tile - 1) // tile, (H + tile - 1) // tile
     mask = None
     if tile_mask is not None:
         mask = np.ascontiguousarray(np.asarray(tile_mask, bool).reshape(TW * TH).astype(np.uint8))
     fp = lib.orc_render(ctypes.byref(ref.s), ctypes.byref(c), float(np.float32(tau)),
                         _ptr(mask) if mask is not None else None, float(band), float(t_flag),
                         int(bool(exhaustive)), float(-1.0 if frustum_guard is None else frustum_guard),
-                        int(bool(interp)), int(lut_m))
+                        int(bool(interp)), int(lut_m), int(tile))
     if not fp:
         raise MemoryError("oracle render")
     try:
@@ -274,7 +277,7 @@ def render(sc: dict, cam: dict, tau: float, *, tile_mask=None, band: float = 2e-
                    flags=_arr(F.flags, np.uint8, W * H).reshape(H, W),
                    n_eval=_arr(F.n_eval, np.uint32, W * H).reshape(H, W),
                    n_contrib=_arr(F.n_contrib, np.uint32, W * H).reshape(H, W),
-                   n_eval_total=int(F.n_eval_total), n_tiles=int(F.n_tiles), tiles=(TW, TH))
+                   n_eval_total=int(F.n_eval_total), n_tiles=int(F.n_tiles), tiles=(TW, TH), tile=int(tile))
         if not exhaustive:
             ncand, np_ = int(F.n_cand), int(F.n_pairs)
             out.update(cand_tile=_arr(F.cand_tile, np.uint32, ncand),

@@ -118,7 +118,7 @@ typedef struct {
     float z_near;
 } orc_camera;
 
-#define ORC_TILE 16
+#define ORC_TILE 16  /* the default tile size (pixels per side) */
 static const double ORC_ALPHA_MIN = 1.0 / 255.0;
 static const double ORC_T_MIN = 1e-4;
 static const double ORC_ALPHA_MAX = 0.99;
@@ -442,27 +442,28 @@ double orc_rho_max_rect(const double conic[3], double u, double v, double x0, do
     return best;
 }
 
-static void orc_tile_rect(const orc_camera* cam, int tx, int ty, double* x0, double* x1, double* y0,
+/* pixel-centre rectangle of tile (tx, ty), tiles of tile x tile pixels */
+static void orc_tile_rect(const orc_camera* cam, int tile, int tx, int ty, double* x0, double* x1, double* y0,
                           double* y1) {
-    *x0 = ORC_TILE * tx + 0.5;
-    *x1 = fmin(ORC_TILE * tx + ORC_TILE - 0.5, (double)cam->width - 0.5);
-    *y0 = ORC_TILE * ty + 0.5;
-    *y1 = fmin(ORC_TILE * ty + ORC_TILE - 0.5, (double)cam->height - 0.5);
+    *x0 = tile * tx + 0.5;
+    *x1 = fmin(tile * tx + tile - 0.5, (double)cam->width - 0.5);
+    *y0 = tile * ty + 0.5;
+    *y1 = fmin(tile * ty + tile - 0.5, (double)cam->height - 0.5);
 }
 
 /* candidate tile rectangle from the opacity-aware bounding box */
-static void orc_candidates(const orc_camera* cam, orc_proj* P) {
+static void orc_candidates(const orc_camera* cam, int tile, orc_proj* P) {
     P->rect[0] = 0; P->rect[1] = 0; P->rect[2] = -1; P->rect[3] = -1;
     if (!P->valid) return;
     if (P->theta < ORC_ALPHA_MIN) return; /* Gaussian-level filter */
     double r2 = 2.0 * (log(P->theta) - log(ORC_ALPHA_MIN));
     if (r2 < 0.0) r2 = 0.0;
     double bx = sqrt(r2 * P->cov[0]), by = sqrt(r2 * P->cov[2]);
-    int TW = (int)((cam->width + ORC_TILE - 1) / ORC_TILE), TH = (int)((cam->height + ORC_TILE - 1) / ORC_TILE);
-    double fx0 = ceil((P->u - bx - (ORC_TILE - 0.5)) / ORC_TILE);
-    double fx1 = floor((P->u + bx - 0.5) / ORC_TILE);
-    double fy0 = ceil((P->v - by - (ORC_TILE - 0.5)) / ORC_TILE);
-    double fy1 = floor((P->v + by - 0.5) / ORC_TILE);
+    int TW = (int)((cam->width + tile - 1) / tile), TH = (int)((cam->height + tile - 1) / tile);
+    double fx0 = ceil((P->u - bx - (tile - 0.5)) / tile);
+    double fx1 = floor((P->u + bx - 0.5) / tile);
+    double fy0 = ceil((P->v - by - (tile - 0.5)) / tile);
+    double fy1 = floor((P->v + by - 0.5) / tile);
     fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
     fx1 = fmin(fx1, TW - 1.0); fy1 = fmin(fy1, TH - 1.0);
     if (fx0 > fx1 || fy0 > fy1) return;
@@ -565,10 +566,15 @@ static void orc_blend_pixel(const orc_proj* P, const uint32_t* idx, int64_t n, d
  * frustum_guard >= 0 (with s->bbox) selects the frustum-aware cut (1b);
  * interp != 0 renders the cut's Gaussians interpolated with their parents (1c).
  * lut_m > 0 blends with the Eq. 5 lookup table of m intervals (6b).
+ * tile: the side of a square tile in pixels (0: ORC_TILE); tile_mask and the
+ * pair lists are per tile of that size.  Binning is exact whatever the size
+ * (no pixel with alpha >= alpha* lies outside a kept pair), so the image does
+ * not depend on it.
  */
 orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, const uint8_t* tile_mask,
                       double band, double t_flag, int exhaustive, float frustum_guard, int interp,
-                      uint32_t lut_m) {
+                      uint32_t lut_m, uint32_t tile_px) {
+    const int tile = tile_px ? (int)tile_px : ORC_TILE;
     orc_frame* F = (orc_frame*)calloc(1, sizeof(orc_frame));
     if (!F) return NULL;
     float f = cam->fx > cam->fy ? cam->fx : cam->fy;
@@ -587,10 +593,10 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
 #pragma omp parallel for schedule(dynamic, 256)
     for (i = 0; i < nc; ++i) {
         orc_project_one(s, cam, F->cut[i], &F->proj[i], interp ? orc_lod_k_t(tau, f) : -1.0f);
-        orc_candidates(cam, &F->proj[i]);
+        orc_candidates(cam, tile, &F->proj[i]);
     }
     const int W = (int)cam->width, H = (int)cam->height;
-    const int TW = (W + ORC_TILE - 1) / ORC_TILE, TH = (H + ORC_TILE - 1) / ORC_TILE;
+    const int TW = (W + tile - 1) / tile, TH = (H + tile - 1) / tile;
     F->n_tiles = (int64_t)TW * TH;
     size_t npx = (size_t)W * H;
     F->image = (double*)calloc(npx ? npx * 3 : 1, sizeof(double));
@@ -620,7 +626,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
 #pragma omp parallel for schedule(dynamic, 64)
         for (p = 0; p < (int64_t)npx; ++p) {
             int x = (int)(p % W), y = (int)(p / W);
-            int t = (y / ORC_TILE) * TW + x / ORC_TILE;
+            int t = (y / tile) * TW + x / tile;
             if (tile_mask && !tile_mask[t]) continue;
             orc_blend_pixel(F->proj, list, m, x + 0.5, y + 0.5, band, t_flag, lut_m, &F->image[3 * p],
                             &F->flags[p], &F->n_eval[p], &F->n_contrib[p]);
@@ -660,7 +666,7 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
             for (int tx = P->rect[0]; tx <= P->rect[2]; ++tx) {
                 if (tile_mask && !tile_mask[ty * TW + tx]) continue;
                 double x0, x1, y0, y1;
-                orc_tile_rect(cam, tx, ty, &x0, &x1, &y0, &y1);
+                orc_tile_rect(cam, tile, tx, ty, &x0, &x1, &y0, &y1);
                 double rm = orc_rho_max_rect(P->conic, P->u, P->v, x0, x1, y0, y1);
                 F->cand_tile[o] = (uint32_t)(ty * TW + tx);
                 F->cand_idx[o] = (uint32_t)i;
@@ -703,8 +709,8 @@ orc_frame* orc_render(const orc_scene* s, const orc_camera* cam, float tau, cons
         int tx = (int)(t % TW), ty = (int)(t / TW);
         const uint32_t* list = F->pair_idx + F->tile_start[t];
         int64_t n = F->tile_start[t + 1] - F->tile_start[t];
-        for (int y = ty * ORC_TILE; y < (ty + 1) * ORC_TILE && y < H; ++y)
-            for (int x = tx * ORC_TILE; x < (tx + 1) * ORC_TILE && x < W; ++x) {
+        for (int y = ty * tile; y < (ty + 1) * tile && y < H; ++y)
+            for (int x = tx * tile; x < (tx + 1) * tile && x < W; ++x) {
                 size_t p = (size_t)y * W + x;
                 orc_blend_pixel(F->proj, list, n, x + 0.5, y + 0.5, band, t_flag, lut_m, &F->image[3 * p],
                                 &F->flags[p], &F->n_eval[p], &F->n_contrib[p]);

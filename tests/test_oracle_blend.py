@@ -49,21 +49,30 @@ def _dc_for(rgb):
     return [(c - 0.5) / C0 for c in rgb]
 
 
-def test_exhaustive_equals_tiled(tiny_scene):
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_exhaustive_equals_tiled(tiny_scene, tile):
     for fr in (0, 7, 15):
         cam = scenegen.trajectory("tiny", fr)
-        a = oracle.render(tiny_scene, cam, 3.0)
+        a = oracle.render(tiny_scene, cam, 3.0, tile=tile)
         b = oracle.render(tiny_scene, cam, 3.0, exhaustive=True)
         assert np.array_equal(a["image"], b["image"])
         assert a["image"].max() > 0.05
+        assert a["tiles"] == ((128 + tile - 1) // tile,) * 2
 
 
-def test_exhaustive_equals_tiled_sh3(small_sh3_scene):
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_exhaustive_equals_tiled_sh3(small_sh3_scene, tile):
+    """Binning is exact at every tile size: the image is the exhaustive one
+    bit for bit; smaller tiles give more, tighter pairs."""
     cam = scenegen.camera((2.0, 15.0, 3.0), 0.2, 96, 80, 90.0)
-    a = oracle.render(small_sh3_scene, cam, 3.0)
+    a = oracle.render(small_sh3_scene, cam, 3.0, tile=tile)
     b = oracle.render(small_sh3_scene, cam, 3.0, exhaustive=True)
     assert np.array_equal(a["image"], b["image"])
     assert a["n_pairs"] > 1000
+    assert len(a["tile_start"]) == a["tiles"][0] * a["tiles"][1] + 1
+    if tile == 8:
+        c = oracle.render(small_sh3_scene, cam, 3.0, tile=16)
+        assert a["n_pairs"] > c["n_pairs"] and a["n_eval_total"] < c["n_eval_total"]
 
 
 def _alpha_at(p, x, y):
@@ -73,9 +82,10 @@ def _alpha_at(p, x, y):
     return np.minimum(0.99, p["theta"] * np.exp(rho)), rho
 
 
-def test_dropped_pairs_never_reach_alpha_min(tiny_scene):
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_dropped_pairs_never_reach_alpha_min(tiny_scene, tile):
     cam = scenegen.trajectory("tiny", 3)
-    r = oracle.render(tiny_scene, cam, 3.0)
+    r = oracle.render(tiny_scene, cam, 3.0, tile=tile)
     TW = r["tiles"][0]
     dropped = np.nonzero(r["cand_margin"] < 0)[0]
     assert len(dropped) > 10
@@ -83,8 +93,8 @@ def test_dropped_pairs_never_reach_alpha_min(tiny_scene):
         p = r["proj"][r["cand_idx"][c]]
         t = int(r["cand_tile"][c])
         tx, ty = t % TW, t // TW
-        xs = np.arange(tx * 16, min(tx * 16 + 16, cam["width"])) + 0.5
-        ys = np.arange(ty * 16, min(ty * 16 + 16, cam["height"])) + 0.5
+        xs = np.arange(tx * tile, min(tx * tile + tile, cam["width"])) + 0.5
+        ys = np.arange(ty * tile, min(ty * tile + tile, cam["height"])) + 0.5
         X, Y = np.meshgrid(xs, ys)
         alpha, _ = _alpha_at(p, X, Y)
         assert alpha.max() < oracle.ALPHA_MIN
@@ -242,27 +252,29 @@ def test_equal_depth_ties_go_to_the_lower_node_id():
         np.testing.assert_allclose(r["image"][24, 32], a * f1 + a * (1 - a) * f2, rtol=1e-12)
 
 
-def test_tile_margin_is_the_max_over_the_pixel_centre_hull(tiny_scene):
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_margin_is_the_max_over_the_pixel_centre_hull(tiny_scene, tile):
     """For every candidate pair, margin + (ln alpha* - ln theta) is the maximum
     of rho over the convex hull of the tile's pixel centres, clipped to the
     image (the ragged last column and row included).  rho is concave, so a
     bounded quasi-Newton solve finds that maximum independently."""
     opt = pytest.importorskip("scipy.optimize")
-    cam = scenegen.camera((2.0, 10.0, 2.5), 0.1, 88, 56, 60.0)
-    r = oracle.render(tiny_scene, cam, 3.0)
+    cam = scenegen.camera((2.0, 10.0, 2.5), 0.1, 88 if tile < 32 else 100, 56 if tile < 32 else 70, 60.0)
+    r = oracle.render(tiny_scene, cam, 3.0, tile=tile)
     TW, TH = r["tiles"]
     W, H = cam["width"], cam["height"]
     rng = np.random.default_rng(3)
     cands = np.arange(len(r["cand_tile"]))
     edge = cands[(r["cand_tile"] % TW == TW - 1) | (r["cand_tile"] // TW == TH - 1)]
     assert len(edge) > 20
-    pick = np.concatenate([rng.choice(cands, 150, replace=False), rng.choice(edge, 50, replace=False)])
+    pick = np.concatenate([rng.choice(cands, min(150, len(cands)), replace=False),
+                           rng.choice(edge, 50, replace=False)])
     for c in pick:
         p = r["proj"][r["cand_idx"][c]]
         t = int(r["cand_tile"][c])
         tx, ty = t % TW, t // TW
-        lo = (16 * tx + 0.5, 16 * ty + 0.5)
-        hi = (min(16 * tx + 15.5, W - 0.5), min(16 * ty + 15.5, H - 0.5))
+        lo = (tile * tx + 0.5, tile * ty + 0.5)
+        hi = (min(tile * tx + tile - 0.5, W - 0.5), min(tile * ty + tile - 0.5, H - 0.5))
         a, b, cc = p["conic"]
 
         def neg(x):

@@ -26,7 +26,7 @@ MUTANTS = [
     ("SH view direction reversed", PROJ, "double dir[3] = {d[0] / nd, d[1] / nd, d[2] / nd};",
      "double dir[3] = {-d[0] / nd, -d[1] / nd, -d[2] / nd};"),
     ("near plane inclusive", PROJ, "if (!(zk > cam->z_near)) return;", "if (!(zk >= cam->z_near)) return;"),
-    ("tile rectangle at the tile edge", BLEND, "*x0 = ORC_TILE * tx + 0.5;", "*x0 = ORC_TILE * tx;"),
+    ("tile rectangle at the tile edge", BLEND, "*x0 = tile * tx + 0.5;", "*x0 = tile * tx;"),
     ("no Gaussian-level filter", BLEND, "if (P->theta < ORC_ALPHA_MIN) return; /* Gaussian-level filter */", ""),
     ("rho_max edge not clamped", BLEND, "double dy = orc_clamp(-b * dx / c, y0 - v, y1 - v);", "double dy = y0 - v;"),
     ("equal depths by descending id", BLEND, "if (x->node != y->node) return x->node < y->node ? -1 : 1;",
@@ -75,8 +75,8 @@ MUTANTS = [
      'return -0.5 * (conic[0] * dx * dx + conic[2] * dy * dy) + conic[1] * dx * dy;'),
     ('rho without 1/2', BLEND, 'return -0.5 * (conic[0]',
      'return -1.0 * (conic[0]'),
-    ('tile rectangle not clipped to the image', BLEND, '*x1 = fmin(ORC_TILE * tx + ORC_TILE - 0.5, (double)cam->width - 0.5);',
-     '*x1 = ORC_TILE * tx + ORC_TILE - 0.5;'),
+    ('tile rectangle not clipped to the image', BLEND, '*x1 = fmin(tile * tx + tile - 0.5, (double)cam->width - 0.5);',
+     '*x1 = tile * tx + tile - 0.5;'),
     ('rho_max without the inside case', BLEND, 'if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.0;',
      ''),
     ('box radius without the factor 2', BLEND, 'double r2 = 2.0 * (log(P->theta)',
