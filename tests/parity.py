@@ -1,11 +1,12 @@
 """Comparison helpers for the GPU-vs-oracle parity tests (not a test module).
 
 Bars (spec tolerances): the cut bit-exact; images within 2e-3 max-abs
-per channel on pixels the oracle does not flag as decision-ambiguous, and
-PSNR >= 55 dB over all pixels.  The pair set must equal the oracle's except
-within the FP32 test slack: every extra GPU pair has an oracle margin
-(rho_max - threshold) in [-(slack + delta), 0) and every missing oracle pair a
-margin below delta.
+per channel on every pixel, and PSNR >= 55 dB over all pixels.  The oracle's
+flag (pixels where an FP32 renderer may take the other side of an alpha*
+decision) is only reported, unless a test passes ``flip_allow`` explicitly.
+The pair set must equal the oracle's except within the FP32 test slack: every
+extra GPU pair has an oracle margin (rho_max - threshold) in
+[-(slack + delta), 0) and every missing oracle pair a margin below delta.
 """
 from __future__ import annotations
 
@@ -19,6 +20,21 @@ IMG_TOL = 2e-3
 PSNR_MIN = 55.0
 TILE_SLACK = 2e-3      # the renderer's FP32 tile-test slack (nats)
 MARGIN_DELTA = 2e-3    # FP32-vs-FP64 error allowance on rho_max (nats)
+FP32_U = 2.0 ** -24    # unit roundoff of FP32
+# Conic bound: the FP32 EWA (Sigma' = J R Sigma R^T J^T + 0.3 I, a few dozen
+# single-rounded operations) perturbs Sigma' by ~c u ||Sigma'||, and inverting
+# amplifies that by the condition number: ||d conic|| / ||conic|| <~ c u kappa(Sigma').
+# A float32 emulation of the kernel's arithmetic on the 1M-leaf box gives
+# max |d conic| / max(|a|, |c|) = 9.1 u kappa (median 0.7); 64 u kappa leaves 7x.
+CONIC_K = 64.0
+
+
+def cond2(cov3: np.ndarray) -> np.ndarray:
+    """Condition number lambda_max / lambda_min of 2x2 symmetric (00, 01, 11) matrices."""
+    cov3 = np.asarray(cov3, np.float64).reshape(-1, 3)
+    half_tr = 0.5 * (cov3[:, 0] + cov3[:, 2])
+    disc = np.sqrt(0.25 * (cov3[:, 0] - cov3[:, 2]) ** 2 + cov3[:, 1] ** 2)
+    return (half_tr + disc) / (half_tr - disc)
 
 
 def psnr(a: np.ndarray, b: np.ndarray) -> float:
@@ -30,29 +46,40 @@ def image_report(img: np.ndarray, ref: dict, tile_mask=None) -> dict:
     H, W = ref["image"].shape[:2]
     sel = np.ones((H, W), bool)
     if tile_mask is not None:
-        TW = (W + 15) // 16
+        T = int(ref.get("tile", 16))
+        TW = (W + T - 1) // T
         ty, tx = np.mgrid[0:H, 0:W]
-        sel = np.asarray(tile_mask).reshape(-1)[(ty // 16) * TW + tx // 16]
+        sel = np.asarray(tile_mask).reshape(-1)[(ty // T) * TW + tx // T]
     ok = sel & (ref["flags"] == 0)
     diff = np.abs(img.astype(np.float64) - ref["image"])
+    flagged = sel & (ref["flags"] != 0)
     return dict(max_abs=float(diff[ok].max()) if ok.any() else 0.0,
                 psnr=psnr(img[sel], ref["image"][sel]),
-                flagged=int((sel & (ref["flags"] != 0)).sum()), pixels=int(sel.sum()),
+                flagged=int(flagged.sum()), pixels=int(sel.sum()),
+                flagged_over_tol=int((flagged & (diff.max(axis=2) > IMG_TOL)).sum()),
                 max_abs_all=float(diff[sel].max()) if sel.any() else 0.0)
 
 
 FLIP_BOUND = 1e-2  # a flipped alpha* decision moves a pixel by at most ~2 alpha* max(rgb)
 
 
-def check_image(img, ref, tile_mask=None, tol=IMG_TOL, psnr_min=PSNR_MIN):
-    """2e-3 on unflagged pixels; flagged pixels (a near-threshold alpha
-    decision at T >= 0.05) within the bound of one flipped decision; PSNR over
-    all pixels.  The count guard catches a flag rule gone wrong."""
+def check_image(img, ref, tile_mask=None, tol=IMG_TOL, psnr_min=PSNR_MIN, flip_allow=0.0):
+    """Every pixel within ``tol`` (2e-3 per channel) of the FP64 oracle and
+    PSNR >= ``psnr_min`` over all pixels.  The oracle's flagged pixels (some
+    Gaussian within 2e-3 nats of the alpha* threshold while T >= 0.05) are
+    counted and returned, not excused.  A test that needs the allowance for
+    flipped alpha* decisions passes ``flip_allow`` (a fraction of the pixels,
+    at most 1 %): then up to that many flagged pixels may err beyond ``tol``,
+    each within FLIP_BOUND."""
+    assert 0.0 <= flip_allow <= 0.01, flip_allow
     r = image_report(img, ref, tile_mask)
-    assert r["max_abs"] <= tol, r
-    assert r["max_abs_all"] <= FLIP_BOUND, r
+    if flip_allow > 0.0:
+        assert r["max_abs"] <= tol, r
+        assert r["max_abs_all"] <= FLIP_BOUND, r
+        assert r["flagged_over_tol"] <= flip_allow * r["pixels"], r
+    else:
+        assert r["max_abs_all"] <= tol, r
     assert r["psnr"] >= psnr_min, r
-    assert r["flagged"] <= max(8, 0.05 * r["pixels"]), r
     return r
 
 
@@ -64,10 +91,11 @@ def pair_margin(ref: dict, tile: int, node: int) -> float:
     assert cut[g] == node
     p = ref["proj"][g]
     H, W = ref["image"].shape[:2]
-    TW = (W + 15) // 16
+    T = int(ref.get("tile", 16))
+    TW = (W + T - 1) // T
     tx, ty = tile % TW, tile // TW
-    x0, y0 = 16 * tx + 0.5, 16 * ty + 0.5
-    x1, y1 = min(16 * tx + 15.5, W - 0.5), min(16 * ty + 15.5, H - 0.5)
+    x0, y0 = T * tx + 0.5, T * ty + 0.5
+    x1, y1 = min(T * tx + T - 0.5, W - 0.5), min(T * ty + T - 0.5, H - 0.5)
     return oracle.rho_max_rect(p["conic"], p["u"], p["v"], x0, x1, y0, y1) - p["thr"]
 
 
@@ -75,22 +103,24 @@ def _pairkey(tile, node):
     return (np.asarray(tile, np.int64) << 32) | np.asarray(node, np.int64)
 
 
-def _rows_needed(A, B, tile, TW, chunk=8192):
-    """Bit w set when some pixel of rows 2w, 2w+1 of the pair's tile has
-    rho >= thr - 1e-3 (FP64, from the pair's FP32 record)."""
+def _rows_needed(A, B, tile, TW, T=16, chunk=8192):
+    """Bit w set when some pixel of the pair's tile in rows w r .. w r + r - 1
+    (r = max(1, T / 8) rows per bit) has rho >= thr - 1e-3 (FP64, from the
+    pair's FP32 record)."""
     out = np.zeros(len(tile), np.int64)
-    c16 = np.arange(16, dtype=np.float64) + 0.5
+    cT = np.arange(T, dtype=np.float64) + 0.5
+    mr = max(1, T // 8)
     for s0 in range(0, len(tile), chunk):
         sl = slice(s0, s0 + chunk)
         t = tile[sl]
         a, b, c = (A[sl, 2].astype(np.float64), A[sl, 3].astype(np.float64), B[sl, 0].astype(np.float64))
-        dx = A[sl, 0].astype(np.float64)[:, None] - ((t % TW) * 16)[:, None] - c16[None, :]   # [P, col]
-        dy = A[sl, 1].astype(np.float64)[:, None] - ((t // TW) * 16)[:, None] - c16[None, :]  # [P, row]
+        dx = A[sl, 0].astype(np.float64)[:, None] - ((t % TW) * T)[:, None] - cT[None, :]   # [P, col]
+        dy = A[sl, 1].astype(np.float64)[:, None] - ((t // TW) * T)[:, None] - cT[None, :]  # [P, row]
         rho = (a[:, None, None] * dx[:, None, :] ** 2 + b[:, None, None] * dx[:, None, :] * dy[:, :, None]
-               + c[:, None, None] * dy[:, :, None] ** 2)                                       # [P, row, col]
-        rows = (rho >= B[sl, 1].astype(np.float64)[:, None, None] - 1e-3).any(axis=2)         # [P, row]
-        pairs = rows[:, 0::2] | rows[:, 1::2]
-        out[sl] = (pairs * (1 << np.arange(8))).sum(axis=1)
+               + c[:, None, None] * dy[:, :, None] ** 2)                                     # [P, row, col]
+        rows = (rho >= B[sl, 1].astype(np.float64)[:, None, None] - 1e-3).any(axis=2)       # [P, row]
+        groups = rows.reshape(len(t), T // mr, mr).any(axis=2)
+        out[sl] = (groups * (1 << np.arange(T // mr))).sum(axis=1)
     return out
 
 
@@ -101,6 +131,7 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None, theta_rtol: float = 0.0) 
     Gaussians are interpolated (then it is computed: theta_rtol > 0)."""
     cut = ref["cut"]
     np.testing.assert_array_equal(dbg["cut"], cut)
+    assert int(dbg.get("tile_size", 16)) == int(ref.get("tile", 16)), "renderer and oracle tile sizes differ"
     proj = ref["proj"]
     # per-cut-index best candidate margin
     best = np.full(len(cut), -np.inf)
@@ -137,8 +168,12 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None, theta_rtol: float = 0.0) 
         assert err.max() < 2e-5, (key, err[w], A[w, j], p[key][w], p["z"][w], p["cov"][w])
     con = np.stack([-2.0 * A[:, 2], -A[:, 3], -2.0 * B[:, 0]], 1)
     cref = p["conic"]
-    cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))[:, None]
-    assert np.max(np.abs(con - cref) / cs) < 2e-3
+    cs = np.maximum(np.abs(cref[:, 0]), np.abs(cref[:, 2]))
+    rel = np.max(np.abs(con - cref), axis=1) / cs
+    kappa = cond2(p["cov"])
+    bound = CONIC_K * FP32_U * kappa
+    worst = int(np.argmax(rel / bound)) if len(rel) else 0
+    assert np.all(rel <= bound), (float(rel[worst]), float(kappa[worst]), float((rel / (FP32_U * kappa)).max()))
     rgb = dbg["vis_rgb"][:, :3]
     assert np.max(np.abs(rgb - p["rgb"])) < 2e-5
     if theta_rtol > 0:
@@ -185,7 +220,7 @@ def check_stages(dbg: dict, ref: dict, tile_mask=None, theta_rtol: float = 0.0) 
     if "pair_rowmask" in dbg and len(pr):
         TW = int(dbg["tiles"][0])
         vis = order[pr]
-        need = _rows_needed(A[vis], B[vis], pt, TW)
+        need = _rows_needed(A[vis], B[vis], pt, TW, int(dbg.get("tile_size", 16)))
         got = dbg["pair_rowmask"].astype(np.int64)
         bad = (got & need) != need
         assert not bad.any(), (int(bad.sum()), got[bad][:5], need[bad][:5])
