@@ -117,18 +117,22 @@ def code_sha256(path: str) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
-def _traffic(kernel: str, source: str, algorithmic: float):
+def _traffic(kernel: str, source: str, units: float):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), used only while the kernel's code is the one the
-    counters were taken on (code_sha256 of csrc/<source>); else None."""
+    counters were taken on (code_sha256 of csrc/<source>); else None.  The
+    counters come from a smaller case of the same workload (one kernel, a few
+    launches); they are scaled to this launch by its units (the count named
+    in the record: visible Gaussians or pairs)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2506_02774_gb300", "csrc", source)
     if not os.path.exists(p) or not os.path.exists(src):
         return None
     d = json.load(open(p)).get(kernel)
-    if not d or d.get("code_sha256") != code_sha256(src):
+    if not d or d.get("code_sha256") != code_sha256(src) or not d.get("units_per_launch"):
         return None
-    return int(d["dram_bytes_per_launch"])
+    per_unit = float(d["dram_bytes_per_launch"]) / float(d["units_per_launch"])
+    return int(round(per_unit * units))
 
 
 def rank_walk(cfg: dict, rank: int):
@@ -193,6 +197,55 @@ def frame_roofline(fb: dict, stage_ms: dict, frame_ms: float, hbm_gbs: float) ->
                 frac=round(roof_ms / frame_ms, 4), stage_frac=per_stage)
 
 
+def blend_roofline(mean: dict, blend_ms: float, sms: int, peaks: dict, blend_bytes: float, blend_gbs: float) -> dict:
+    """The blend (the kernel with the largest share of the frame) against its
+    plain-ALU roofline: FP32 lane-instructions the method needs per evaluated
+    pixel-pair (dx, dy, rho, Eq. 4 test) and per blended one (exp argument,
+    alpha, T update, test, weight, 3 colour FMAs), against the device's SMs x
+    128 FP32 lanes x the maximum SM clock."""
+    X, K = mean["pixel_pair_evals"], mean["pixel_pair_contribs"]
+    ops = OPS_PER_EVAL * X + OPS_PER_CONTRIB * K
+    t = blend_ms * 1e-3
+    peak_t = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    units = mean["pair_count"]
+    return dict(bound="alu", stage="blend", kernel="k_blend", achieved=round(ops / t / 1e12, 3),
+                peak=round(peak_t, 2), unit="TFLOP/s", frac=round(ops / t / 1e12 / peak_t, 4),
+                traffic=_traffic("k_blend", "k_blend.cu", units),
+                peak_source="%d SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz, %s), one op per FP32 "
+                            "lane-instruction" % (sms, peaks["sm_max_mhz"], peaks["source"]),
+                ops_per_launch=int(ops), kernel_ms=round(blend_ms, 4), algorithmic_bytes=int(blend_bytes),
+                hbm_frac=round(blend_gbs / peaks["hbm_gbs"], 4))
+
+
+def hbm_roofline(stage: str, kernel: str, source: str, alg_bytes: float, ms: float, peaks: dict, units: float) -> dict:
+    """An HBM-bound stage: algorithmic bytes per launch over its mean stage time
+    against the measured copy bandwidth."""
+    gbs = alg_bytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return dict(bound="hbm", stage=stage, kernel=kernel, achieved=round(gbs, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=round(gbs / peaks["hbm_gbs"], 4), traffic=_traffic(kernel, source, units),
+                peak_source=peaks["source"] + " hbm_gbs (MEASURED_PEAKS.json)", algorithmic_bytes=int(alg_bytes),
+                kernel_ms=round(ms, 4))
+
+
+def workload_label(wl: dict, leaves: int) -> dict:
+    """The workload with its label naming an overridden leaf count."""
+    if not leaves:
+        return wl
+    return dict(wl, label="%s (%d leaves)" % (wl["label"].replace("18M-leaves-", ""), leaves))
+
+
+def workload_config(wl: dict, sc: dict, cfg: dict, args, ws: int) -> dict:
+    """The `config` of the JSON line; identical for both arms of a run."""
+    nbytes = sum(int(np.asarray(sc[k]).nbytes) for k in
+                 ("parent", "first_child", "n_child", "mean", "cov6", "opacity", "sh", "radius2", "bbox")
+                 if sc.get(k) is not None)
+    return dict(workload=wl["label"], leaves=int(sc["n_leaves"]), nodes=int(sc["n_nodes"]),
+                width=cfg["width"], height=cfg["height"], tau=cfg["tau"], storage=args.storage,
+                frames="%d..%d of the %d-frame walk" % (args.warmup, args.warmup + args.steps - 1, cfg["frames"]),
+                l2="inputs larger than L2 (scene arrays %.1f GB)" % (nbytes / 1e9),
+                parallelism="replicas" if ws > 1 else "single")
+
+
 def run_ours(args) -> dict:
     import torch
 
@@ -211,8 +264,7 @@ def run_ours(args) -> dict:
     cfg = scenegen.CONFIGS[wl["scene"]]
     t0 = time.time()
     sc = scenegen.make_scene(wl["scene"], n_leaves=args.leaves or None)
-    if args.leaves:
-        wl = dict(wl, label="%s (%d leaves)" % (wl["label"].replace("18M-leaves-", ""), args.leaves))
+    wl = workload_label(wl, args.leaves)
     t_gen = time.time() - t0
     t0 = time.time()
     h = vgr.Hierarchy(sc, storage=vgr.STORE_HALF if args.storage == "half" else vgr.STORE_FP32)
@@ -457,43 +509,21 @@ def run_ours(args) -> dict:
     fb = _frame_bytes(sc, mean, W, H, tp)
     peaks = _peaks()
     shares = {s: float(stage_ms[i]) for i, s in enumerate(vgr.STAGES)}
-    top = max(shares, key=shares.get)
     hbm_stages = {s: fb[s] / (shares[s] * 1e-3) / 1e9 for s in vgr.STAGES if shares[s] > 0}
-    if top == "blend":
-        # plain-ALU roofline: FP32 lane-instructions the method needs per
-        # evaluated pixel-pair (dx, dy, rho, Eq. 4 test) and per blended one
-        # (exp argument, alpha, T update, test, weight, 3 colour FMAs),
-        # against SMs x 128 FP32 lanes x clock
-        X, K = mean["pixel_pair_evals"], mean["pixel_pair_contribs"]
-        ops = OPS_PER_EVAL * X + OPS_PER_CONTRIB * K
-        t = shares[top] * 1e-3
-        peak_t = 152 * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        roof = dict(bound="alu", stage=top, achieved=round(ops / t / 1e12, 3), peak=round(peak_t, 2),
-                    unit="TFLOP/s", frac=round(ops / t / 1e12 / peak_t, 4),
-                    traffic=_traffic("k_blend", "k_blend.cu", fb[top]),
-                    peak_source="152 SMs x 128 FP32 lanes x %.0f MHz (sm_max_mhz of %s), one op per FP32 "
-                                "lane-instruction" % (peaks["sm_max_mhz"], peaks["source"]),
-                    ops_per_launch=int(ops), kernel_ms=round(shares[top], 4),
-                    hbm_frac=round(hbm_stages[top] / peaks["hbm_gbs"], 4))
-    else:
-        roof = dict(bound="hbm", stage=top, achieved=round(hbm_stages.get(top, 0.0), 1), peak=peaks["hbm_gbs"],
-                    unit="GB/s", frac=round(hbm_stages.get(top, 0.0) / peaks["hbm_gbs"], 4),
-                    traffic=None, peak_source=peaks["source"] + " hbm_gbs (MEASURED_PEAKS.json)",
-                    algorithmic_bytes=int(fb[top]), kernel_ms=round(shares[top], 4))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof_blend = blend_roofline(mean, shares["blend"], sms, peaks, fb["blend"], hbm_stages.get("blend", 0.0))
+    roof_color = hbm_roofline("color", "k_color", "k_preprocess.cu", fb["color"], shares["color"], peaks,
+                              mean["visible_count"])
     out = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=ws, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms / args.steps, 4), higher_is_better=True,
                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-               config=dict(workload=wl["label"], leaves=int(sc["n_leaves"]), nodes=int(sc["n_nodes"]),
-                           width=W, height=H, tau=tau, storage=args.storage,
-                           frames="%d..%d of the %d-frame walk" % (args.warmup, args.warmup + args.steps - 1, nfr),
-                           l2="inputs larger than L2 (scene %.1f GB on the device)" % (h.device_bytes / 1e9),
-                           parallelism="replicas" if ws > 1 else "single"),
+               config=workload_config(wl, sc, cfg, args, ws),
                e2e=dict(value=round(e2e["value"], 2), unit=e2e["unit"],
                         h2d_bytes_per_step=e2e["h2d_bytes_per_step"], d2h_bytes_per_step=e2e["d2h_bytes_per_step"]),
                gpu_launches=int(kernels),
                launch_mode="cuda-graph replay per frame" if not args.no_graph else "plain launch loop",
                value_plain_loop=round(value_loop, 2),
-               roofline=roof, clocks=clocks,
+               roofline=roof_blend, roofline_blend=roof_blend, roofline_color=roof_color, clocks=clocks,
                frame_latency_ms=dict(p50=round(1e3 * float(np.percentile(lat, 50)), 4),
                                      p99=round(1e3 * float(np.percentile(lat, 99)), 4)),
                stage_ms={k: round(v, 4) for k, v in shares.items()},
@@ -552,6 +582,11 @@ def run_batched(sc, n_views: int, steps: int, warmup: int, seed: int = 4) -> dic
     frames = list(range(300 - warmup, 300 + steps))
     cams = {fr: [scenegen.street_trajectory("city", 200 + i, fr, *sizes[i]) for i in range(n_views)] for fr in frames}
     taus = [tau] * n_views
+    # the single blend launch of the batch: its tile size and staging depth
+    # tuned on the batch itself (frames 290..295 of every view's walk), then left set
+    tune_steps = [[scenegen.street_trajectory("city", 200 + i, fr, *sizes[i]) for i in range(n_views)]
+                  for fr in range(290, 296)]
+    batch_tuned = autotune.tune_batch(views, tune_steps, taus)
     out = {}
     for mode in ("sequential", "batched"):
         for v in views:
@@ -577,9 +612,13 @@ def run_batched(sc, n_views: int, steps: int, warmup: int, seed: int = 4) -> dic
     counts = {n: pick.count(n) for n in names}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     tuned = {n: dict(grid_wide_per_sm=g["grid_wide"] // sms, grid_scan_per_sm=g["grid_scan"] // sms,
-                     ms=g["ms"], default_ms=g["default_ms"]) for n, g in geom.items()}
+                     tile_size_alone=g["tile_size"], blend_depth_alone=g["blend_depth"], ms=g["ms"],
+                     default_ms=g["default_ms"])
+             for n, g in geom.items()}
     return dict(views=n_views, sizes=counts, frames="300..%d of each view's own street walk" % (300 + steps - 1),
-                autotuned=tuned,
+                autotuned=tuned, batch_tuned=batch_tuned,
+                launch="every view's frame a branch of one captured graph up to its tile order; one launch "
+                       "orders all views' tiles, one persistent blend shades them",
                 storage="fp16 SH + bf16 covariance", views_device_gb=round(dev_bytes / 1e9, 1),
                 speedup=round(out["batched"]["views_per_s"] / out["sequential"]["views_per_s"], 3), **out)
 
@@ -690,6 +729,10 @@ def cpu_baseline(sc, cams, tau, budget_s: float = 20.0, single_thread: bool = Tr
 
 
 def run_reference(args) -> dict:
+    """The reference arm: the FP64 oracle (the paper released no code) on the
+    host cores, on the same walk, config, metric and unit as the GPU arm.
+    Every step is one whole frame of the walk: W untimed warm-up frames, then
+    the K timed ones (about 1.7 s each on 16 Arm cores for the city)."""
     import oracle
     import scenegen
     ws, rank, _ = _dist()
@@ -697,26 +740,23 @@ def run_reference(args) -> dict:
     cfg = scenegen.CONFIGS[wl["scene"]]
     if rank != 0:
         return None
-    sc = scenegen.make_scene(wl["scene"])
+    sc = scenegen.make_scene(wl["scene"], n_leaves=args.leaves or None)
+    wl = workload_label(wl, args.leaves)
     cams = [scenegen.trajectory(wl["scene"], f % cfg["frames"]) for f in range(args.warmup + args.steps)]
     n_thr = oracle.num_threads()
-    # each step is a bounded sample: every (K/stride)-th frame keeps the run within minutes
-    per_frame_cap = max(1, int(math.ceil(args.steps / 4)))
-    sample = cams[args.warmup::max(1, args.steps // per_frame_cap)][:per_frame_cap]
-    for cam in cams[:min(1, args.warmup)]:
+    for cam in cams[:args.warmup]:
         oracle.render(sc, cam, cfg["tau"])
     t = time.perf_counter()
-    for cam in sample:
+    for cam in cams[args.warmup:]:
         oracle.render(sc, cam, cfg["tau"])
     dt = time.perf_counter() - t
-    value = len(sample) / dt
-    desc = "%d of the %d timed frames (every %d-th), FP64 oracle, %d OpenMP threads, %.1f s" % (
-        len(sample), args.steps, max(1, args.steps // per_frame_cap), n_thr, dt)
+    value = args.steps / dt
+    desc = "all %d timed frames %d..%d of the walk after %d warm-up frames, FP64 oracle, %d OpenMP threads, %.1f s" % (
+        args.steps, args.warmup, args.warmup + args.steps - 1, args.warmup, n_thr, dt)
     return dict(impl="reference", metric=METRIC, value=round(value, 4), unit="frames/s", n_gpus=ws,
-                steps=args.steps, warmup=args.warmup, ms_per_step=round(1e3 / value, 2), higher_is_better=True,
-                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=wl["label"], leaves=int(sc["n_leaves"]), nodes=int(sc["n_nodes"]),
-                            width=cfg["width"], height=cfg["height"], tau=cfg["tau"]),
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(1e3 * dt / args.steps, 2),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=workload_config(wl, sc, cfg, args, ws),
                 cpu_baseline=dict(value=round(value, 4), unit="frames/s", cores=n_thr, kind="oracle", sample=desc),
                 e2e=dict(value=round(value, 4), unit="frames/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
@@ -724,8 +764,9 @@ def run_reference(args) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed frames (default 300; 20 for --impl reference, whose frames take seconds)")
+    ap.add_argument("--warmup", type=int, default=None, help="untimed frames before them (default 10; 3 for the reference)")
     ap.add_argument("--no-graph", action="store_true", help="headline view without CUDA graph replay")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batch leg")
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16-store run of the walk")
@@ -750,6 +791,11 @@ def main():
     ap.add_argument("--no-cpu-single", action="store_true", help="skip the single-threaded oracle frame")
     ap.add_argument("--leaves", type=int, default=0, help="override the workload's leaf count (smaller profiling cases)")
     args = ap.parse_args()
+    ref = args.impl == "reference"
+    if args.steps is None:
+        args.steps = 20 if ref else 300
+    if args.warmup is None:
+        args.warmup = 3 if ref else 10
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         out = run_reference(args)

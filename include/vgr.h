@@ -132,6 +132,11 @@ typedef struct {
     float lod_frustum_guard; /* pixels the frustum test adds beyond each image edge (default 2) */
     uint32_t lod_interp;     /* 1: parent-child weight interpolation of the cut's Gaussians (default 0),
                                 see vgr_render_frame */
+    uint32_t blend_depth;    /* Gaussians the blend stages per warp and chunk: 16, 32 or 48 (0 = 32).
+                                A tuning knob: results do not depend on it. */
+    uint32_t tile_size;      /* side of a square tile in pixels: 8, 16 or 32 (0 = 16); 8 needs images of
+                                at most 8192 x 8192 and a blend_depth of 16 or 32.  The pairs are per
+                                tile; the cut and the image do not depend on it. */
 } vgr_view_opts;
 
 enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1 };
@@ -184,8 +189,10 @@ typedef struct {
     const uint32_t* depth_order;  /* [n_front] in-front index by depth rank; the first n_visible are visible */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */
     const uint32_t* pair_val;     /* [n_pairs] in-front index << 8 | row mask (bit w: the footprint box reaches
-                                     pixel row 2w or 2w + 1 of the tile; all ones in the canonical mode) */
+                                     one of the tile's pixel rows w r .. w r + r - 1, r = max(1, tile_size / 8);
+                                     all ones in the canonical mode) */
     const uint32_t* tile_range;   /* [2 tiles] start, end into the pair list */
+    uint32_t tile_size;           /* side of a tile in pixels; a row-mask bit covers max(1, tile_size / 8) rows */
 } vgr_debug_buffers;
 
 void vgr_default_view_opts(vgr_view_opts* opts);
@@ -205,6 +212,17 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
 vgr_status vgr_destroy_view(vgr_view* v);
 /* Forget the previous cut: the next frame finds its cut top-down. */
 vgr_status vgr_reset_view(vgr_view* v);
+/*
+ * Change a view's tuning knobs (vgr_view_opts.grid_wide, grid_scan,
+ * blend_depth, tile_size; 0 keeps the current value) between frames, for an
+ * autotuner.  The cut and the image do not depend on them (the pair lists
+ * follow the tile size).  Captured frames are dropped and captured again on
+ * next use; the previous cut is kept.  VGR_E_INVALID while a frame is in
+ * flight, for a depth other than 16, 32, 48, a tile size other than 8, 16,
+ * 32, or depth 48 with 8-pixel tiles.
+ */
+vgr_status vgr_view_set_tuning(vgr_view* v, uint32_t grid_wide, uint32_t grid_scan, uint32_t blend_depth,
+                               uint32_t tile_size);
 vgr_status vgr_view_device_bytes(const vgr_view* v, uint64_t* bytes);
 
 /*
@@ -294,12 +312,19 @@ vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* 
 /*
  * Frame server with continuous batching (no counterpart in the paper, which
  * renders one view).  Each client of a server owns a view (own stream),
- * created when the client's first request is admitted: admission requires
+ * created when the client's first request is admitted.  Admission requires
  * free device memory >= vgr_view_bytes_estimate at the request's image size
- * + hbm_reserve, otherwise the request completes with VGR_E_NOMEM.  A
- * client's requests run in arrival order, one frame in flight per client;
- * frames of different clients run concurrently, at most max_inflight at a
- * time, and a request starts as soon as its client and a slot are free.
+ * + hbm_reserve.  When that is short, the server (evict_idle set) releases
+ * the views of idle clients -- no frame in flight and no request waiting --
+ * least recently used first, until the view fits; if it still does not fit
+ * while other frames are in flight, the request stays queued and admission
+ * is tried again each time a frame completes.  Only a request that cannot
+ * fit with nothing else in flight and no idle view left completes with
+ * VGR_E_NOMEM.  A released client's next frame finds its cut top-down, which
+ * gives the same cut as the temporal update.  A client's requests run in
+ * arrival order, one frame in flight per client; frames of different clients
+ * run concurrently on their own streams, at most max_inflight at a time, and
+ * a request starts as soon as its client, a slot and the memory are free.
  */
 typedef struct vgr_server vgr_server;
 
@@ -310,6 +335,8 @@ typedef struct {
     uint64_t hbm_reserve;    /* free device bytes admission keeps (default 1 GiB) */
     vgr_view_opts view;      /* options of every client's view; stream and timing are ignored
                                 (default: vgr_default_view_opts with use_graph = 1) */
+    uint32_t evict_idle;     /* 1 (default): release idle clients' views, least recently used
+                                first, when admission lacks memory; 0: never release a view */
 } vgr_serve_opts;
 
 typedef struct {
@@ -317,16 +344,23 @@ typedef struct {
     float tau;
     double arrival_s;        /* seconds after the start of vgr_serve_trace; non-decreasing */
     vgr_camera cam;
+    float* host_rgb;         /* NULL, or a caller-owned host buffer of cam.height x cam.width x 3
+                                floats for this request's image (used instead of the client's
+                                buffer); pinned memory of the server's device is written by the
+                                blend itself, other memory receives a copy after the frame.  It
+                                must stay valid until vgr_serve_trace returns. */
 } vgr_request;
 
 typedef struct {
     double start_s;          /* submission (after admission) */
     double finish_s;         /* completion seen by the server: image in device memory, and in the
-                                client's host buffer when host_images is set */
-    vgr_status status;       /* VGR_OK, VGR_E_NOMEM (not admitted) or the frame's error */
+                                request's or the client's host buffer when one is used */
+    vgr_status status;       /* VGR_OK, VGR_E_NOMEM (could not be admitted) or the frame's error */
     uint32_t cut_count, visible_count;
     uint64_t pair_count;
     uint32_t replays, lod_from_scratch;
+    uint32_t admission_waits;  /* times admission found too little memory and the request waited */
+    uint32_t views_released;   /* idle clients' views released to admit this request */
 } vgr_request_result;
 
 void vgr_default_serve_opts(vgr_serve_opts* opts);
@@ -382,13 +416,15 @@ vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint
  *   - n is limited to VGR_SORT_NOALLOC_MAX_N (262,144) pairs; larger n
  *     returns VGR_E_INVALID without touching the GPU.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address and clears the array on 'stream'; make that
- *     first call before any stream capture.
- *   - Every call on a device shares the one array, which keeps the last
+ *     array's device address, clears the array on 'stream' and waits for the
+ *     clear; make that first call before any stream capture.
+ *   - Every call waits for its stream before it returns, so a call made
+ *     after another call has returned -- on any stream -- is ordered after
+ *     it.  Every call on a device shares the one array, which keeps the last
  *     call's contents; each call clears what it needs at its start.  Calls
- *     whose work overlaps on the GPU (different streams or threads without
- *     ordering between them) race on the array and give wrong results:
- *     order them.
+ *     that run at the same time (from different host threads, on different
+ *     streams) race on the array and give wrong results: do not overlap
+ *     them.
  */
 vgr_status vgr_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                   uint32_t* vals_out, uint64_t n, uint32_t key_bits, void* stream);

@@ -17,7 +17,7 @@ from . import _abi
 from ._abi import (EXP_EXACT, EXP_LUT, FILTER_CANONICAL, FILTER_PREEMPTIVE, STAGES, STORE_FP32, STORE_HALF,
                    VgrError)
 
-__all__ = ["Renderer", "Hierarchy", "View", "FrameResult", "Server", "render_batch", "camera_struct", "sort_pairs", "VgrError",
+__all__ = ["Renderer", "Hierarchy", "View", "FrameResult", "Server", "render_batch", "camera_struct", "sort_pairs", "VgrError", "view_bytes_estimate",
            "load_library", "STORE_FP32",
            "STORE_HALF", "FILTER_PREEMPTIVE", "FILTER_CANONICAL", "EXP_EXACT", "EXP_LUT", "STAGES"]
 
@@ -169,7 +169,8 @@ class View:
                  lut_size: int = 32, temporal: bool = True, timing: bool = False, use_graph: bool = False,
                  cut_capacity: int = 0, pair_capacity: int = 0, lod_budget: int = 0, grid_wide: int = 0,
                  grid_scan: int = 0, test_hooks: int = 0, lod_frustum: bool = False,
-                 lod_frustum_guard: float = 2.0, lod_interp: bool = False, stream=None):
+                 lod_frustum_guard: float = 2.0, lod_interp: bool = False, blend_depth: int = 0,
+                 tile_size: int = 0, stream=None):
         lib = _abi.load()
         o = _abi.ViewOpts()
         lib.vgr_default_view_opts(ctypes.byref(o))
@@ -182,6 +183,10 @@ class View:
         o.test_hooks = int(test_hooks)
         o.lod_frustum, o.lod_frustum_guard = int(lod_frustum), float(lod_frustum_guard)
         o.lod_interp = int(lod_interp)
+        if blend_depth:
+            o.blend_depth = int(blend_depth)
+        if tile_size:
+            o.tile_size = int(tile_size)
         if stream is not None:
             o.stream = ctypes.c_void_p(int(stream))
         v = ctypes.c_void_p()
@@ -236,6 +241,12 @@ class View:
     def reset(self):
         _abi.check(_abi.load().vgr_reset_view(self.handle))
 
+    def set_tuning(self, grid_wide: int = 0, grid_scan: int = 0, blend_depth: int = 0, tile_size: int = 0):
+        """Change the launch geometry, the blend's staging depth and the tile
+        size (0 keeps a value; ``vgr_view_set_tuning``)."""
+        _abi.check(_abi.load().vgr_view_set_tuning(self.handle, int(grid_wide), int(grid_scan), int(blend_depth),
+                                                   int(tile_size)))
+
     def device_bytes(self) -> int:
         b = ctypes.c_uint64()
         _abi.check(_abi.load().vgr_view_device_bytes(self.handle, ctypes.byref(b)))
@@ -270,7 +281,7 @@ class View:
                     vis_recA=f32(d.vis_recA, (nf, 4))[vis], vis_recB=f32(d.vis_recB, (nf, 4))[vis],
                     vis_rgb=f32(d.vis_rgb, (nf, 4))[vis], depth_order=compact[order].astype(np.uint32),
                     pair_tile=u32(d.pair_tile, npairs), pair_rank=rank_of_front[pval >> 8], pair_rowmask=pval & 0xFF,
-                    tile_range=u32(d.tile_range, 2 * T).reshape(T, 2))
+                    tile_range=u32(d.tile_range, 2 * T).reshape(T, 2), tile_size=int(d.tile_size))
 
     def close(self):
         if self.handle:
@@ -340,15 +351,29 @@ class Renderer:
         return False
 
 
+def view_bytes_estimate(hier: Hierarchy, width: int, height: int, **view_kw) -> int:
+    """Device bytes a view with these options holds after its first frame at
+    width x height (``vgr_view_bytes_estimate``)."""
+    lib = _abi.load()
+    o = _abi.ViewOpts()
+    lib.vgr_default_view_opts(ctypes.byref(o))
+    for k, val in view_kw.items():
+        setattr(o, k, val)
+    b = ctypes.c_uint64()
+    _abi.check(lib.vgr_view_bytes_estimate(hier.handle, ctypes.byref(o), int(width), int(height), ctypes.byref(b)))
+    return int(b.value)
+
+
 class Server:
     """Continuous-batching frame server over one hierarchy (``vgr_create_server``)."""
 
     def __init__(self, hier: Hierarchy, n_clients: int, *, max_inflight: int = 0, host_images: bool = False,
-                 hbm_reserve: int | None = None, use_graph: bool = True, **view_kw):
+                 hbm_reserve: int | None = None, use_graph: bool = True, evict_idle: bool = True, **view_kw):
         lib = _abi.load()
         o = _abi.ServeOpts()
         lib.vgr_default_serve_opts(ctypes.byref(o))
         o.n_clients, o.max_inflight, o.host_images = int(n_clients), int(max_inflight), int(host_images)
+        o.evict_idle = int(bool(evict_idle))
         if hbm_reserve is not None:
             o.hbm_reserve = int(hbm_reserve)
         o.view.use_graph = int(use_graph)
@@ -360,26 +385,39 @@ class Server:
         self.hier = hier
         self.n_clients = int(n_clients)
 
-    def serve(self, requests):
+    def serve(self, requests, images: bool = False):
         """Serve a trace in real time.  ``requests``: list of dicts with client,
         arrival_s, cam, tau (arrival_s non-decreasing).  Returns a numpy record
-        array with start_s, finish_s, status, counts per request."""
+        array with start_s, finish_s, status, counts per request; with
+        ``images`` also a list of every request's image (pinned host buffers
+        the blend writes directly, one per request)."""
         n = len(requests)
         rq = (_abi.Request * max(1, n))()
+        bufs = []
+        if images:
+            import torch
         for i, r in enumerate(requests):
             rq[i].client = int(r["client"])
             rq[i].tau = float(r["tau"])
             rq[i].arrival_s = float(r["arrival_s"])
             rq[i].cam = camera_struct(r["cam"])
+            if images:
+                b = torch.zeros((int(r["cam"]["height"]), int(r["cam"]["width"]), 3), dtype=torch.float32,
+                                pin_memory=True)
+                bufs.append(b)
+                rq[i].host_rgb = b.data_ptr()
         rs = (_abi.RequestResult * max(1, n))()
         _abi.check(_abi.load().vgr_serve_trace(self.handle, rq, n, rs))
         out = np.zeros(n, dtype=[("client", "u4"), ("arrival_s", "f8"), ("start_s", "f8"), ("finish_s", "f8"),
                                  ("status", "i4"), ("cut_count", "u4"), ("visible_count", "u4"),
-                                 ("pair_count", "u8"), ("replays", "u4"), ("lod_from_scratch", "u4")])
+                                 ("pair_count", "u8"), ("replays", "u4"), ("lod_from_scratch", "u4"),
+                                 ("admission_waits", "u4"), ("views_released", "u4")])
         for i in range(n):
             x = rs[i]
             out[i] = (rq[i].client, rq[i].arrival_s, x.start_s, x.finish_s, x.status, x.cut_count, x.visible_count,
-                      x.pair_count, x.replays, x.lod_from_scratch)
+                      x.pair_count, x.replays, x.lod_from_scratch, x.admission_waits, x.views_released)
+        if images:
+            return out, [b.numpy().copy() for b in bufs]
         return out
 
     def client_host_image(self, client: int, height: int, width: int):

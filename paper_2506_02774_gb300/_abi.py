@@ -34,7 +34,7 @@ class ViewOpts(ctypes.Structure):
                 ("temporal", c_u32), ("timing", c_u32), ("use_graph", c_u32), ("cut_capacity", c_u64),
                 ("pair_capacity", c_u64), ("lod_budget", c_u32), ("grid_wide", c_u32), ("grid_scan", c_u32),
                 ("test_hooks", c_u32), ("lod_frustum", c_u32), ("lod_frustum_guard", c_f32),
-                ("lod_interp", c_u32)]
+                ("lod_interp", c_u32), ("blend_depth", c_u32), ("tile_size", c_u32)]
 
 
 class FrameStats(ctypes.Structure):
@@ -55,22 +55,23 @@ class DebugBuffers(ctypes.Structure):
                 ("tiles_y", c_u32), ("cut", c_vp), ("vis_node", c_vp), ("vis_depth", c_vp),
                 ("vis_ntile", c_vp), ("vis_rect", c_vp), ("vis_recA", c_vp), ("vis_recB", c_vp),
                 ("vis_rgb", c_vp), ("depth_order", c_vp), ("pair_tile", c_vp), ("pair_val", c_vp),
-                ("tile_range", c_vp)]
+                ("tile_range", c_vp), ("tile_size", c_u32)]
 
 
 class ServeOpts(ctypes.Structure):
     _fields_ = [("n_clients", c_u32), ("max_inflight", c_u32), ("host_images", c_u32), ("hbm_reserve", c_u64),
-                ("view", ViewOpts)]
+                ("view", ViewOpts), ("evict_idle", c_u32)]
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("client", c_u32), ("tau", c_f32), ("arrival_s", ctypes.c_double), ("cam", Camera)]
+    _fields_ = [("client", c_u32), ("tau", c_f32), ("arrival_s", ctypes.c_double), ("cam", Camera),
+                ("host_rgb", c_vp)]
 
 
 class RequestResult(ctypes.Structure):
     _fields_ = [("start_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("status", c_i32),
                 ("cut_count", c_u32), ("visible_count", c_u32), ("pair_count", c_u64), ("replays", c_u32),
-                ("lod_from_scratch", c_u32)]
+                ("lod_from_scratch", c_u32), ("admission_waits", c_u32), ("views_released", c_u32)]
 
 
 _PROTOS = {
@@ -81,6 +82,7 @@ _PROTOS = {
     "vgr_create_view": (c_i32, [c_vp, ctypes.POINTER(ViewOpts), ctypes.POINTER(c_vp)]),
     "vgr_destroy_view": (c_i32, [c_vp]),
     "vgr_reset_view": (c_i32, [c_vp]),
+    "vgr_view_set_tuning": (c_i32, [c_vp, c_u32, c_u32, c_u32, c_u32]),
     "vgr_view_device_bytes": (c_i32, [c_vp, ctypes.POINTER(c_u64)]),
     "vgr_render_frame": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, ctypes.POINTER(Frame)]),
     "vgr_render_frame_host": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp, ctypes.POINTER(Frame)]),

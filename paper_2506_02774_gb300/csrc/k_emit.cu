@@ -14,10 +14,10 @@
 // tile sort moves behind every real pair (which stay in depth order within
 // a tile, the sort being stable).  The slot's value is the Gaussian's index
 // in the in-front arrays << 8 | its row mask in that tile: bit w is set when
-// the footprint box reaches pixel row 2w or 2w+1 of the tile (the rows the
-// blend's warp w shades; outside the box the Eq. 4 test fails at every
-// pixel), so the blend reads only the records a warp needs, straight from
-// the in-front arrays.  Indices therefore take 24 bits: a frame with more
+// the footprint box reaches one of the tile's pixel rows w MR .. w MR + MR - 1,
+// MR = tile / 8 rows (1 for 8-pixel tiles); outside the box the Eq. 4 test
+// fails at every pixel, so the blend reads only the records a strip needs,
+// straight from the in-front arrays.  Indices therefore take 24 bits: a frame with more
 // cut nodes in front of the camera reports an overflow.  The digit
 // histograms of the tile sort are accumulated here as well.
 #include <cuda_fp16.h>
@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
     const uint32_t ntiles = (n_vis + EM_TILE - 1) / EM_TILE;
     const uint32_t epoch = fp->epoch;
     const uint32_t TW = fp->tiles_x;
+    const int T = (int)fp->tile;
+    const int MR = T >= 8 ? T / 8 : 1;  // tile rows per row-mask bit (8 bits)
     const float Wf = fp->width_f, Hf = fp->height_f;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     uint32_t kept = 0;
@@ -138,14 +140,14 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
                 keep = true;
                 if (!canonical) {
                     const float4 G = s_g[g], Hh = s_h[g];
-                    keep = tile_keep(G.x, G.y, G.z, G.w, Hh.x, Hh.y, Hh.z, Hh.w, tx, ty, Wf, Hf);
-                    // tile rows r with |row0 + r - v| <= half-height, as row pairs
-                    const float row0 = (float)(ty * TILE) + 0.5f, hh = __half2float(s_hh[g]);
+                    keep = tile_keep(G.x, G.y, G.z, G.w, Hh.x, Hh.y, Hh.z, Hh.w, tx, ty, Wf, Hf, T);
+                    // tile rows r with |row0 + r - v| <= half-height, as groups of MR rows
+                    const float row0 = (float)(ty * T) + 0.5f, hh = __half2float(s_hh[g]);
                     const float rlo = fmaxf(0.f, ceilf(G.y - hh - row0));
-                    const float rhi = fminf((float)(TILE - 1), floorf(G.y + hh - row0));
+                    const float rhi = fminf((float)(T - 1), floorf(G.y + hh - row0));
                     rows = 0u;
                     if (rlo <= rhi) {
-                        const uint32_t w0 = (uint32_t)rlo >> 1, w1 = (uint32_t)rhi >> 1;
+                        const uint32_t w0 = (uint32_t)rlo / MR, w1 = (uint32_t)rhi / MR;
                         rows = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
                     }
                 }
@@ -183,14 +185,15 @@ void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32
                                        tile_passes, sentinel, status, ctr, fp);
 }
 
-// Blend order: tiles by descending pair count (buckets of floor(log2(count+1)),
-// heaviest bucket first), so the long tiles start in the first wave and the
-// short ones fill in behind them.  One CTA; the order inside a bucket does
+// Blend order: tiles by descending pair count (classes of floor(log2(count+1)),
+// heaviest class first), so the long tiles start in the first round and the
+// short ones fill in behind them.  One CTA; the order inside a class does
 // not matter (tiles are independent).  It also finishes the ranges the last
 // tile-sort pass recorded as (start, ~end) by atomic minima from all ones:
-// each becomes [start, end), or [0, 0) for a tile without pairs.
+// each becomes [start, end), or [0, 0) for a tile without pairs.  The class
+// counts go to the frame's counters, for a batch's order over all its views.
 __global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges, uint32_t n_tiles,
-                                                     uint32_t* __restrict__ order) {
+                                                     uint32_t* __restrict__ order, Counters* __restrict__ ctr) {
     pdl_wait();
     __shared__ uint32_t s_cnt[33], s_start[33];
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges,
         atomicAdd(&s_cnt[32 - __clz(r.y - r.x + 1u)], 1u);
     }
     __syncthreads();
+    if (threadIdx.x < 33) ctr->tile_buckets[threadIdx.x] = s_cnt[threadIdx.x];
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int b = 32; b >= 0; --b) { s_start[b] = run; run += s_cnt[b]; }
@@ -213,8 +217,61 @@ __global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges,
     }
 }
 
-void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {
-    launch_k(k_tile_order, 1, 1024, s, ranges, n_tiles, order);
+void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, Counters* ctr, cudaStream_t s) {
+    launch_k(k_tile_order, 1, 1024, s, ranges, n_tiles, order, ctr);
+}
+
+// The blend order of a batch: the tiles of all its views by class, heaviest
+// first, each view's tiles of a class in that view's own order.  Class b of
+// view v starts at off(b, v) = (tiles of every view in the classes above b)
+// + (class-b tiles of the views before v); within view v's own order the
+// class starts at start(b, v) = (v's tiles in the classes above b), so a tile
+// at position p of v's order goes to p + off(b, v) - start(b, v): one CTA
+// computes that difference per (class, view), then a grid places the tiles.
+constexpr uint32_t BATCH_MAX_VIEWS = 1024;
+
+__global__ void __launch_bounds__(1024) k_batch_offsets(const FrameParams* const* __restrict__ fps, uint32_t n_views,
+                                                        uint32_t* __restrict__ delta) {
+    pdl_wait();
+    __shared__ uint32_t s_scan[33];
+    const uint32_t v = threadIdx.x;
+    const Counters* c = v < n_views ? fps[v]->bl_ctr : nullptr;
+    uint32_t run = 0, vstart = 0;
+    for (int b = 32; b >= 0; --b) {
+        const uint32_t cnt = c ? c->tile_buckets[b] : 0u;
+        uint32_t total;
+        const uint32_t pre = block_excl_scan<32>(cnt, s_scan, &total);
+        if (c) delta[(size_t)b * n_views + v] = run + pre - vstart;
+        vstart += cnt;
+        run += total;
+        __syncthreads();  // s_scan is reused by the next class
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_scatter(const FrameParams* const* __restrict__ fps, uint32_t n_views,
+                                                       const uint32_t* const* __restrict__ orders,
+                                                       const uint32_t* __restrict__ tile_base, uint32_t total,
+                                                       const uint32_t* __restrict__ delta, uint32_t* __restrict__ work) {
+    pdl_wait();
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n_views;  // the view v with tile_base[v] <= g < tile_base[v + 1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tile_base[mid] <= g) lo = mid; else hi = mid;
+        }
+        const uint32_t v = lo, p = g - tile_base[v];
+        const uint32_t t = orders[v][p];
+        const uint2 r = fps[v]->bl_ranges[t];
+        const uint32_t b = 32 - __clz(r.y - r.x + 1u);
+        work[p + delta[(size_t)b * n_views + v]] = (v << 20) | t;
+    }
+}
+
+void launch_batch_order(const FrameParams* const* fps, uint32_t n_views, const uint32_t* const* orders,
+                        const uint32_t* tile_base, uint32_t total_tiles, uint32_t* delta, uint32_t* work, int grid,
+                        cudaStream_t s) {
+    launch_k(k_batch_offsets, 1, BATCH_MAX_VIEWS, s, fps, n_views, delta);
+    launch_k(k_batch_scatter, grid, 256, s, fps, n_views, orders, tile_base, total_tiles, (const uint32_t*)delta, work);
 }
 
 }  // namespace vgr

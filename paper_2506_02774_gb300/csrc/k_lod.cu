@@ -36,7 +36,7 @@ namespace vgr {
 // m0^T S m0 <= lambda_max(S) |m0|^2 <= L |m0|^2, L the largest absolute row
 // sum of S (Gershgorin, stored per node at load); so with
 //   Bx = 3.34 sqrt(L (fx/z)^2 (1 + limx^2) + 0.3) + 0.01
-// a Gaussian with u + Bx < 0.5 or u - Bx > 16 tiles_x - 0.5 (or likewise in
+// a Gaussian with u + Bx < 0.5 or u - Bx > T tiles_x - 0.5 (or likewise in
 // v) has no candidate tile in preprocess and can be left out here.  The
 // canonical mode's 3-sigma box is bounded the same way.
 // Set bit n of bm in the lanes where pred holds, one atomic per run of lanes
@@ -162,8 +162,8 @@ __device__ __forceinline__ CutOut make_cut_out(const FrameParams* fp, const Scen
     o.fx = fp->fx; o.fy = fp->fy; o.cx = fp->cx; o.cy = fp->cy;
     o.kx = fp->fx * fp->fx * (1.0f + fp->limx * fp->limx);
     o.ky = fp->fy * fp->fy * (1.0f + fp->limy * fp->limy);
-    o.umax = (float)(TILE * fp->tiles_x) - 0.5f;
-    o.vmax = (float)(TILE * fp->tiles_y) - 0.5f;
+    o.umax = (float)(fp->tile * fp->tiles_x) - 0.5f;
+    o.vmax = (float)(fp->tile * fp->tiles_y) - 0.5f;
     o.canonical = fp->filter == VGR_FILTER_CANONICAL;
     o.interp = IP;  // a compile-time constant: the other form's code is not generated
     return o;

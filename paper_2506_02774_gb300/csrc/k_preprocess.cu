@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
     const float fx = fp->fx, fy = fp->fy, cx = fp->cx, cy = fp->cy, z_near = fp->z_near;
     const float limx = fp->limx, limy = fp->limy, Wf = fp->width_f, Hf = fp->height_f;
     const int TW = (int)fp->tiles_x, TH = (int)fp->tiles_y;
+    const float Tf = (float)fp->tile, iT = 1.0f / Tf;  // tile side (a power of two: exact)
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     const float lod_t = fp->lod_t;
     uint32_t n_visible = 0;
@@ -230,11 +231,11 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
                         const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
                         bx = by = ceilf(3.0f * sqrtf(lam));
                     }
-                    tx0 = max(0, (int)ceilf((u - bx - (TILE - 0.5f)) * (1.0f / TILE)));
-                    tx1 = min(TW - 1, (int)floorf((u + bx - 0.5f) * (1.0f / TILE)));
-                    ty0 = max(0, (int)ceilf((vv - by - (TILE - 0.5f)) * (1.0f / TILE)));
-                    ty1 = min(TH - 1, (int)floorf((vv + by - 0.5f) * (1.0f / TILE)));
-                    if (!(u - bx < Wf + TILE) || !(u + bx > -TILE) || !(vv - by < Hf + TILE) || !(vv + by > -TILE)) {
+                    tx0 = max(0, (int)ceilf((u - bx - (Tf - 0.5f)) * iT));
+                    tx1 = min(TW - 1, (int)floorf((u + bx - 0.5f) * iT));
+                    ty0 = max(0, (int)ceilf((vv - by - (Tf - 0.5f)) * iT));
+                    ty1 = min(TH - 1, (int)floorf((vv + by - 0.5f) * iT));
+                    if (!(u - bx < Wf + Tf) || !(u + bx > -Tf) || !(vv - by < Hf + Tf) || !(vv + by > -Tf)) {
                         tx1 = -1;  // far outside (also guards the float->int conversions)
                     }
                     if (tx0 > tx1 || ty0 > ty1) v = false;

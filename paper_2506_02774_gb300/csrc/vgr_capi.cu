@@ -212,6 +212,8 @@ void vgr_default_view_opts(vgr_view_opts* o) {
     o->lod_frustum = 0;
     o->lod_frustum_guard = 2.0f;
     o->lod_interp = 0;
+    o->blend_depth = 32;
+    o->tile_size = TILE_DEFAULT;
 }
 
 // ------------------------------------------------------------- hierarchy
@@ -470,7 +472,15 @@ struct BatchGraph {
     std::vector<uint64_t> key;
     cudaGraphExec_t exec = nullptr;
     uint64_t last_use = 0;
+    void* dev = nullptr;  // the batch blend's view table and work list
 };
+
+void destroy_batch(BatchGraph& b) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.dev) cudaFree(b.dev);
+    b.exec = nullptr;
+    b.dev = nullptr;
+}
 std::mutex g_batch_mu;
 std::vector<BatchGraph> g_batches;
 uint64_t g_batch_clock = 0;
@@ -483,7 +493,7 @@ void forget_batches(uint64_t uid) {
         for (size_t k = 0; k < g_batches[i].key.size(); k += 6)
             if (g_batches[i].key[k] == uid) hit = true;
         if (hit) {
-            cudaGraphExecDestroy(g_batches[i].exec);
+            destroy_batch(g_batches[i]);
             g_batches.erase(g_batches.begin() + (long)i);
         } else {
             ++i;
@@ -584,8 +594,12 @@ vgr_status alloc_status(vgr_view* v) {
     return s;
 }
 
+uint32_t tile_of(const vgr_view* v) { return v->opts.tile_size ? v->opts.tile_size : TILE_DEFAULT; }
+uint32_t tiles_for(uint32_t W, uint32_t H, uint32_t T) { return ((W + T - 1) / T) * ((H + T - 1) / T); }
+
 vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
-    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
+    const uint32_t T = tile_of(v);
+    const uint32_t TW = (W + T - 1) / T, TH = (H + T - 1) / T;
     const uint64_t px = (uint64_t)W * H, tiles = (uint64_t)TW * TH;
     if (px <= v->cap_pixels && tiles <= v->cap_tiles) return VGR_OK;
     drop_graphs(v);
@@ -648,6 +662,20 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     if (v->opts.lut_size == 0) v->opts.lut_size = 32;
     if (v->opts.lut_size > 256) { delete v; return fail(VGR_E_INVALID, "lut_size must be <= 256"); }
     if (v->opts.lod_budget == 0) v->opts.lod_budget = 4096;
+    if (v->opts.blend_depth == 0) v->opts.blend_depth = 32;
+    if (v->opts.tile_size == 0) v->opts.tile_size = TILE_DEFAULT;
+    if (v->opts.blend_depth != 16 && v->opts.blend_depth != 32 && v->opts.blend_depth != 48) {
+        delete v;
+        return fail(VGR_E_INVALID, "blend_depth must be 16, 32 or 48");
+    }
+    if (v->opts.tile_size != 8 && v->opts.tile_size != 16 && v->opts.tile_size != 32) {
+        delete v;
+        return fail(VGR_E_INVALID, "tile_size must be 8, 16 or 32");
+    }
+    if (v->opts.tile_size == 8 && v->opts.blend_depth == 48) {
+        delete v;
+        return fail(VGR_E_INVALID, "blend_depth 48 needs tiles of 16 or 32 pixels");
+    }
     if (v->opts.lod_frustum && !h->box) {
         delete v;
         return fail(VGR_E_INVALID, "lod_frustum needs node boxes (vgr_scene_desc.bbox)");
@@ -738,6 +766,25 @@ vgr_status vgr_destroy_view(vgr_view* v) {
     return VGR_OK;
 }
 
+vgr_status vgr_view_set_tuning(vgr_view* v, uint32_t grid_wide, uint32_t grid_scan, uint32_t blend_depth,
+                               uint32_t tile_size) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is in flight");
+    if (blend_depth != 0 && blend_depth != 16 && blend_depth != 32 && blend_depth != 48)
+        return fail(VGR_E_INVALID, "blend_depth must be 0, 16, 32 or 48");
+    if (tile_size != 0 && tile_size != 8 && tile_size != 16 && tile_size != 32)
+        return fail(VGR_E_INVALID, "tile_size must be 0, 8, 16 or 32");
+    const uint32_t d = blend_depth ? blend_depth : v->opts.blend_depth;
+    const uint32_t t = tile_size ? tile_size : v->opts.tile_size;
+    if (t == 8 && d == 48) return fail(VGR_E_INVALID, "blend_depth 48 needs tiles of 16 or 32 pixels");
+    if (grid_wide) v->grid_wide = (int)std::min<uint32_t>(grid_wide, 1u << 16);
+    if (grid_scan) v->grid_scan = (int)std::min<uint32_t>(grid_scan, 1u << 16);
+    v->opts.blend_depth = d;
+    v->opts.tile_size = t;
+    drop_graphs(v);  // captured frames hold the old launch shapes
+    return VGR_OK;
+}
+
 vgr_status vgr_reset_view(vgr_view* v) {
     if (!v) return fail(VGR_E_INVALID, "null view");
     if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is in flight");
@@ -763,7 +810,8 @@ vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* 
     const uint64_t RT = radix_tile();
     const uint64_t status_words = 2 * (cut_compact_tiles((uint32_t)n_words) + 1) + ceil_div(cap_vis, emit_tile()) + 1 +
                                   4 * (ceil_div(cap_vis, RT) + 1) * 256 + 4 * (ceil_div(cap_pairs, RT) + 1) * 256;
-    const uint64_t tiles = (uint64_t)((width + TILE - 1) / TILE) * ((height + TILE - 1) / TILE);
+    const uint32_t T = o.tile_size ? o.tile_size : TILE_DEFAULT;
+    const uint64_t tiles = (uint64_t)((width + T - 1) / T) * ((height + T - 1) / T);
     uint64_t b = 3 * 4 * cap_cut + per_vis * cap_vis + 4 * 4 * cap_pairs + 2 * 4 * n_words + 2 * 4 * N +
                  sizeof(Counters) + sizeof(ViewState) + sizeof(FrameParams) + 260 * 4 + 8 * status_words;
     b += (uint64_t)width * height * 3 * 4 + tiles * (sizeof(uint2) + 4);
@@ -799,11 +847,19 @@ uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
            1u /*emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
 }
 
+// The frame's status block and cut sizes, read back after its last kernel.
+void frame_readback(vgr_view* v, cudaStream_t s) {
+    cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
+}
+
 // Enqueue one frame.  'scratch' selects the top-down cut; 'captured': the
 // frame is being captured into a graph, where the colour pass runs on the
 // side stream (launched one by one, the extra stream calls cost more host
-// time than the overlap saves).  Returns the number of kernels launched.
-uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured) {
+// time than the overlap saves).  'own_blend' false: the frame stops before
+// the blend, which a batch runs over all its views (frame_readback then
+// follows that blend).  Returns the number of kernels launched.
+uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured, bool own_blend = true) {
     const SceneDev& sc = v->h->dev;
     cudaStream_t s = v->stream;
     const bool timing = v->opts.timing != 0;
@@ -877,20 +933,20 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
                           v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
                           v->fp_dev, v->ctr, v->grid_scan, s, 1, last ? v->ranges : nullptr, n_tiles);
     }
-    const int fb = tile_passes & 1;
-    v->last_tile_buf = fb;
+    v->last_tile_buf = tile_passes & 1;
     mark(VGR_STAGE_RANGES);
-    launch_tile_order(v->ranges, n_tiles, v->tile_order, s);
-    mark(VGR_STAGE_BLEND);
+    launch_tile_order(v->ranges, n_tiles, v->tile_order, v->ctr, s);
     if (side) {
-        cudaStreamWaitEvent(s, v->side_join, 0);
+        cudaStreamWaitEvent(s, v->side_join, 0);  // the colour pass is done
         pdl_state().plain_next = true;
     }
-    launch_blend(n_tiles, v->tile_order, v->ranges, v->pairV[fb], v->vis.recA, v->vis.recB, v->vis.rgb, v->fp_dev, v->lut, v->image, v->ctr,
-                 v->opts.filter, v->opts.exp_mode, s);
+    if (!own_blend) return frame_kernels(v, scratch, tile_passes) - 1u;  // a batch blend follows
+    mark(VGR_STAGE_BLEND);
+    launch_blend(v->fp_dev, nullptr, v->tile_order, n_tiles, &v->ctr->blend_next,
+                 v->h->num_sms * blend_ctas_per_sm(v->opts.filter, v->opts.exp_mode, v->opts.blend_depth, fh.tile),
+                 v->opts.filter, v->opts.exp_mode, v->opts.blend_depth, fh.tile, s);
     mark(VGR_N_STAGES);
-    cudaMemcpyAsync(v->ctr_host, v->ctr, COUNTERS_HEAD, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
+    frame_readback(v, s);
     return frame_kernels(v, scratch, tile_passes);
 }
 
@@ -990,7 +1046,7 @@ void frustum_planes(const vgr_camera* cam, float guard, float out[5][4]) {
     }
 }
 
-void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* host_dev) {
+void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* host_dev, int tile_passes) {
     const uint32_t W = cam->width, H = cam->height;
     FrameParams& p = *v->fp_host;
     memcpy(p.R, cam->R, sizeof(p.R));
@@ -1002,7 +1058,8 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* ho
     p.limy = 1.3f * (0.5f * (float)H / cam->fy);
     p.width_f = (float)W; p.height_f = (float)H;
     p.width = W; p.height = H;
-    p.tiles_x = (W + TILE - 1) / TILE; p.tiles_y = (H + TILE - 1) / TILE;
+    p.tile = tile_of(v);
+    p.tiles_x = (W + p.tile - 1) / p.tile; p.tiles_y = (H + p.tile - 1) / p.tile;
     p.epoch = ++v->epoch;  // fresh look-back tags for every launch sequence
     if ((p.epoch & 0x3FFFFFFFu) == 0) p.epoch = ++v->epoch;
     p.filter = v->opts.filter; p.exp_mode = v->opts.exp_mode; p.lut_size = v->opts.lut_size;
@@ -1015,6 +1072,16 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* ho
     p.lod_interp = v->opts.lod_interp ? 1u : 0u;
     p.lod_t = t;
     if (p.lod_frustum) frustum_planes(cam, v->opts.lod_frustum_guard, p.frustum);
+    // the blend's buffers: the tile sort's last pass leaves the pairs in
+    // buffer (passes & 1)
+    p.bl_ranges = v->ranges;
+    p.bl_pair_val = v->pairV[tile_passes & 1];
+    p.bl_recA = v->vis.recA;
+    p.bl_recB = v->vis.recB;
+    p.bl_rgb = v->vis.rgb;
+    p.bl_lut = v->lut;
+    p.bl_image = v->image;
+    p.bl_ctr = v->ctr;
 }
 
 // Enqueue the frame (and the image copy to host_rgb, if given) and record the
@@ -1029,8 +1096,11 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
     if (s != VGR_OK) return s;
     VGR_CK(cudaSetDevice(v->h->device));
     const uint32_t W = cam->width, H = cam->height;
+    const uint32_t T = tile_of(v);
+    if (T == 8 && (W > 8192 || H > 8192))
+        return fail(VGR_E_INVALID, "8-pixel tiles need an image of at most 8192 x 8192");
     if ((s = ensure_image(v, W, H)) != VGR_OK) return s;
-    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
+    const uint32_t TW = (W + T - 1) / T, TH = (H + T - 1) / T;
     PendingFrame& q = v->pend;
     q = PendingFrame{};
     q.cam = *cam;
@@ -1045,7 +1115,7 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
     q.k = k;
     q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
     q.host_dev = mapped_host(v, host_rgb);
-    fill_params(v, cam, q.t, q.k, q.host_dev);
+    fill_params(v, cam, q.t, q.k, q.host_dev, q.tile_passes);
     return VGR_OK;
 }
 
@@ -1072,8 +1142,9 @@ vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* hos
     vgr_status s = prepare_frame(v, cam, tau, host_rgb);
     if (s != VGR_OK) return s;
     PendingFrame& q = v->pend;
-    const uint32_t TW = (q.cam.width + TILE - 1) / TILE, TH = (q.cam.height + TILE - 1) / TILE;
-    if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
+    if ((s = run_frame(v, q.scratch, q.tile_passes, tiles_for(q.cam.width, q.cam.height, tile_of(v)), &q.kernels)) !=
+        VGR_OK)
+        return s;
     return close_frame(v, v->stream);
 }
 
@@ -1084,8 +1155,29 @@ struct BatchStream {
 };
 BatchStream g_bstream[64];
 
+// Views whose blend joins the batch's single blend launch: the exact
+// exponential and the preemptive filter (the kernel's default mode), at the
+// first such view's staging depth and tile size, at most BATCH_VIEWS_MAX of
+// them; the others blend in their own branch.
+std::vector<uint32_t> batch_blend_views(vgr_view* const* views, uint32_t n) {
+    std::vector<uint32_t> sh;
+    uint32_t depth = 0, tile = 0;
+    for (uint32_t i = 0; i < n && sh.size() < BATCH_VIEWS_MAX; ++i) {
+        const vgr_view_opts& o = views[i]->opts;
+        if (o.filter != VGR_FILTER_PREEMPTIVE || o.exp_mode != VGR_EXP_EXACT) continue;
+        if (!depth) {
+            depth = o.blend_depth;
+            tile = o.tile_size;
+        }
+        if (o.blend_depth == depth && o.tile_size == tile) sh.push_back(i);
+    }
+    return sh;
+}
+
 // All views prepared: run their frames as one captured graph (captured on
-// first use of this combination).
+// first use of this combination).  Each view's frame up to its tile order is
+// a parallel branch on the view's stream; then one launch orders the tiles
+// of all the views heaviest first and one persistent blend shades them all.
 vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
     NvtxRange r("vgr batch graph");
     const int dev = views[0]->h->device;
@@ -1101,23 +1193,77 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
     for (uint32_t i = 0; i < n; ++i) {
         const vgr_view* v = views[i];
         const PendingFrame& q = v->pend;
-        const uint64_t tiles = (uint64_t)((q.cam.width + TILE - 1) / TILE) * ((q.cam.height + TILE - 1) / TILE);
+        const uint64_t tiles = tiles_for(q.cam.width, q.cam.height, tile_of(v));
         key.insert(key.end(), {v->uid, v->gen, (uint64_t)q.scratch, (uint64_t)v->parity, tiles,
                                (uint64_t)q.tile_passes});
     }
+    const std::vector<uint32_t> sh = batch_blend_views(views, n);
+    std::vector<char> shared(n, 0);
+    for (uint32_t i : sh) shared[i] = 1;
     BatchGraph* bg = nullptr;
     for (auto& b : g_batches)
         if (b.key == key) bg = &b;
     if (!bg) {
+        // the batch blend's table: per shared view its frame parameters and
+        // tile order, the first tile of each view in the batch's tile count,
+        // the per-(class, view) offsets, and the work list
+        const uint32_t ns = (uint32_t)sh.size();
+        std::vector<const FrameParams*> fps(ns);
+        std::vector<const uint32_t*> orders(ns);
+        std::vector<uint32_t> base(ns + 1, 0);
+        for (uint32_t j = 0; j < ns; ++j) {
+            const vgr_view* v = views[sh[j]];
+            const uint32_t tiles = tiles_for(v->pend.cam.width, v->pend.cam.height, tile_of(v));
+            fps[j] = v->fp_dev;
+            orders[j] = v->tile_order;
+            base[j + 1] = base[j] + tiles;
+        }
+        const uint32_t total = base[ns];
+        const size_t off_orders = 8 * (size_t)ns, off_base = 16 * (size_t)ns,
+                     off_delta = (off_base + 4 * (size_t)(ns + 1) + 15) / 16 * 16,
+                     off_work = off_delta + 4 * 33 * (size_t)ns, off_next = off_work + 4 * (size_t)total,
+                     bytes = off_next + 16;
+        void* devbuf = nullptr;
+        if (ns) {
+            cudaError_t e = cudaMalloc(&devbuf, bytes);
+            if (e == cudaSuccess) e = cudaMemcpy(devbuf, fps.data(), 8 * (size_t)ns, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy((char*)devbuf + off_orders, orders.data(), 8 * (size_t)ns, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy((char*)devbuf + off_base, base.data(), 4 * (size_t)(ns + 1), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                if (devbuf) cudaFree(devbuf);
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? VGR_E_NOMEM : VGR_E_CUDA, "batch blend table: %s",
+                            cudaGetErrorString(e));
+            }
+        }
         VGR_CK(cudaStreamBeginCapture(bs.s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaEventRecord(bs.fork, bs.s);
         for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
             vgr_view* v = views[i];
             e = cudaStreamWaitEvent(v->stream, bs.fork, 0);
             if (e != cudaSuccess) break;
-            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, true);
+            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, true, !shared[i]);
             e = cudaEventRecord(v->join_ev, v->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
+        }
+        if (e == cudaSuccess && ns) {
+            PdlScope pdl(true);  // the first kernel follows the joins in plain stream order
+            auto* fps_d = reinterpret_cast<const FrameParams* const*>(devbuf);
+            auto* orders_d = reinterpret_cast<const uint32_t* const*>((char*)devbuf + off_orders);
+            auto* base_d = reinterpret_cast<const uint32_t*>((char*)devbuf + off_base);
+            auto* delta_d = reinterpret_cast<uint32_t*>((char*)devbuf + off_delta);
+            auto* work_d = reinterpret_cast<uint32_t*>((char*)devbuf + off_work);
+            auto* next_d = reinterpret_cast<uint32_t*>((char*)devbuf + off_next);
+            const vgr_view* v0 = views[sh[0]];
+            const uint32_t d = v0->opts.blend_depth, t = v0->opts.tile_size;
+            e = cudaMemsetAsync(next_d, 0, sizeof(uint32_t), bs.s);  // the blend's tile counter
+            launch_batch_order(fps_d, ns, orders_d, base_d, total, delta_d, work_d, v0->h->num_sms * 4, bs.s);
+            launch_blend(v0->fp_dev, fps_d, work_d, total, next_d,
+                         v0->h->num_sms * blend_ctas_per_sm(VGR_FILTER_PREEMPTIVE, VGR_EXP_EXACT, d, t),
+                         VGR_FILTER_PREEMPTIVE, VGR_EXP_EXACT, d, t, bs.s);
+            for (uint32_t j = 0; j < ns; ++j) frame_readback(views[sh[j]], bs.s);
         }
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(bs.s, &g);
@@ -1128,16 +1274,17 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            if (devbuf) cudaFree(devbuf);
             return fail(VGR_E_CUDA, "batch capture: %s", cudaGetErrorString(e));
         }
         if (g_batches.size() >= BATCH_GRAPHS_KEPT) {  // evict the least recently used
             size_t old = 0;
             for (size_t i = 1; i < g_batches.size(); ++i)
                 if (g_batches[i].last_use < g_batches[old].last_use) old = i;
-            cudaGraphExecDestroy(g_batches[old].exec);
+            destroy_batch(g_batches[old]);
             g_batches.erase(g_batches.begin() + (long)old);
         }
-        g_batches.push_back(BatchGraph{key, exec, 0});
+        g_batches.push_back(BatchGraph{key, exec, 0, devbuf});
         bg = &g_batches.back();
     }
     bg->last_use = ++g_batch_clock;
@@ -1145,7 +1292,8 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
     for (uint32_t i = 0; i < n; ++i) {
         vgr_view* v = views[i];
         v->last_tile_buf = v->pend.tile_passes & 1;
-        v->pend.kernels += frame_kernels(v, v->pend.scratch, v->pend.tile_passes);
+        v->pend.kernels += frame_kernels(v, v->pend.scratch, v->pend.tile_passes) - (shared[i] ? 1u : 0u);
+        if (!sh.empty() && i == sh[0]) v->pend.kernels += 3u;  // class offsets, tile placement, the batch blend
         vgr_status s = close_frame(v, bs.s);
         if (s != VGR_OK) return s;
     }
@@ -1163,7 +1311,8 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
     VGR_CK(cudaSetDevice(v->h->device));
     PendingFrame& q = v->pend;
     const uint32_t W = q.cam.width, H = q.cam.height;
-    const uint32_t TW = (W + TILE - 1) / TILE, TH = (H + TILE - 1) / TILE;
+    const uint32_t T = tile_of(v);
+    const uint32_t TW = (W + T - 1) / T, TH = (H + T - 1) / T;
     const Counters* ch = reinterpret_cast<const Counters*>(v->ctr_host);
     VGR_CK(cudaEventSynchronize(v->done_ev));
     vgr_status s = VGR_OK;
@@ -1203,7 +1352,7 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         if (!again) break;
         if (attempt >= 12) return fail(VGR_E_OVERFLOW, "frame did not settle after %d replays", attempt + 1);
         ++replays;
-        fill_params(v, &q.cam, q.t, q.k, q.host_dev);
+        fill_params(v, &q.cam, q.t, q.k, q.host_dev, q.tile_passes);
         if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
         if (q.host && !q.host_dev)
             VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
@@ -1365,6 +1514,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     o->pair_tile = v->pairK[v->last_tile_buf];
     o->pair_val = v->pairV[v->last_tile_buf];
     o->tile_range = reinterpret_cast<const uint32_t*>(v->ranges);
+    o->tile_size = tile_of(v);
     return VGR_OK;
 }
 

@@ -10,7 +10,7 @@
 
 namespace vgr {
 
-constexpr int TILE = 16;                      // 16x16-pixel tiles
+constexpr int TILE_DEFAULT = 16;              // tiles of 16 x 16 pixels unless a view asks for 8 or 32
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr float ALPHA_MIN = 1.0f / 255.0f;    // alpha* (Sec. 3.1 'Rasterization')
 constexpr float LN_ALPHA_MIN = -5.5412635451584260f;  // ln(1/255)
@@ -41,6 +41,8 @@ enum : uint32_t {
 // ticket slots (dynamic tile order for the chained scans)
 enum : int { TK_COMPACT = 0, TK_PRE = 1, TK_EMIT = 2, TK_SORT0 = 3 /* .. TK_SORT0 + 7 */, TK_COUNT = 12 };
 
+struct Counters;
+
 // Per-frame parameters, uploaded once per frame (a graph replays them).
 struct FrameParams {
     float R[9];
@@ -51,6 +53,7 @@ struct FrameParams {
     float limx, limy;  // 1.3 (W/2)/fx, 1.3 (H/2)/fy
     float width_f, height_f;
     uint32_t width, height, tiles_x, tiles_y;
+    uint32_t tile;        // tile side in pixels: 8, 16 or 32
     uint32_t epoch;    // tags look-back words; new value per launch sequence
     uint32_t filter, exp_mode, lut_size;
     float lut_step;    // 5.55 / m
@@ -63,6 +66,16 @@ struct FrameParams {
     float lod_t;          // fl(tau / f), the size ratio the interpolation weight is measured against
     // its planes: world normal w (xyz) and offset o (w), inside iff w.x - o >= 0 (read as float4)
     alignas(16) float frustum[5][4];
+    // the buffers the blend reads and writes for this frame (a batch's blend
+    // reaches every view's through these)
+    const uint2* bl_ranges;      // [tiles] pair range of each tile
+    const uint32_t* bl_pair_val; // sorted pair values (in-front index << 8 | row mask)
+    const float4* bl_recA;
+    const float4* bl_recB;
+    const float4* bl_rgb;
+    const float* bl_lut;         // Eq. 5 table (m + 1 entries)
+    float* bl_image;             // H x W x 3
+    Counters* bl_ctr;
 };
 
 // Zeroed at the start of every frame.  Scalars first: the host reads back
@@ -81,6 +94,8 @@ struct Counters {
     uint32_t frontier_n[MAX_TREE_DEPTH + 2];
     uint32_t depth_hist[4][256];
     uint32_t tile_hist[4][256];
+    uint32_t tile_buckets[33];  // tiles per log2(pairs + 1) class (the blend order)
+    uint32_t blend_next;        // the blend's next tile in its work list
 };
 constexpr size_t COUNTERS_HEAD = 56;  // bytes read back per frame (n_vis .. pix_contribs)
 

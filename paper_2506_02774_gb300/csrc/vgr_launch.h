@@ -106,12 +106,23 @@ void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
 void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
                  unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
 uint32_t emit_tile();
-void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
+void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, Counters* ctr, cudaStream_t s);
+constexpr uint32_t BATCH_VIEWS_MAX = 1024;  // views of one batch blend (k_batch_offsets: one thread each)
 
-// k_blend.cu
-void launch_blend(uint32_t n_tiles, const uint32_t* tile_order, const uint2* ranges, const uint32_t* pair_val,
-                  const float4* recA, const float4* recB, const float4* rgb, const FrameParams* fp, const float* lut, float* image,
-                  Counters* ctr, uint32_t filter, uint32_t exp_mode, cudaStream_t s);
+// k_blend.cu: the persistent blend over a work list of (view << 20 | tile)
+// items in blend order; fps == null: every item is of the view of fp0.  'next'
+// (zero before the launch) hands out the list's tiles.  grid = SMs x
+// blend_ctas_per_sm(...); depth: hits staged per chunk (16, 32, 48; 48 needs
+// tiles of 16 or 32); tile: 8, 16 or 32 pixels.
+void launch_blend(const FrameParams* fp0, const FrameParams* const* fps, const uint32_t* work, uint32_t n_work,
+                  uint32_t* next, int grid, uint32_t filter, uint32_t exp_mode, uint32_t depth, uint32_t tile,
+                  cudaStream_t s);
+int blend_ctas_per_sm(uint32_t filter, uint32_t exp_mode, uint32_t depth, uint32_t tile);
+// k_emit.cu: the order of a batch's tiles over all its views (heaviest class
+// first), from each view's tile order and class counts
+void launch_batch_order(const FrameParams* const* fps, uint32_t n_views, const uint32_t* const* orders,
+                        const uint32_t* tile_base, uint32_t total_tiles, uint32_t* delta, uint32_t* work,
+                        int grid, cudaStream_t s);
 
 // vgr_sort_api.cu: enqueue a standalone pair sort on caller-provided scratch
 size_t sort_status_words(uint64_t n, int passes);

@@ -8,8 +8,10 @@
 // own streams, and a request starts as soon as a slot (a frame in flight) is
 // free: it does not wait for a batch to fill or drain.  Admission compares
 // the free device memory with the view's estimated footprint at the
-// request's image size plus a reserve.  The paper serves one view; nothing
-// here has a counterpart in it.
+// request's image size plus a reserve; when memory is short it releases idle
+// clients' views (least recently used first), and a request that still does
+// not fit waits in the queue until a frame completes.  The paper serves one
+// view; nothing here has a counterpart in it.
 //
 // Host code only: the frames themselves go through vgr_submit_frame /
 // vgr_frame_done / vgr_finish_frame.
@@ -40,10 +42,27 @@ namespace {
 
 using clock_type = std::chrono::steady_clock;
 
-vgr_status admit(vgr_server* sv, uint32_t c, const vgr_camera& cam) {
+// Per-trace scheduling state the admission step reads.
+struct TraceState {
+    std::vector<int64_t> inflight;   // request index in flight per client, -1 if none
+    std::vector<uint32_t> queued;    // arrived, not started requests per client
+    std::vector<uint64_t> last_use;  // completion tick of the client's last frame (LRU order)
+};
+
+// The least recently used client (other than c) whose view is idle: no frame
+// in flight and no request waiting for it; -1 if there is none.
+int64_t lru_idle(const vgr_server* sv, const TraceState& ts, uint32_t c) {
+    int64_t best = -1;
+    for (uint32_t j = 0; j < sv->clients.size(); ++j) {
+        if (j == c || !sv->clients[j].view || ts.inflight[j] >= 0 || ts.queued[j] > 0) continue;
+        if (best < 0 || ts.last_use[j] < ts.last_use[(size_t)best]) best = j;
+    }
+    return best;
+}
+
+vgr_status admit(vgr_server* sv, uint32_t c, const vgr_camera& cam, const TraceState& ts, uint32_t* released) {
     vgr_server::Client& cl = sv->clients[c];
-    const size_t need_floats = (size_t)cam.width * cam.height * 3;
-    if (!cl.view) {
+    while (!cl.view) {
         uint64_t est = 0;
         vgr_status s = vgr_view_bytes_estimate(sv->h, &sv->opts.view, cam.width, cam.height, &est);
         if (s != VGR_OK) return s;
@@ -52,20 +71,37 @@ vgr_status admit(vgr_server* sv, uint32_t c, const vgr_camera& cam) {
             vgr::set_last_error("cudaMemGetInfo failed");
             return VGR_E_CUDA;
         }
-        if ((uint64_t)free_b < est + sv->opts.hbm_reserve) {
+        bool fits = (uint64_t)free_b >= est + sv->opts.hbm_reserve;
+        if (fits) {
+            vgr_view_opts vo = sv->opts.view;
+            vo.stream = nullptr;  // every client gets its own stream
+            vo.timing = 0;
+            s = vgr_create_view(sv->h, &vo, &cl.view);
+            if (s == VGR_OK) break;
+            if (s != VGR_E_NOMEM) return s;
+            cl.view = nullptr;  // the estimate was short: same as not fitting
+        }
+        const int64_t j = sv->opts.evict_idle ? lru_idle(sv, ts, c) : -1;
+        if (j < 0) {
             vgr::set_last_error("admission: not enough free device memory for this client's view");
             return VGR_E_NOMEM;
         }
-        vgr_view_opts vo = sv->opts.view;
-        vo.stream = nullptr;  // every client gets its own stream
-        vo.timing = 0;
-        if ((s = vgr_create_view(sv->h, &vo, &cl.view)) != VGR_OK) return s;
+        vgr_destroy_view(sv->clients[(size_t)j].view);  // waits for its stream, frees its buffers
+        sv->clients[(size_t)j].view = nullptr;
+        ++*released;
     }
+    return VGR_OK;
+}
+
+vgr_status host_buffer(vgr_server* sv, uint32_t c, const vgr_camera& cam) {
+    vgr_server::Client& cl = sv->clients[c];
+    const size_t need_floats = (size_t)cam.width * cam.height * 3;
     if (sv->opts.host_images && cl.host_floats < need_floats) {
         if (cl.host) cudaFreeHost(cl.host);
         cl.host = nullptr;
         cl.host_floats = 0;
         if (cudaMallocHost((void**)&cl.host, need_floats * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
             vgr::set_last_error("pinned host image buffer");
             return VGR_E_NOMEM;
         }
@@ -87,6 +123,7 @@ void vgr_default_serve_opts(vgr_serve_opts* o) {
     o->hbm_reserve = 1ull << 30;
     vgr_default_view_opts(&o->view);
     o->view.use_graph = 1;
+    o->evict_idle = 1;
 }
 
 vgr_status vgr_create_server(vgr_hierarchy* h, const vgr_serve_opts* opts, vgr_server** out) {
@@ -150,8 +187,15 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
     for (uint32_t i = 0; i < n; ++i) res[i] = vgr_request_result{};
     nvtxRangePushA("vgr serve trace");
     const uint32_t C = (uint32_t)sv->clients.size();
-    std::vector<int64_t> inflight(C, -1);  // request index in flight per client
+    TraceState ts;
+    ts.inflight.assign(C, -1);
+    ts.queued.assign(C, 0);
+    ts.last_use.assign(C, 0);
     std::deque<uint32_t> arrived;          // arrived and not started, arrival order
+    // completion count when a request last failed admission for memory: it is
+    // tried again only after another frame has completed
+    std::vector<uint64_t> mem_wait(n, UINT64_MAX);
+    uint64_t completions = 0;
     uint32_t next = 0, done = 0, n_inflight = 0;
     vgr_status first_err = VGR_OK;
     const auto t0 = clock_type::now();
@@ -162,18 +206,19 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
         double now = now_s();
         while (next < n && reqs[next].arrival_s <= now) {
             arrived.push_back(next);
+            ++ts.queued[reqs[next].client];
             ++next;
             progress = true;
         }
         // completions
         for (uint32_t c = 0; c < C && n_inflight; ++c) {
-            if (inflight[c] < 0) continue;
+            if (ts.inflight[c] < 0) continue;
             int fin = 0;
             vgr_status s = vgr_frame_done(sv->clients[c].view, &fin);
             if (s == VGR_OK && !fin) continue;
             vgr_frame fr;
             if (s == VGR_OK) s = vgr_finish_frame(sv->clients[c].view, &fr);
-            vgr_request_result& r = res[inflight[c]];
+            vgr_request_result& r = res[ts.inflight[c]];
             r.finish_s = now_s();
             r.status = s;
             if (s == VGR_OK) {
@@ -185,7 +230,8 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
             } else if (first_err == VGR_OK) {
                 first_err = s;
             }
-            inflight[c] = -1;
+            ts.inflight[c] = -1;
+            ts.last_use[c] = ++completions;
             --n_inflight;
             ++done;
             progress = true;
@@ -194,23 +240,35 @@ vgr_status vgr_serve_trace(vgr_server* sv, const vgr_request* reqs, uint32_t n, 
         for (auto it = arrived.begin(); it != arrived.end() && n_inflight < sv->opts.max_inflight;) {
             const uint32_t i = *it;
             const uint32_t c = reqs[i].client;
-            if (inflight[c] >= 0) { ++it; continue; }
-            it = arrived.erase(it);
+            if (ts.inflight[c] >= 0 || mem_wait[i] == completions) { ++it; continue; }
             vgr_request_result& r = res[i];
-            r.start_s = now_s();
-            vgr_status s = admit(sv, c, reqs[i].cam);
-            if (s == VGR_OK)
-                s = vgr_submit_frame(sv->clients[c].view, &reqs[i].cam, reqs[i].tau,
-                                     sv->opts.host_images ? sv->clients[c].host : nullptr);
+            vgr_status s = admit(sv, c, reqs[i].cam, ts, &r.views_released);
+            if (s == VGR_OK) s = host_buffer(sv, c, reqs[i].cam);
+            float* dst = reqs[i].host_rgb ? reqs[i].host_rgb : (sv->opts.host_images ? sv->clients[c].host : nullptr);
+            if (s == VGR_OK) {
+                r.start_s = now_s();
+                s = vgr_submit_frame(sv->clients[c].view, &reqs[i].cam, reqs[i].tau, dst);
+            }
+            if (s == VGR_E_NOMEM && n_inflight > 0) {
+                // memory frees up as frames complete: keep the request queued
+                if (mem_wait[i] == UINT64_MAX) ++r.admission_waits;
+                mem_wait[i] = completions;
+                ++it;
+                continue;
+            }
+            it = arrived.erase(it);
+            --ts.queued[c];
             progress = true;
             if (s != VGR_OK) {
+                if (r.start_s == 0.0) r.start_s = now_s();
                 r.finish_s = now_s();
                 r.status = s;
                 ++done;
                 if (s != VGR_E_NOMEM && first_err == VGR_OK) first_err = s;  // refusals are results
                 continue;
             }
-            inflight[c] = i;
+            if (mem_wait[i] != UINT64_MAX) mem_wait[i] = UINT64_MAX;
+            ts.inflight[c] = i;
             ++n_inflight;
         }
         if (!progress) {

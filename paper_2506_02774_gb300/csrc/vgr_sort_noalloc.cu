@@ -74,7 +74,9 @@ extern "C" vgr_status vgr_sort_pairs_noalloc(const uint32_t* keys_in, const uint
             void* p = nullptr;
             if ((e = cudaGetSymbolAddress(&p, g_sort_scratch)) != cudaSuccess)
                 return na_fail(VGR_E_CUDA, "cudaGetSymbolAddress of the sort scratch", e);
-            if ((e = cudaMemsetAsync(p, 0, NA_BYTES, s)) != cudaSuccess)
+            // the clear is waited for here, once, so that a later call on any
+            // other stream is ordered after it
+            if ((e = cudaMemsetAsync(p, 0, NA_BYTES, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
                 return na_fail(VGR_E_CUDA, "clearing the sort scratch", e);
             int sms = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -24,12 +24,13 @@ __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fm
 // rho is a concave quadratic in the free coordinate: on the edges x = x0, x1
 // its optimum is dy* = (-b/c) dx = ry dx, on y = y0, y1 it is
 // dx* = (-b/a) dy = rx dy, each clamped to the edge.
+// T is the tile side in pixels (8, 16 or 32): every coordinate below is exact in FP32.
 __device__ __forceinline__ bool tile_keep(float u, float v, float a, float b, float c, float rx, float ry, float thre,
-                                          int tx, int ty, float W, float H) {
-    const float x0 = (float)(tx * TILE) + 0.5f;
-    const float x1 = fminf((float)(tx * TILE) + (TILE - 0.5f), W - 0.5f);
-    const float y0 = (float)(ty * TILE) + 0.5f;
-    const float y1 = fminf((float)(ty * TILE) + (TILE - 0.5f), H - 0.5f);
+                                          int tx, int ty, float W, float H, int T) {
+    const float x0 = (float)(tx * T) + 0.5f;
+    const float x1 = fminf((float)(tx * T) + ((float)T - 0.5f), W - 0.5f);
+    const float y0 = (float)(ty * T) + 0.5f;
+    const float y1 = fminf((float)(ty * T) + ((float)T - 0.5f), H - 0.5f);
     if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return thre <= 0.f;
     const float dy_lo = __fsub_rn(y0, v), dy_hi = __fsub_rn(y1, v);
     const float dx_lo = __fsub_rn(x0, u), dx_hi = __fsub_rn(x1, u);

@@ -32,15 +32,35 @@ def test_traffic_record_only_for_the_code_it_was_taken_on(tmp_path, monkeypatch)
     (tmp_path / "profiles").mkdir()
     src = csrc / "k_blend.cu"
     src.write_text("__global__ void k() {}\n")
-    rec = {"k_blend": {"code_sha256": bench.code_sha256(str(src)), "dram_bytes_per_launch": 123456}}
+    rec = {"k_blend": {"code_sha256": bench.code_sha256(str(src)), "dram_bytes_per_launch": 123456,
+                       "units_per_launch": 1000}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic("k_blend", "k_blend.cu", 1.0) == 123456
+    assert bench._traffic("k_blend", "k_blend.cu", 1000.0) == 123456
+    assert bench._traffic("k_blend", "k_blend.cu", 3000.0) == 3 * 123456  # scaled by the units of the launch
     src.write_text("// comment only\n__global__ void k() {}\n")
-    assert bench._traffic("k_blend", "k_blend.cu", 1.0) == 123456
+    assert bench._traffic("k_blend", "k_blend.cu", 1000.0) == 123456
     src.write_text("__global__ void k() { int x = 0; }\n")
     assert bench._traffic("k_blend", "k_blend.cu", 1.0) is None
     assert bench._traffic("k_emit", "k_emit.cu", 1.0) is None
+
+
+def test_reference_arm_times_every_step_it_reports():
+    """The reference arm's line reports the steps and warm-up frames it ran,
+    all of them timed, on the GPU arm's config dict."""
+    import subprocess
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "tiny",
+           "--steps", "3", "--warmup", "4"]
+    out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600,
+                         env=dict(os.environ, OMP_NUM_THREADS="2"))
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["steps"] == 3 and d["warmup"] == 4
+    assert d["cpu_baseline"]["sample"].startswith("all 3 timed frames 4..6")
+    assert abs(d["ms_per_step"] * d["value"] - 1000.0) < 1.0
+    assert d["config"]["frames"] == "4..6 of the 16-frame walk" and d["config"]["workload"] == "box-4096-leaves-128px"
+    assert set(d["config"]) == {"workload", "leaves", "nodes", "width", "height", "tau", "storage", "frames", "l2",
+                                "parallelism"}
 
 
 

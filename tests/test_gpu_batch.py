@@ -87,22 +87,50 @@ def test_batch_equals_individual(small_sh3_scene, h_small):
 
 
 def _trace(n_clients, per_client, rate, seed):
+    """Every client's first request at t = 0 (a burst), then Poisson arrivals."""
     rng = np.random.default_rng(seed)
     reqs = []
     for c in range(n_clients):
-        t = np.cumsum(rng.exponential(1.0 / rate, per_client))
+        t = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0 / rate, per_client - 1))])
         for k, cam in enumerate(_cams(c, per_client, SIZES[c % len(SIZES)])):
             reqs.append(dict(client=c, arrival_s=float(t[k]), cam=cam, tau=3.0, k=k))
-    reqs.sort(key=lambda r: r["arrival_s"])
+    reqs.sort(key=lambda r: (r["arrival_s"], r["client"]))
     return reqs
+
+
+def _solo_walks(h, n_clients, per_client):
+    """Each client's walk rendered alone: images and (cut, pairs) per frame."""
+    out = {}
+    for c in range(n_clients):
+        v = vgr.View(h)
+        imgs, counts = [], []
+        for cam in _cams(c, per_client, SIZES[c % len(SIZES)]):
+            r = v.render(cam, 3.0)
+            imgs.append(r.image().cpu().numpy().copy())
+            counts.append((r.cut_count, r.stats["pair_count"]))
+        v.close()
+        out[c] = (imgs, counts)
+    return out
+
+
+def _overlapping_clients(res):
+    """Pairs of requests of different clients whose [start, finish) intersect."""
+    n = len(res)
+    return [(i, j) for i in range(n) for j in range(i + 1, n)
+            if res["client"][i] != res["client"][j] and res["start_s"][i] < res["finish_s"][j]
+            and res["start_s"][j] < res["finish_s"][i]]
 
 
 @pytest.mark.parametrize("max_inflight", [0, 1])
 def test_server_trace_equals_solo(h_small, max_inflight):
+    """Continuous batching (max_inflight 0) keeps frames of different clients
+    in flight together; one frame at a time (1) never does.  Either way every
+    served frame -- not only each client's last -- equals the same client's
+    walk rendered alone, bit for bit, through per-request host images."""
     C, K = 4, 6
     reqs = _trace(C, K, 200.0, 5)
     sv = vgr.Server(h_small, C, max_inflight=max_inflight, host_images=True)
-    res = sv.serve(reqs)
+    res, imgs = sv.serve(reqs, images=True)
     assert (res["status"] == 0).all()
     assert (res["finish_s"] >= res["start_s"]).all() and (res["start_s"] >= res["arrival_s"] - 1e-9).all()
     # per client: requests started in arrival order and never overlapped
@@ -111,26 +139,66 @@ def test_server_trace_equals_solo(h_small, max_inflight):
         assert (np.diff(rc["start_s"]) >= 0).all()
         assert (rc["start_s"][1:] >= rc["finish_s"][:-1]).all()
         assert rc["lod_from_scratch"][0] == 1 and (rc["lod_from_scratch"][1:] == 0).all()
+    overlap = _overlapping_clients(res)
     if max_inflight == 1:
+        assert not overlap
         order = np.argsort(res["start_s"])
         assert (res["start_s"][order][1:] >= res["finish_s"][order][:-1]).all()
-    # each client's last image equals the same walk rendered alone
-    for c in range(C):
-        v = vgr.View(h_small)
-        for cam in _cams(c, K, SIZES[c % len(SIZES)]):
-            r = v.render(cam, 3.0)
-        W, H = SIZES[c % len(SIZES)]
-        assert np.array_equal(sv.client_host_image(c, H, W), r.image().cpu().numpy())
-        rc = res[res["client"] == c]
-        assert rc["cut_count"][-1] == r.cut_count and rc["pair_count"][-1] == r.stats["pair_count"]
-        v.close()
+    else:
+        # the t = 0 burst: all four first frames are submitted before any completes
+        assert len(overlap) >= C - 1, overlap
+    solo = _solo_walks(h_small, C, K)
+    for i, r in enumerate(reqs):
+        simg, scounts = solo[r["client"]]
+        assert np.array_equal(imgs[i], simg[r["k"]]), (i, r["client"], r["k"])
+        assert (res["cut_count"][i], res["pair_count"][i]) == scounts[r["k"]]
     sv.close()
 
 
 def test_server_admission_refusal(h_small):
     sv = vgr.Server(h_small, 2, hbm_reserve=1 << 62)
     res = sv.serve(_trace(2, 2, 500.0, 6))
-    assert (res["status"] == 2).all()  # VGR_E_NOMEM: not admitted, nothing rendered
+    assert (res["status"] == 2).all()  # VGR_E_NOMEM: cannot fit even alone, nothing rendered
+    sv.close()
+
+
+def test_server_memory_pressure_serves_every_request(h_small):
+    """The clients' views together need more device memory than admission
+    allows (the reserve leaves room for about two of four): requests wait for
+    memory instead of being refused, idle clients' views are released least
+    recently used first, and every request is served with the image its
+    client gets rendering the walk alone (a released client's next frame finds
+    its cut top-down: the same cut)."""
+    C, K = 4, 5
+    est = max(vgr.view_bytes_estimate(h_small, W, H) for W, H in SIZES)
+    free = torch.cuda.mem_get_info()[0]
+    sv = vgr.Server(h_small, C, max_inflight=0, hbm_reserve=int(free - 2.5 * est))
+    reqs = _trace(C, K, 300.0, 7)
+    res, imgs = sv.serve(reqs, images=True)
+    assert (res["status"] == 0).all(), res["status"]
+    assert res["views_released"].sum() > 0 and res["admission_waits"].sum() > 0, res
+    assert res["lod_from_scratch"].sum() >= C
+    solo = _solo_walks(h_small, C, K)
+    for i, r in enumerate(reqs):
+        simg, scounts = solo[r["client"]]
+        assert np.array_equal(imgs[i], simg[r["k"]]), (i, r["client"], r["k"])
+        assert (res["cut_count"][i], res["pair_count"][i]) == scounts[r["k"]]
+    sv.close()
+
+
+def test_server_without_release_waits_for_memory(h_small):
+    """With evict_idle off, views are never released: once two views exist a
+    third client can never be admitted, and its request completes with
+    VGR_E_NOMEM as soon as nothing else is in flight; the others are served."""
+    C = 3
+    est = max(vgr.view_bytes_estimate(h_small, W, H) for W, H in SIZES[:C])
+    free = torch.cuda.mem_get_info()[0]
+    sv = vgr.Server(h_small, C, max_inflight=0, hbm_reserve=int(free - 2.5 * est), evict_idle=False)
+    reqs = _trace(C, 2, 300.0, 8)
+    res = sv.serve(reqs)
+    ok = res["status"] == 0
+    assert ok.sum() >= 2 and (res["status"][~ok] == 2).all()
+    assert (res["views_released"] == 0).all()
     sv.close()
 
 
@@ -157,6 +225,56 @@ def test_whole_batch_graph_equals_individual(small_sh3_scene, h_small):
                 assert np.array_equal(hosts[i], img)
         if k == 0:
             assert res[1].stats["replays"] >= 1  # the small pair buffer grew
+    for v in batch + solo:
+        v.close()
+
+
+def test_batch_single_blend_launch(small_sh3_scene, h_small):
+    """A captured batch runs one blend launch over the tiles of every view
+    with the exact exponential at the first such view's staging depth (one
+    view here has another depth, one the Eq. 5 table: those two blend in their
+    own branch).  Every frame equals the view alone, bit for bit, and the
+    kernels launched are the views' own minus one blend per shared view plus
+    the batch's three (class offsets, tile placement, blend)."""
+    n = len(SIZES)
+    kinds = [dict(), dict(blend_depth=16), dict(exp_mode=vgr.EXP_LUT), dict()]
+    batch = [vgr.View(h_small, use_graph=True, **kinds[i]) for i in range(n)]
+    solo = [vgr.View(h_small, **kinds[i]) for i in range(n)]
+    walks = [_cams(i, 3, SIZES[i]) for i in range(n)]
+    for k in range(3):
+        cams = [walks[i][k] for i in range(n)]
+        res = vgr.render_batch(batch, cams, [3.0] * n)
+        alone = [solo[i].render(cams[i], 3.0) for i in range(n)]
+        for i in range(n):
+            np.testing.assert_array_equal(res[i].cut().cpu().numpy(), alone[i].cut().cpu().numpy())
+            assert np.array_equal(res[i].image().cpu().numpy(), alone[i].image().cpu().numpy()), (k, i)
+            assert res[i].stats["pixel_pair_evals"] == alone[i].stats["pixel_pair_evals"]
+            assert res[i].stats["pixel_pair_contribs"] == alone[i].stats["pixel_pair_contribs"]
+        shared = 2  # views 0 and 3
+        assert sum(r.stats["kernels"] for r in res) == sum(a.stats["kernels"] for a in alone) - shared + 3
+        if k == 0:
+            ref = oracle.render(small_sh3_scene, cams[3], 3.0)
+            check_image(res[3].image().cpu().numpy(), ref)
+    for v in batch + solo:
+        v.close()
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_batch_blend_at_other_tile_sizes(small_sh3_scene, h_small, tile):
+    """The batch blend over views with 8- or 32-pixel tiles (one of another
+    size blends in its own branch): every frame equals the view alone."""
+    n = len(SIZES)
+    sizes = [tile, tile, 16, tile]
+    batch = [vgr.View(h_small, use_graph=True, tile_size=sizes[i]) for i in range(n)]
+    solo = [vgr.View(h_small, tile_size=sizes[i]) for i in range(n)]
+    walks = [_cams(i, 2, SIZES[i]) for i in range(n)]
+    for k in range(2):
+        cams = [walks[i][k] for i in range(n)]
+        res = vgr.render_batch(batch, cams, [3.0] * n)
+        alone = [solo[i].render(cams[i], 3.0) for i in range(n)]
+        for i in range(n):
+            assert np.array_equal(res[i].image().cpu().numpy(), alone[i].image().cpu().numpy()), (k, i)
+        assert sum(r.stats["kernels"] for r in res) == sum(a.stats["kernels"] for a in alone) - 3 + 3
     for v in batch + solo:
         v.close()
 

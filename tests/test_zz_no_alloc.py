@@ -52,6 +52,44 @@ def test_noalloc_matches_allocating_sort_twice():
         np.testing.assert_array_equal(got_v, vals[order])
 
 
+def test_noalloc_allocates_nothing_single_pass_and_second_stream():
+    """After a first call on the device, further calls leave the free device
+    memory (cudaMemGetInfo) unchanged -- the property the entry point exists
+    for -- including a single-pass sort (key_bits = 8: no ping-pong buffer)
+    and a call on a second stream made after the first call returned; both
+    results equal the allocating sort's."""
+    lib = _abi.load()
+    rng = np.random.default_rng(7)
+    n = 50_001
+    keys = rng.integers(0, 1 << 8, size=n, dtype=np.uint64).astype(np.uint32)
+    vals = rng.integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    keys32 = (keys.astype(np.uint64) * 2654435761 + np.arange(n, dtype=np.uint64)) % (1 << 32)
+    keys32 = keys32.astype(np.uint32)
+    ref8_k, ref8_v = _run("vgr_sort_pairs", keys, vals, 8)
+    ref32_k, ref32_v = _run("vgr_sort_pairs", keys32, vals, 32)
+    # every tensor and stream exists before the measurement
+    k8 = torch.from_numpy(keys.view(np.int32)).cuda()
+    k32 = torch.from_numpy(keys32.view(np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo, ko2, vo2 = (torch.empty_like(v) for _ in range(4))
+    s1, s2 = torch.cuda.current_stream(), torch.cuda.Stream()
+    _abi.check(lib.vgr_sort_pairs_noalloc(k8.data_ptr(), v.data_ptr(), ko.data_ptr(), vo.data_ptr(), n, 16,
+                                          ctypes.c_void_p(s1.cuda_stream)))  # warm-up call on this device
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        _abi.check(lib.vgr_sort_pairs_noalloc(k8.data_ptr(), v.data_ptr(), ko.data_ptr(), vo.data_ptr(), n, 8,
+                                              ctypes.c_void_p(s1.cuda_stream)))
+        _abi.check(lib.vgr_sort_pairs_noalloc(k32.data_ptr(), v.data_ptr(), ko2.data_ptr(), vo2.data_ptr(), n, 32,
+                                              ctypes.c_void_p(s2.cuda_stream)))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), ref8_k)
+    np.testing.assert_array_equal(vo.cpu().numpy().view(np.uint32), ref8_v)
+    np.testing.assert_array_equal(ko2.cpu().numpy().view(np.uint32), ref32_k)
+    np.testing.assert_array_equal(vo2.cpu().numpy().view(np.uint32), ref32_v)
+
+
 def test_noalloc_rejects_oversize():
     lib = _abi.load()
     x = torch.zeros(8, dtype=torch.int32, device="cuda")
