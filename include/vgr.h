@@ -139,7 +139,9 @@ typedef struct {
                                 tile; the cut and the image do not depend on it. */
 } vgr_view_opts;
 
-enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1 };
+enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1,
+       VGR_HOOK_FULL_STRIP_WALK = 2  /* the blend walks every record of a strip at every pixel instead of only
+                                        the records whose footprint box covers the pixel (same image) */ };
 
 enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT, VGR_STAGE_COLOR,
        VGR_STAGE_EMIT, VGR_STAGE_TILE_SORT, VGR_STAGE_RANGES, VGR_STAGE_BLEND, VGR_N_STAGES };
@@ -184,7 +186,8 @@ typedef struct {
     const uint32_t* vis_ntile;    /* [n_front] candidate tiles (area of vis_rect), 0 if culled */
     const uint32_t* vis_rect;     /* [2 n_front] candidate tiles: x0 | y0 << 16, x1 | y1 << 16 */
     const float* vis_recA;        /* [4 n_front] u v A B, rho = A dx^2 + B dx dy + C dy^2 */
-    const float* vis_recB;        /* [4 n_front] C thr theta h, thr = ln alpha* - ln theta, h = box half-height */
+    const float* vis_recB;        /* [4 n_front] C thr theta h, thr = ln alpha* - ln theta, h = the footprint box's
+                                     half-height | half-width << 16 as FP16 bits (rounded up) */
     const float* vis_rgb;         /* [4 n_front] r g b 0 (visible entries only) */
     const uint32_t* depth_order;  /* [n_front] in-front index by depth rank; the first n_visible are visible */
     const uint32_t* pair_tile;    /* [n_pairs] tile id, sorted */

@@ -76,8 +76,33 @@ constexpr float LOG2_ALPHA_MIN = -7.9943534368588578f;  // log2(1/255)
 // Eq. 4 becomes rho' >= log2 alpha* (one constant) and Eq. 3 alpha =
 // min(0.99, 2^rho'): X = (u, A', -, -).  R_0, R_1 replace the raw second
 // record half in b; rows 2 and 3 (strips of 4 rows) go to b2.
-template <int MODE, int SR>
-__device__ __forceinline__ void blend_prepare(float4& a, float4& b, float4& b2, float row0) {
+//
+// Returns the record's pixel mask in the strip: bit q (pixel q = row q / T,
+// column q % T) is set when q lies in the footprint box, the axis-aligned
+// box of {rho >= ln alpha* - ln theta - 2e-3} (with a margin) that preprocess
+// stored as FP16 half-extents rounded up.  Outside it the Eq. 4 test fails,
+// so the pixel need not look at the record.  The canonical mode (no Eq. 4
+// before Eq. 3) and 'full' mark every pixel.
+template <int MODE, int SR, int T>
+__device__ __forceinline__ uint32_t blend_prepare(float4& a, float4& b, float4& b2, float row0, float col0,
+                                                  bool full) {
+    uint32_t pmask = 0xFFFFFFFFu;
+    if (MODE != 1 && !full) {
+        const uint32_t hw = __float_as_uint(b.w);
+        const float by = __half2float(__ushort_as_half((unsigned short)(hw & 0xFFFFu))) + 0.01f;
+        const float bx = __half2float(__ushort_as_half((unsigned short)(hw >> 16))) + 0.01f;
+        const float cl = ceilf(a.x - bx - col0), ch = floorf(a.x + bx - col0);  // columns c: |col0 + c - u| <= bx
+        const float rl = ceilf(a.y - by - row0), rh = floorf(a.y + by - row0);  // rows of the strip likewise
+        pmask = 0u;
+        if (cl <= ch && rl <= rh && ch >= 0.f && cl <= (float)(T - 1) && rh >= 0.f && rl <= (float)(SR - 1)) {
+            const uint32_t c0 = (uint32_t)fmaxf(cl, 0.f), c1 = (uint32_t)fminf(ch, (float)(T - 1));
+            const uint32_t r0 = (uint32_t)fmaxf(rl, 0.f), r1 = (uint32_t)fminf(rh, (float)(SR - 1));
+            const uint32_t cols = ((2u << c1) - 1u) & ~((1u << c0) - 1u);
+#pragma unroll
+            for (uint32_t r = 0; r < (uint32_t)SR; ++r)
+                if (r >= r0 && r <= r1) pmask |= cols << (r * T);
+        }
+    }
     float Bc, Cc, add;
     if (MODE == 0) {
         Bc = a.w * LOG2E;
@@ -100,6 +125,24 @@ __device__ __forceinline__ void blend_prepare(float4& a, float4& b, float4& b2, 
     a = X;
     b = make_float4(R[0], R[1], SR > 1 ? R[2 % (2 * SR)] : 0.f, SR > 1 ? R[3 % (2 * SR)] : 0.f);
     if (SR > 2) b2 = make_float4(R[4 % (2 * SR)], R[5 % (2 * SR)], R[6 % (2 * SR)], R[7 % (2 * SR)]);
+    return pmask;
+}
+
+// Transpose of the 32 x 32 bit matrix held by a warp, lane l holding row l:
+// afterwards lane q holds column q (bit l = bit q of lane l's row).  Five
+// exchange steps, each swapping the off-diagonal blocks of half the size.
+template <uint32_t J, uint32_t M>
+__device__ __forceinline__ uint32_t transpose_step(uint32_t x, uint32_t lane) {
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, J);
+    return (lane & J) ? ((x & ~M) | ((y & ~M) >> J)) : ((x & M) | ((y & M) << J));
+}
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+    const uint32_t lane = lane_id();
+    x = transpose_step<16, 0x0000FFFFu>(x, lane);
+    x = transpose_step<8, 0x00FF00FFu>(x, lane);
+    x = transpose_step<4, 0x0F0F0F0Fu>(x, lane);
+    x = transpose_step<2, 0x33333333u>(x, lane);
+    return transpose_step<1, 0x55555555u>(x, lane);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -211,6 +254,7 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
     __shared__ uint32_t s_ring[BL_WARPS][RING];  // per-warp queue of hit pair values
     __shared__ float s_lut[MODE == 2 ? 260 : 1];
     __shared__ WarpItem s_item[BL_WARPS];
+    __shared__ uint32_t s_pm[BL_WARPS][DEPTH];   // staged records' pixel masks
     __shared__ uint32_t s_claim;                 // next (slot, strip) item of this CTA
     __shared__ uint32_t s_slot_tile[4], s_slot_tag[4], s_slot_read[4];
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -234,6 +278,7 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
     __syncthreads();
     uint32_t* ring = s_ring[warp];
     volatile WarpItem& it = s_item[warp];
+    const bool full_walk = (fp0->test_hooks & VGR_HOOK_FULL_STRIP_WALK) != 0u;
     volatile uint32_t* slot_tile = s_slot_tile;
     volatile uint32_t* slot_tag = s_slot_tag;
     volatile uint32_t* slot_read = s_slot_read;
@@ -278,7 +323,7 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
         strip = __shfl_sync(FULL, strip, 0);
         if (__shfl_sync(FULL, (uint32_t)timed_out, 0) || idx >= n_work) break;
         uint2 rg;
-        float rlo;
+        float rlo, clo;
         uint32_t wbits;
         bool inside;
         {
@@ -308,6 +353,7 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
             inside = x0 + lane % T < W && y0 + lane / T < H;
             wbits = ((1u << SB) - 1u) << (SR * strip / MR);
             rlo = (float)y0 + 0.5f;  // centre of the strip's first row
+            clo = (float)x0 + 0.5f;  // and column
             __syncwarp();
         }
         BlendPixel p;
@@ -389,27 +435,46 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
 #pragma unroll
             for (int q = 0; q < (DEPTH + 31) / 32; ++q) {
                 const uint32_t sl = 32u * q + lane;
-                if (sl < nh)  // each lane its own slots
-                    blend_prepare<MODE, SR>(wA[sl], sbuf[buf][2][warp][sl], sbuf[buf][NP - 1][warp][sl], rlo);
+                if (sl < (uint32_t)DEPTH)  // each lane its own slots; empty slots reach no pixel
+                    s_pm[warp][sl] = sl < nh ? blend_prepare<MODE, SR, T>(wA[sl], sbuf[buf][2][warp][sl],
+                                                                           sbuf[buf][NP - 1][warp][sl], rlo, clo,
+                                                                           full_walk)
+                                             : 0u;
             }
             __syncwarp();
+            // the records that can reach this lane's pixel, as slot bits in
+            // depth order: the transpose of the records' pixel masks
+            uint32_t reach[(DEPTH + 31) / 32];
+#pragma unroll
+            for (int q = 0; q < (DEPTH + 31) / 32; ++q) {
+                const uint32_t sl = 32u * q + lane;
+                reach[q] = warp_transpose32(sl < (uint32_t)DEPTH ? s_pm[warp][sl] : 0u);
+            }
             if (!p.done) {
                 // this lane's row r = lane / T: its terms are float2 (r & 1) of part 2 + r / 2
                 const uint32_t r = lane / T;
                 const float2* wR = reinterpret_cast<const float2*>(sbuf[buf][2 + r / 2][warp]) + (r & 1u);
-                uint32_t i = 0, ev = nh;
-                for (; i + 2 <= nh; i += 2) {
-                    const float4 X0 = load_x<MODE>(wA, i), X1 = load_x<MODE>(wA, i + 1);
-                    const float2 R0 = wR[2 * i], R1 = wR[2 * i + 2];
-                    const float r0 = blend_rho(p, X0, R0), r1 = blend_rho(p, X1, R1);
-                    if (!blend_step<MODE>(p, X0, wC, i, r0, s_lut, m, lut_scale)) { ev = i + 1; break; }
-                    if (!blend_step<MODE>(p, X1, wC, i + 1, r1, s_lut, m, lut_scale)) { ev = i + 2; break; }
+#pragma unroll
+                for (int q = 0; q < (DEPTH + 31) / 32; ++q) {
+                    uint32_t mm = reach[q];
+                    while (mm != 0u) {  // two records at a time for instruction-level parallelism
+                        const uint32_t i0 = 32u * q + __ffs(mm) - 1u;
+                        mm &= mm - 1u;
+                        const bool two = mm != 0u;
+                        const uint32_t i1 = two ? 32u * q + __ffs(mm) - 1u : i0;
+                        mm &= mm - 1u;
+                        const float4 X0 = load_x<MODE>(wA, i0), X1 = load_x<MODE>(wA, i1);
+                        const float2 R0 = wR[2 * i0], R1 = wR[2 * i1];
+                        const float r0 = blend_rho(p, X0, R0), r1 = blend_rho(p, X1, R1);
+                        ++evals;
+                        if (!blend_step<MODE>(p, X0, wC, i0, r0, s_lut, m, lut_scale)) break;
+                        if (two) {
+                            ++evals;
+                            if (!blend_step<MODE>(p, X1, wC, i1, r1, s_lut, m, lut_scale)) break;
+                        }
+                    }
+                    if (p.done) break;
                 }
-                if (!p.done && i < nh) {
-                    const float4 X0 = load_x<MODE>(wA, i);
-                    if (!blend_step<MODE>(p, X0, wC, i, blend_rho(p, X0, wR[2 * i]), s_lut, m, lut_scale)) ev = i + 1;
-                }
-                evals += ev;
             }
             __syncwarp();  // the walk is done with this buffer before it is refilled
             buf ^= 1;

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
                 s_h[q] = make_float4(cc, __fdiv_rn(-cb, ca), __fdiv_rn(-cb, cc), B.y - TILE_EPS);
                 const uint32_t x0 = rect.x & 0xFFFFu, y0 = rect.x >> 16;
                 s_rect[q] = x0 | (y0 << 10) | (((rect.y & 0xFFFFu) - x0 + 1u) << 20);
-                s_hh[q] = __float2half_ru(B.w);
+                s_hh[q] = __ushort_as_half((unsigned short)(__float_as_uint(B.w) & 0xFFFFu));  // half-height
             }
             s_off[q] = area;
         }

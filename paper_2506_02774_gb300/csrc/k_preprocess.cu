@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
         bool v = i < n_front;
         uint32_t node = node_next, zbits = 0xFFFFFFFFu;
         node_next = i + stride < n_front ? front[i + stride] : 0u;
-        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, half_h = 0.f, lw = 0.f;
+        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, thr = 0.f, theta = 0.f, lw = 0.f;
+        uint32_t box_hw = 0u;  // footprint box half-height | half-width << 16, FP16 rounded up
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
             float4 m = sc.cr[node];
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
                         tx1 = -1;  // far outside (also guards the float->int conversions)
                     }
                     if (tx0 > tx1 || ty0 > ty1) v = false;
-                    half_h = by;
+                    box_hw = (uint32_t)__half_as_ushort(__float2half_ru(by)) |
+                             ((uint32_t)__half_as_ushort(__float2half_ru(bx)) << 16);
                 }
             }
             if (v) zbits = __float_as_uint(z);
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
             vis.ntile[i] = v ? (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1) : 0u;
             vis.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
             vis.recA[i] = make_float4(u, vv, -0.5f * ca, -cb);
-            vis.recB[i] = make_float4(-0.5f * cc, thr, theta, half_h);
+            vis.recB[i] = make_float4(-0.5f * cc, thr, theta, __uint_as_float(box_hw));
             if (INTERP) vis.lw[i] = lw;
         }
     }

@@ -79,7 +79,7 @@ struct VisBuffers {
     uint32_t* ntile;
     uint2* rect;
     float4* recA;   // u v A B   (rho = A dx^2 + B dx dy + C dy^2)
-    float4* recB;   // C thr theta half-height of the footprint box
+    float4* recB;   // C thr theta, and the footprint box's half-height | half-width << 16 (FP16 bits, rounded up)
     float4* rgb;    // r g b 0
     float* lw;      // parent weight of the interpolated Gaussian (weight interpolation only)
 };

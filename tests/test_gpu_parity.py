@@ -284,3 +284,42 @@ def test_lut_mode_error(small_sh3_scene):
         assert rl["psnr"] >= max(50.0, r["psnr"] + 6.0), (m, r, rl)
         v.close()
     h.close()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_footprint_walk_equals_full_walk(small_sh3_scene, tile):
+    """Each pixel walks only the staged records whose footprint box covers it
+    (the box of {rho >= ln alpha* - ln theta - 2e-3}, so every record left out
+    fails Eq. 4 there).  The image, and the number of contributions, must
+    equal those of the full strip walk (every record at every pixel, the
+    VGR_HOOK_FULL_STRIP_WALK hook) bit for bit, with fewer evaluations; in the
+    exact mode and the Eq. 5 table mode."""
+    h = vgr.Hierarchy(small_sh3_scene)
+    for kw in (dict(), dict(exp_mode=vgr.EXP_LUT)):
+        va = vgr.View(h, tile_size=tile, **kw)
+        vb = vgr.View(h, tile_size=tile, test_hooks=2, **kw)
+        for fr, (W, H) in enumerate([(328, 250), (257, 131), (640, 360)]):
+            cam = scenegen.camera((2.0 + 0.3 * fr, 15.0 - fr, 3.0), 0.2 + 0.1 * fr, W, H, 260.0 * W / 328.0)
+            a, b = va.render(cam, 3.0), vb.render(cam, 3.0)
+            assert np.array_equal(_img(a), _img(b)), (kw, fr)
+            assert a.stats["pixel_pair_contribs"] == b.stats["pixel_pair_contribs"]
+            assert a.stats["pixel_pair_evals"] < b.stats["pixel_pair_evals"]
+        va.close()
+        vb.close()
+    h.close()
+
+
+def test_footprint_walk_equals_full_walk_1m():
+    """The same on the 1M-leaf box at 1920 x 1080 (a first frame and a
+    temporal update), where many records are a few pixels wide."""
+    sc = scenegen.make_scene("m1")
+    h = vgr.Hierarchy(sc)
+    va, vb = vgr.View(h), vgr.View(h, test_hooks=2)
+    for fr in (0, 5):
+        cam = scenegen.trajectory("m1", fr)
+        a, b = va.render(cam, 3.0), vb.render(cam, 3.0)
+        assert np.array_equal(_img(a), _img(b)), fr
+        assert a.stats["pixel_pair_contribs"] == b.stats["pixel_pair_contribs"]
+        print("evaluations: footprint walk %d, full strip walk %d" % (a.stats["pixel_pair_evals"],
+                                                                   b.stats["pixel_pair_evals"]))
+    va.close(); vb.close(); h.close()
