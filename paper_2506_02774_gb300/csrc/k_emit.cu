@@ -2,24 +2,26 @@
 // tile-level preemptive alpha test, and the blend's tile order (which also
 // finishes the per-tile ranges the last tile-sort pass records).
 //
-// Visible Gaussians are visited in depth order (the output of the depth
-// sort), 512 per CTA tile (2 per thread).  Each one owns as many pair slots as it has
-// candidate tiles; a decoupled look-back scan over the candidate counts gives
-// every CTA tile its global slot range.  The CTA then walks its slots with
-// all 256 threads (slot -> Gaussian by binary search over the CTA's
-// exclusive offsets in shared memory), so a Gaussian with thousands of
-// candidate tiles costs no more per thread than one with a single tile.  For
-// each slot the tile-level form of Eq. 4 (paper Sec. 4.2) decides: a kept
-// slot gets key = tile id, a dropped one the sentinel key, which the stable
-// tile sort moves behind every real pair (which stay in depth order within
-// a tile, the sort being stable).  The slot's value is the Gaussian's index
-// in the in-front arrays << 8 | its row mask in that tile: bit w is set when
-// the footprint box reaches one of the tile's pixel rows w MR .. w MR + MR - 1,
-// MR = tile / 8 rows (1 for 8-pixel tiles); outside the box the Eq. 4 test
-// fails at every pixel, so the blend reads only the records a strip needs,
-// straight from the in-front arrays.  Indices therefore take 24 bits: a frame with more
-// cut nodes in front of the camera reports an overflow.  The digit
-// histograms of the tile sort are accumulated here as well.
+// Two kernels.  k_slot_scan gives every visible Gaussian, in depth order (the
+// output of the depth sort), the first of its pair slots: an exclusive scan of
+// the candidate-tile counts by decoupled look-back over tiles of 2048, whose
+// per-tile work is light, so the chain of tiles moves fast.  k_emit then takes
+// 512 Gaussians per CTA tile with no ticket and no look-back (their slot range
+// is known): it gathers their records, and walks the tile's slots with all 256
+// threads (slot -> Gaussian by binary search over the CTA's offsets in shared
+// memory), so a Gaussian with thousands of candidate tiles costs no more per
+// thread than one with a single tile.  For each slot the tile-level form of
+// Eq. 4 (paper Sec. 4.2) decides: a kept slot gets key = tile id, a dropped one
+// the sentinel key, which the stable tile sort moves behind every real pair
+// (which stay in depth order within a tile, the sort being stable).  The slot's
+// value is the Gaussian's index in the in-front arrays << 8 | its row mask in
+// that tile: bit w is set when the footprint box reaches one of the tile's
+// pixel rows w MR .. w MR + MR - 1, MR = tile / 8 rows (1 for 8-pixel tiles);
+// outside the box the Eq. 4 test fails at every pixel, so the blend reads only
+// the records a strip needs, straight from the in-front arrays.  Indices
+// therefore take 24 bits: a frame with more cut nodes in front of the camera
+// reports an overflow.  The digit histograms of the tile sort are accumulated
+// here as well.
 #include <cuda_fp16.h>
 
 #include "vgr_internal.cuh"
@@ -34,16 +36,82 @@ constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
 
 uint32_t emit_tile() { return EM_TILE; }
 
-__global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
-                                                     VisBuffers vis,
-                                                     uint32_t* __restrict__ pair_key,
-                                                     uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,
-                                                     uint32_t sentinel, unsigned long long* __restrict__ status,
-                                                     Counters* __restrict__ ctr, const FrameParams* __restrict__ fp) {
+constexpr int SS_THREADS = 256;
+constexpr int SS_ITEMS = 8;
+constexpr int SS_TILE = SS_THREADS * SS_ITEMS;  // Gaussians per look-back tile of the slot scan
+
+uint32_t slot_scan_tile() { return SS_TILE; }
+
+// off[r] = candidate slots of the Gaussians of depth rank < r (r <= n_vis);
+// off[n_vis] is the frame's candidate-slot count.
+__global__ void __launch_bounds__(SS_THREADS) k_slot_scan(const uint32_t* __restrict__ order, uint32_t cap_vis,
+                                                          const uint32_t* __restrict__ ntile,
+                                                          uint32_t* __restrict__ off, uint64_t cap_pairs,
+                                                          unsigned long long* __restrict__ status,
+                                                          Counters* __restrict__ ctr,
+                                                          const FrameParams* __restrict__ fp) {
     pdl_wait();
     __shared__ uint32_t s_scan[9];
     __shared__ uint32_t s_tile, s_prefix;
-    __shared__ uint32_t s_off[EM_TILE + 1];   // candidate counts, then exclusive slot offsets
+    const uint32_t n_vis = min(ctr->n_vis, cap_vis);
+    const uint32_t ntiles = (n_vis + SS_TILE - 1) / SS_TILE;
+    const uint32_t epoch = fp->epoch;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->n_front > MAX_RANKS) atomicOr(&ctr->flags, F_OVF_VIS);
+    if (n_vis == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            off[0] = 0u;
+            ctr->n_cand = 0ull;
+        }
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_EMIT], 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        // thread t owns ranks tile * SS_TILE + SS_ITEMS t .. + SS_ITEMS - 1 (gathers in flight together)
+        const uint32_t r0 = tile * SS_TILE + SS_ITEMS * threadIdx.x;
+        uint32_t c[SS_ITEMS], vi[SS_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) vi[k] = r0 + k < n_vis ? order[r0 + k] : NONE;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) c[k] = vi[k] != NONE ? ntile[vi[k]] : 0u;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) sum += c[k];
+        uint32_t total;
+        uint32_t run = block_excl_scan<SS_THREADS / 32>(sum, s_scan, &total);
+        if (threadIdx.x < 32) {
+            // (test hook: tile 0 stays silent, so the others' bounded waits run out)
+            const bool silent = tile == 0 && (fp->test_hooks & VGR_HOOK_WITHHOLD_LOOKBACK);
+            const uint32_t pre = silent ? 0u : lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
+            if (threadIdx.x == 0) s_prefix = pre;
+        }
+        __syncthreads();
+        run += s_prefix;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) {
+            if (r0 + k < n_vis) off[r0 + k] = run;
+            run += c[k];
+        }
+        if (tile == ntiles - 1 && threadIdx.x == 0) {
+            const uint64_t ns = (uint64_t)s_prefix + total;
+            off[n_vis] = (uint32_t)ns;
+            ctr->n_cand = ns;
+            if (ns > cap_pairs) atomicOr(&ctr->flags, F_OVF_PAIRS);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
+                                                     VisBuffers vis, const uint32_t* __restrict__ slot_off,
+                                                     uint32_t* __restrict__ pair_key,
+                                                     uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,
+                                                     uint32_t sentinel, Counters* __restrict__ ctr,
+                                                     const FrameParams* __restrict__ fp) {
+    pdl_wait();
+    __shared__ uint32_t s_off[EM_TILE + 1];   // exclusive slot offsets within the CTA tile, then its total
     __shared__ float4 s_g[EM_TILE];           // u v a b
     __shared__ float4 s_h[EM_TILE];           // c rx ry thre
     __shared__ uint32_t s_rect[EM_TILE];      // x0 | y0 << 10 | width << 20 (tiles; 16384-px images: < 2^10)
@@ -52,65 +120,50 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     const uint32_t n_vis = min(ctr->n_vis, cap_vis);
     const uint32_t ntiles = (n_vis + EM_TILE - 1) / EM_TILE;
-    const uint32_t epoch = fp->epoch;
     const uint32_t TW = fp->tiles_x;
     const int T = (int)fp->tile;
     const int MR = T >= 8 ? T / 8 : 1;  // tile rows per row-mask bit (8 bits)
     const float Wf = fp->width_f, Hf = fp->height_f;
     const bool canonical = fp->filter == VGR_FILTER_CANONICAL;
     uint32_t kept = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->n_front > MAX_RANKS) atomicOr(&ctr->flags, F_OVF_VIS);
+    __shared__ uint32_t s_tile;
     __syncthreads();
 
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_EMIT], 1u);
+        // tiles are claimed in order as CTAs free up: their slot counts vary widely
+        if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_PRE], 1u);
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) break;
+        const uint32_t g0 = tile * EM_TILE;
+        const uint32_t base32 = slot_off[g0];
         // gather EM_ITEMS Gaussians per thread (independent loads in flight)
 #pragma unroll
         for (int k = 0; k < EM_ITEMS; ++k) {
             const uint32_t q = k * EM_THREADS + threadIdx.x;  // position in depth order within the CTA tile
-            const uint32_t r = tile * EM_TILE + q;
-            uint32_t area = 0;
+            const uint32_t r = g0 + q;
             if (r < n_vis) {
                 const uint32_t vi = order[r];
-                area = vis.ntile[vi];
                 const uint2 rect = vis.rect[vi];
                 const float4 A = vis.recA[vi];
                 const float4 B = vis.recB[vi];
                 // the conic is stored pre-scaled (A = -a/2, B = -b, C = -c/2): exact to undo
                 const float ca = -2.0f * A.z, cb = -A.w, cc = -2.0f * B.x;
                 s_g[q] = make_float4(A.x, A.y, ca, cb);
-                s_h[q] = make_float4(cc, __fdiv_rn(-cb, ca), __fdiv_rn(-cb, cc), B.y - TILE_EPS);
+                // edge optima dy* = (-b / c) dx, dx* = (-b / a) dy; an ulp or two of
+                // error moves rho_max by far less than the test's 2e-3 slack
+                s_h[q] = make_float4(cc, __fdividef(-cb, ca), __fdividef(-cb, cc), B.y - TILE_EPS);
                 const uint32_t x0 = rect.x & 0xFFFFu, y0 = rect.x >> 16;
                 s_rect[q] = x0 | (y0 << 10) | (((rect.y & 0xFFFFu) - x0 + 1u) << 20);
                 s_hh[q] = __ushort_as_half((unsigned short)(__float_as_uint(B.w) & 0xFFFFu));  // half-height
             }
-            s_off[q] = area;
+            // offsets within the tile; past the last Gaussian: the tile's total
+            s_off[q] = slot_off[min(r, n_vis)] - base32;
         }
+        if (threadIdx.x == 0) s_off[EM_TILE] = slot_off[min(g0 + EM_TILE, n_vis)] - base32;
         __syncthreads();
-        // exclusive scan of the candidate counts in depth order: thread t owns entries
-        // EM_ITEMS t .. EM_ITEMS t + EM_ITEMS - 1
-        uint32_t a4[EM_ITEMS];
-        uint32_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < EM_ITEMS; ++k) { a4[k] = s_off[EM_ITEMS * threadIdx.x + k]; sum += a4[k]; }
-        uint32_t total;
-        uint32_t run = block_excl_scan<EM_THREADS / 32>(sum, s_scan, &total);
-#pragma unroll
-        for (int k = 0; k < EM_ITEMS; ++k) { s_off[EM_ITEMS * threadIdx.x + k] = run; run += a4[k]; }
-        if (threadIdx.x < 32) {
-            // (test hook: tile 0 stays silent, so the others' bounded waits run out)
-            const bool silent = tile == 0 && (fp->test_hooks & VGR_HOOK_WITHHOLD_LOOKBACK);
-            const uint32_t pre = silent ? 0u : lookback_warp(status, 1, tile, total, epoch, &ctr->flags);
-            if (threadIdx.x == 0) {
-                s_off[EM_TILE] = total;
-                s_prefix = pre;
-            }
-        }
-        __syncthreads();
-        const uint64_t base = s_prefix;
+        const uint32_t total = s_off[EM_TILE];
+        const uint64_t base = base32;
         // slots in warp-sized runs: the owner of the run's first slot by a
         // warp-uniform binary search, the other lanes' owners by counting the
         // Gaussians that start inside the run (every visible Gaussian has at
@@ -135,8 +188,11 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
                 const uint32_t local = j - s_off[g];
                 const uint32_t rc = s_rect[g];
                 const uint32_t w = rc >> 20;
-                const int tx = (int)(rc & 0x3FFu) + (int)(local % w);
-                const int ty = (int)((rc >> 10) & 0x3FFu) + (int)(local / w);
+                // local / w and local % w: local < 2^20 and w <= 2^10, so (local + 1/2) / w is
+                // at least 1 / 2^11 from an integer and its FP32 quotient floors exactly
+                const uint32_t qy = (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w));
+                const int tx = (int)(rc & 0x3FFu) + (int)(local - qy * w);
+                const int ty = (int)((rc >> 10) & 0x3FFu) + (int)qy;
                 keep = true;
                 if (!canonical) {
                     const float4 G = s_g[g], Hh = s_h[g];
@@ -162,11 +218,6 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
                 for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
             }
         }
-        if (tile == ntiles - 1 && threadIdx.x == 0) {
-            const uint64_t ns = base + total;
-            ctr->n_cand = ns;
-            if (ns > cap) atomicOr(&ctr->flags, F_OVF_PAIRS);
-        }
         __syncthreads();
     }
     const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, kept);
@@ -178,11 +229,14 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
     }
 }
 
-void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes,
-                 uint32_t sentinel, unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid,
+void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* slot_off, uint32_t* pair_key,
+                 uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
+                 unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid_scan, int grid,
                  cudaStream_t s) {
-    launch_k(k_emit, grid, EM_THREADS, s, order, cap_vis, vis, pair_key, pair_val, cap_pairs,
-                                       tile_passes, sentinel, status, ctr, fp);
+    launch_k(k_slot_scan, grid_scan, SS_THREADS, s, order, cap_vis, (const uint32_t*)vis.ntile, slot_off, cap_pairs,
+             status, ctr, fp);
+    launch_k(k_emit, grid, EM_THREADS, s, order, cap_vis, vis, (const uint32_t*)slot_off, pair_key, pair_val, cap_pairs,
+             tile_passes, sentinel, ctr, fp);
 }
 
 // Blend order: tiles by descending pair count (classes of floor(log2(count+1)),

@@ -147,6 +147,7 @@ struct vgr_view {
     VisBuffers vis{};
     uint32_t* sortK[2] = {nullptr, nullptr};
     uint32_t* sortV[2] = {nullptr, nullptr};
+    uint32_t* slot_off = nullptr;  // first pair slot of each visible Gaussian by depth rank (cap_vis + 1)
     uint32_t* pairK[2] = {nullptr, nullptr};
     uint32_t* pairV[2] = {nullptr, nullptr};
     uint2* ranges = nullptr;
@@ -513,6 +514,7 @@ void free_vis(vgr_view* v) {
     dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
     dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb); dfree(v->vis.lw);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
+    dfree(v->slot_off);
     v->vis_bytes = 0;
 }
 
@@ -526,7 +528,7 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
         (s = dalloc(&v->vis.rgb, cap, &b)) || (s = dalloc(&v->vis.lw, cap, &b)) ||
         (s = dalloc(&v->sortK[0], cap, &b)) ||
         (s = dalloc(&v->sortK[1], cap, &b)) || (s = dalloc(&v->sortV[0], cap, &b)) ||
-        (s = dalloc(&v->sortV[1], cap, &b))) {
+        (s = dalloc(&v->sortV[1], cap, &b)) || (s = dalloc(&v->slot_off, (size_t)cap + 1, &b))) {
         free_vis(v);
         return s;
     }
@@ -806,6 +808,7 @@ vgr_status vgr_view_bytes_estimate(const vgr_hierarchy* h, const vgr_view_opts* 
     const uint64_t TW = cut_compact_tile_words();
     const uint64_t n_words = ((N + 31) / 32 + TW - 1) / TW * TW;
     const uint64_t per_vis = 3 * sizeof(uint32_t) + sizeof(uint2) + 3 * sizeof(float4) + sizeof(float) /* visible SoA */ +
+                             sizeof(uint32_t) /* slot offsets */ +
                              4 * sizeof(uint32_t) /* depth-sort ping-pong */ + 3 * sizeof(float4) /* rank records */;
     const uint64_t RT = radix_tile();
     const uint64_t status_words = 2 * (cut_compact_tiles((uint32_t)n_words) + 1) + ceil_div(cap_vis, emit_tile()) + 1 +
@@ -844,7 +847,7 @@ constexpr int EMIT_GRID_NUM = 6;
 uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
     return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
-           1u /*emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
+           2u /*slot scan, emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
 }
 
 // The frame's status block and cut sizes, read back after its last kernel.
@@ -922,8 +925,8 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
     }
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
-    launch_emit(order, v->cap_vis, v->vis, v->pairK[0], v->pairV[0], v->cap_pairs,
-                tile_passes, sentinel, v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan * EMIT_GRID_NUM / 4, s);
+    launch_emit(order, v->cap_vis, v->vis, v->slot_off, v->pairK[0], v->pairV[0], v->cap_pairs, tile_passes, sentinel,
+                v->status + v->st_emit, v->ctr, v->fp_dev, v->grid_scan, v->grid_scan * EMIT_GRID_NUM / 4, s);
     mark(VGR_STAGE_TILE_SORT);
     // (the last pass also records each tile's range)
     for (int p = 0; p < tile_passes; ++p) {

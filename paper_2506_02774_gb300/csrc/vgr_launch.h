@@ -103,9 +103,13 @@ void launch_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_
                        uint32_t n_ranges = 0);
 
 // k_emit.cu
-void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* pair_key, uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
-                 unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid, cudaStream_t s);
+// k_slot_scan (slot offsets in depth order, into slot_off[cap_vis + 1]) then k_emit
+void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32_t* slot_off, uint32_t* pair_key,
+                 uint32_t* pair_val, uint64_t cap_pairs, int tile_passes, uint32_t sentinel,
+                 unsigned long long* status, Counters* ctr, const FrameParams* fp, int grid_scan, int grid,
+                 cudaStream_t s);
 uint32_t emit_tile();
+uint32_t slot_scan_tile();
 void launch_tile_order(uint2* ranges, uint32_t n_tiles, uint32_t* order, Counters* ctr, cudaStream_t s);
 constexpr uint32_t BATCH_VIEWS_MAX = 1024;  // views of one batch blend (k_batch_offsets: one thread each)
 
