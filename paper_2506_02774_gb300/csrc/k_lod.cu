@@ -353,73 +353,98 @@ __global__ void __launch_bounds__(256) k_lod_level(int level, const uint32_t* __
 // Bitmaps -> ascending id lists (the cut, and its in-front part), clearing
 // both bitmaps for the next frame.  Tiles of 256 threads x 4 words; two
 // decoupled look-back chains (warp 0: cut, warp 1: in-front) give each tile
-// its output offsets; each warp then writes its 128 words' ids in order, one
-// word per step with a ballot, so every store instruction is coalesced.
-constexpr int CC_WORDS = 4;
-constexpr int CC_TILE_WORDS = 256 * CC_WORDS;
+// its output offsets.  A warp owns 128 contiguous words of the tile and takes
+// them in four rounds of 32 (lane l holds word 32 j + l of round j, so every
+// load is coalesced): a shuffle scan of the words' bit counts places each
+// lane's ids in the warp's staging buffer in shared memory, and the warp then
+// stores the round's ids contiguously (coalesced) -- no serial per-word loop.
+constexpr int CC_THREADS = 256;
+constexpr int CC_WARPS = CC_THREADS / 32;
+constexpr int CC_WORDS = 4;  // words per lane = rounds per warp
+constexpr int CC_TILE_WORDS = CC_THREADS * CC_WORDS;
 
-__device__ __forceinline__ void cc_write(const uint32_t (&w)[4], uint32_t wbase, uint32_t off, uint32_t* out,
-                                         uint32_t cap) {
+// One round of one bitmap: this lane's word `word` (index `wi`), the round's
+// ids staged in `stage` (32 words x 32 bits at most) and stored from `off`.
+__device__ __forceinline__ uint32_t cc_round(uint32_t word, uint32_t wi, uint32_t off, uint32_t* stage,
+                                             uint32_t* out, uint32_t cap) {
     const uint32_t lane = lane_id();
-    uint32_t nz = __ballot_sync(0xFFFFFFFFu, (w[0] | w[1] | w[2] | w[3]) != 0u);
-    while (nz) {
-        const int src = __ffs(nz) - 1;
-        nz &= nz - 1u;
+    const uint32_t c = __popc(word);
+    uint32_t incl = c;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t word = __shfl_sync(0xFFFFFFFFu, w[j], src);
-            if (word == 0u) continue;
-            const bool bit = (word >> lane) & 1u;
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
-            if (bit) {
-                const uint32_t pos = off + __popc(m & lanemask_lt());
-                if (pos < cap) out[pos] = (wbase + (uint32_t)src * 4u + (uint32_t)j) * 32u + lane;
-            }
-            off += __popc(m);
-        }
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if ((int)lane >= d) incl += y;
     }
+    const uint32_t n = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (n == 0u) return off;
+    uint32_t p = incl - c;
+    while (word) {
+        stage[p++] = wi * 32u + (uint32_t)(__ffs(word) - 1);
+        word &= word - 1u;
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32u)
+        if (off + i < cap) out[off + i] = stage[i];
+    __syncwarp();  // the buffer is read before the next round writes it
+    return off + n;
 }
 
-__global__ void __launch_bounds__(256) k_cut_compact(uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
-                                                     uint32_t n_words, uint32_t* __restrict__ cut,
-                                                     uint32_t* __restrict__ front_list, uint32_t cap,
-                                                     uint32_t* __restrict__ n_cut_out,
-                                                     unsigned long long* __restrict__ status,
-                                                     unsigned long long* __restrict__ status_front,
-                                                     Counters* __restrict__ ctr,
-                                                     const FrameParams* __restrict__ fp) {
+__global__ void __launch_bounds__(CC_THREADS) k_cut_compact(uint32_t* __restrict__ bitmap, uint32_t* __restrict__ front,
+                                                            uint32_t n_words, uint32_t* __restrict__ cut,
+                                                            uint32_t* __restrict__ front_list, uint32_t cap,
+                                                            uint32_t* __restrict__ n_cut_out,
+                                                            unsigned long long* __restrict__ status,
+                                                            unsigned long long* __restrict__ status_front,
+                                                            Counters* __restrict__ ctr,
+                                                            const FrameParams* __restrict__ fp) {
     pdl_wait();
-    __shared__ uint32_t s_scan[9];
+    __shared__ uint32_t s_stage[CC_WARPS][32 * 32];
+    __shared__ uint32_t s_wtot[CC_WARPS];
     __shared__ uint32_t s_tile, s_prefix[2];
     const uint32_t ntiles = (n_words + CC_TILE_WORDS - 1) / CC_TILE_WORDS;
     const uint32_t epoch = fp->epoch;
-    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&ctr->tickets[TK_COMPACT], 1u);
         __syncthreads();
         const uint32_t tile = s_tile;
         if (tile >= ntiles) break;
-        const uint32_t w0 = tile * CC_TILE_WORDS + threadIdx.x * CC_WORDS;
         // the bitmaps are padded to a whole number of tiles
-        const uint4 a = *reinterpret_cast<const uint4*>(bitmap + w0);
-        const uint4 b = *reinterpret_cast<const uint4*>(front + w0);
-        const uint32_t ca = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w);
-        const uint32_t cb = __popc(b.x) + __popc(b.y) + __popc(b.z) + __popc(b.w);
-        uint32_t total;  // both counts in one scan: at most 32768 each per tile
-        const uint32_t excl = block_excl_scan<8>(ca | (cb << 16), s_scan, &total);
+        const uint32_t wbase = tile * CC_TILE_WORDS + warp * (32u * CC_WORDS);
+        uint32_t a[CC_WORDS], b[CC_WORDS];
+#pragma unroll
+        for (int j = 0; j < CC_WORDS; ++j) {
+            a[j] = bitmap[wbase + 32u * j + lane];
+            b[j] = front[wbase + 32u * j + lane];
+        }
+        uint32_t cnt = 0;  // both counts packed: at most 32768 each per tile
+#pragma unroll
+        for (int j = 0; j < CC_WORDS; ++j) cnt += __popc(a[j]) | (__popc(b[j]) << 16);
+        cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        if (lane == 0) s_wtot[warp] = cnt;
+        __syncthreads();
+        uint32_t wexcl = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < CC_WARPS; ++w) {
+            const uint32_t v = s_wtot[w];
+            wexcl += (uint32_t)w < warp ? v : 0u;
+            total += v;
+        }
         if (warp < 2) {
             const uint32_t agg = warp == 0 ? (total & 0xFFFFu) : (total >> 16);
             const uint32_t pre = lookback_warp(warp == 0 ? status : status_front, 1, tile, agg, epoch, &ctr->flags);
-            if (lane_id() == 0) s_prefix[warp] = pre;
+            if (lane == 0) s_prefix[warp] = pre;
         }
         __syncthreads();
-        const uint32_t wbase = tile * CC_TILE_WORDS + warp * 32u * CC_WORDS;
-        const uint32_t wa[4] = {a.x, a.y, a.z, a.w}, wb[4] = {b.x, b.y, b.z, b.w};
-        const uint32_t e0 = __shfl_sync(0xFFFFFFFFu, excl, 0);
-        cc_write(wa, wbase, s_prefix[0] + (e0 & 0xFFFFu), cut, cap);
-        cc_write(wb, wbase, s_prefix[1] + (e0 >> 16), front_list, cap);
-        if (ca) *reinterpret_cast<uint4*>(bitmap + w0) = make_uint4(0u, 0u, 0u, 0u);
-        if (cb) *reinterpret_cast<uint4*>(front + w0) = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t oa = s_prefix[0] + (wexcl & 0xFFFFu), ob = s_prefix[1] + (wexcl >> 16);
+#pragma unroll
+        for (int j = 0; j < CC_WORDS; ++j) {
+            const uint32_t wi = wbase + 32u * j + lane;
+            oa = cc_round(a[j], wi, oa, s_stage[warp], cut, cap);
+            ob = cc_round(b[j], wi, ob, s_stage[warp], front_list, cap);
+            if (a[j]) bitmap[wi] = 0u;
+            if (b[j]) front[wi] = 0u;
+        }
         if (tile == ntiles - 1 && threadIdx.x == 0) {
             const uint32_t n = s_prefix[0] + (total & 0xFFFFu);
             *n_cut_out = n;
@@ -465,7 +490,7 @@ void launch_cut_compact(uint32_t* bitmap, uint32_t* front, uint32_t n_words, uin
                         uint32_t cap, uint32_t* n_cut_out, unsigned long long* status,
                         unsigned long long* status_front, Counters* ctr, const FrameParams* fp, int grid,
                         cudaStream_t s) {
-    launch_k(k_cut_compact, grid, 256, s, bitmap, front, n_words, cut, front_list, cap, n_cut_out, status,
+    launch_k(k_cut_compact, grid, CC_THREADS, s, bitmap, front, n_words, cut, front_list, cap, n_cut_out, status,
                                        status_front, ctr, fp);
 }
 
