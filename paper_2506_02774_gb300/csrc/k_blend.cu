@@ -121,6 +121,12 @@ __device__ __forceinline__ uint32_t blend_prepare(float4& a, float4& b, float4& 
         R[2 * r] = Bc * dy;
         R[2 * r + 1] = MODE == 0 ? fmaf(Cc * dy, dy, add) : (Cc * dy) * dy;
     }
+    if (MODE == 0 && SR <= 2) {  // one float4 per row: (u, A', B' dy_r, C' dy_r^2 + log2 theta)
+        const float u = a.x, Ap = a.z * LOG2E;
+        a = make_float4(u, Ap, R[0], R[1]);
+        if (SR == 2) b = make_float4(u, Ap, R[2 % (2 * SR)], R[3 % (2 * SR)]);
+        return pmask;
+    }
     const float4 X = MODE == 0 ? make_float4(a.x, a.z * LOG2E, 0.f, 0.f) : make_float4(a.x, a.z, b.y, b.z);
     a = X;
     b = make_float4(R[0], R[1], SR > 1 ? R[2 % (2 * SR)] : 0.f, SR > 1 ? R[3 % (2 * SR)] : 0.f);
@@ -451,9 +457,23 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
                 reach[q] = warp_transpose32(sl < (uint32_t)DEPTH ? s_pm[warp][sl] : 0u);
             }
             if (!p.done) {
-                // this lane's row r = lane / T: its terms are float2 (r & 1) of part 2 + r / 2
+                // this lane's row r = lane / T.  Exact mode with strips of one or two
+                // rows: the row's whole record is the float4 of part 0 (row 0) or 2
+                // (row 1), one load per evaluation.  Otherwise X of part 0 and the
+                // row's terms: float2 (r & 1) of part 2 + r / 2.
                 const uint32_t r = lane / T;
+                const float4* wY = sbuf[buf][r == 0 ? 0 : 2][warp];
                 const float2* wR = reinterpret_cast<const float2*>(sbuf[buf][2 + r / 2][warp]) + (r & 1u);
+                auto eval = [&](uint32_t i, float4& X) -> float {
+                    if constexpr (MODE == 0 && SR <= 2) {
+                        X = wY[i];
+                        const float dx = X.x - p.fxp;
+                        return fmaf(fmaf(X.y, dx, X.z), dx, X.w);
+                    } else {
+                        X = load_x<MODE>(wA, i);
+                        return blend_rho(p, X, wR[2 * i]);
+                    }
+                };
 #pragma unroll
                 for (int q = 0; q < (DEPTH + 31) / 32; ++q) {
                     uint32_t mm = reach[q];
@@ -463,9 +483,8 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
                         const bool two = mm != 0u;
                         const uint32_t i1 = two ? 32u * q + __ffs(mm) - 1u : i0;
                         mm &= mm - 1u;
-                        const float4 X0 = load_x<MODE>(wA, i0), X1 = load_x<MODE>(wA, i1);
-                        const float2 R0 = wR[2 * i0], R1 = wR[2 * i1];
-                        const float r0 = blend_rho(p, X0, R0), r1 = blend_rho(p, X1, R1);
+                        float4 X0, X1;
+                        const float r0 = eval(i0, X0), r1 = eval(i1, X1);
                         ++evals;
                         if (!blend_step<MODE>(p, X0, wC, i0, r0, s_lut, m, lut_scale)) break;
                         if (two) {

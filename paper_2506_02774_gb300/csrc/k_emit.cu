@@ -8,7 +8,7 @@
 // per-tile work is light, so the chain of tiles moves fast.  k_emit then takes
 // 512 Gaussians per CTA tile with no ticket and no look-back (their slot range
 // is known): it gathers their records, and walks the tile's slots with all 256
-// threads (slot -> Gaussian by binary search over the CTA's offsets in shared
+// threads (slot -> Gaussian by a search over the CTA's offsets in shared
 // memory), so a Gaussian with thousands of candidate tiles costs no more per
 // thread than one with a single tile.  For each slot the tile-level form of
 // Eq. 4 (paper Sec. 4.2) decides: a kept slot gets key = tile id, a dropped one
@@ -32,7 +32,8 @@ namespace vgr {
 
 constexpr int EM_THREADS = 256;
 constexpr int EM_ITEMS = 2;
-constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per look-back tile
+constexpr int EM_TILE = EM_THREADS * EM_ITEMS;  // Gaussians per CTA tile
+static_assert(EM_TILE == 512, "the owner search takes two ballots over 32 x 16 Gaussians");
 
 uint32_t emit_tile() { return EM_TILE; }
 
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
     __shared__ float4 s_h[EM_TILE];           // c rx ry thre
     __shared__ uint32_t s_rect[EM_TILE];      // x0 | y0 << 10 | width << 20 (tiles; 16384-px images: < 2^10)
     __shared__ __half s_hh[EM_TILE];          // footprint half-height, rounded up
+    __shared__ uint32_t s_vi[EM_TILE];        // index in the in-front arrays
     __shared__ uint32_t s_hist[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     const uint32_t n_vis = min(ctr->n_vis, cap_vis);
@@ -144,6 +146,7 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
             const uint32_t r = g0 + q;
             if (r < n_vis) {
                 const uint32_t vi = order[r];
+                s_vi[q] = vi;
                 const uint2 rect = vis.rect[vi];
                 const float4 A = vis.recA[vi];
                 const float4 B = vis.recB[vi];
@@ -165,16 +168,18 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
         const uint32_t total = s_off[EM_TILE];
         const uint64_t base = base32;
         // slots in warp-sized runs: the owner of the run's first slot by a
-        // warp-uniform binary search, the other lanes' owners by counting the
+        // warp-wide search, the other lanes' owners by counting the
         // Gaussians that start inside the run (every visible Gaussian has at
         // least one slot, so starts are distinct)
         const uint32_t lane = lane_id();
         for (uint32_t j0 = (threadIdx.x & ~31u); j0 < total; j0 += EM_THREADS) {
-            uint32_t lo = 0, hi = EM_TILE;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (s_off[mid] <= j0) lo = mid; else hi = mid;
-            }
+            // the last Gaussian starting at or before j0 (offsets ascend, so the
+            // test holds on a prefix): lane k tests Gaussian 16 k, then lanes 0..15
+            // the 16 Gaussians of the last such stride -- two ballots
+            const uint32_t cm = __ballot_sync(0xFFFFFFFFu, s_off[16u * lane] <= j0);  // bit 0: s_off[0] = 0
+            const uint32_t kc = 31u - __clz(cm);
+            const uint32_t fm = __ballot_sync(0xFFFFFFFFu, lane < 16u && s_off[16u * kc + (lane & 15u)] <= j0);
+            const uint32_t lo = 16u * kc + 31u - __clz(fm);
             const uint32_t gi = lo + 1u + lane;
             const uint32_t d = (gi <= (uint32_t)EM_TILE ? s_off[gi] : 0xFFFFFFFFu) - j0;  // >= 1
             const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, d < 32u ? 1u << d : 0u);
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restri
             const bool write = valid && pos < cap;
             if (write) {
                 pair_key[pos] = key;
-                pair_val[pos] = (order[tile * EM_TILE + g] << 8) | rows;  // L1: loaded by the gather above
+                pair_val[pos] = (s_vi[g] << 8) | rows;
                 for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p][(key >> (8 * p)) & 255u], 1u);
             }
         }
