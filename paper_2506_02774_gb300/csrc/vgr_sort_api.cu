@@ -130,9 +130,10 @@ extern "C" vgr_status vgr_sort_pairs(const uint32_t* keys_in, const uint32_t* va
         if (c.tmp) cudaFree(c.tmp);
         c.tmp = nullptr;
         c.tmp_n = 0;
-        if ((e = cudaMalloc(&c.tmp, 2 * n * sizeof(uint32_t))) != cudaSuccess)
+        const uint64_t n_al = (n + 63u) & ~(uint64_t)63u;  // the value half starts 256-byte aligned
+        if ((e = cudaMalloc(&c.tmp, 2 * n_al * sizeof(uint32_t))) != cudaSuccess)
             return sort_fail(VGR_E_NOMEM, "sort ping-pong buffer", e);
-        c.tmp_n = n;
+        c.tmp_n = n_al;
     }
     cudaStream_t s = (cudaStream_t)stream;
     e = sort_pairs_enqueue(keys_in, vals_in, keys_out, vals_out, n, key_bits, c.fp, c.ctr, c.status, c.tmp,

@@ -1,6 +1,7 @@
 """The standalone pair sort (vgr_sort_pairs) against numpy's stable sort:
-bit-exact keys and values, across tile edges (3840 keys per tile), key widths
-and degenerate inputs (all equal, presorted, reversed)."""
+bit-exact keys and values, across tile edges (3840 keys per tile), key widths,
+degenerate inputs (all equal, presorted, reversed) and arrays that do not
+start on a 16-byte boundary."""
 import numpy as np
 import pytest
 
@@ -44,6 +45,24 @@ def test_degenerate_inputs():
     _sort_check(np.arange(n, dtype=np.uint32)[::-1].copy(), vals, 24)  # reversed
     few = np.random.default_rng(2).integers(0, 3, size=n).astype(np.uint32)
     _sort_check(few, np.arange(n, dtype=np.uint32), 2)         # heavy ties
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_inputs_not_16_byte_aligned(offset):
+    """Arrays that start 4, 8 or 12 bytes past a 16-byte boundary (views into
+    a larger tensor) sort exactly like aligned ones."""
+    n = 3 * 3840 + 17
+    rng = np.random.default_rng(40 + offset)
+    keys = rng.integers(0, 2**32, size=n + offset, dtype=np.uint64).astype(np.uint32)
+    vals = np.arange(n + offset, dtype=np.uint32)
+    k = torch.from_numpy(keys.view(np.int32)).cuda()[offset:]
+    v = torch.from_numpy(vals.view(np.int32)).cuda()[offset:]
+    assert k.data_ptr() % 16 != 0 and v.data_ptr() % 16 != 0
+    ko, vo = vgr.sort_pairs(k, v, 32)
+    torch.cuda.synchronize()
+    order = np.argsort(keys[offset:], kind="stable")
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), keys[offset:][order])
+    np.testing.assert_array_equal(vo.cpu().numpy().view(np.uint32), vals[offset:][order])
 
 
 def test_large_and_wide():
