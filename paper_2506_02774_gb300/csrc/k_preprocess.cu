@@ -247,11 +247,12 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
             if (v) zbits = __float_as_uint(z);
         }
         n_visible += __popc(__ballot_sync(0xFFFFFFFFu, v));
+        // one shared-memory atomic per digit: equal digits within the warp (the
+        // high bytes of neighbouring nodes' depths) are combined by the hardware,
+        // cheaper than finding the peers first
+        if (i < n_front) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const uint32_t dd = i < n_front ? ((zbits >> (8 * p)) & 255u) : 256u;
-            const uint32_t peers = match_digit(dd);
-            if (dd < 256u && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[p][dd], (uint32_t)__popc(peers));
+            for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(zbits >> (8 * p)) & 255u], 1u);
         }
         if (i < n_front) {
             vis.node[i] = node;
