@@ -21,8 +21,9 @@ constexpr int RS_BINS = 256;
 
 uint32_t radix_tile() { return RS_TILE; }
 
-// Digit histograms of up to 4 passes (shift 0, 8, 16, 24), aggregated per
-// warp with match_any before the shared-memory atomics.
+// Digit histograms of up to 4 passes (shift 0, 8, 16, 24): one shared-memory
+// atomic per key and digit (equal digits within a warp are combined by the
+// hardware), then one global atomic per nonzero bin and CTA.
 __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys,
                                                     const uint32_t* __restrict__ n32,
                                                     const unsigned long long* __restrict__ n64, uint64_t cap,
@@ -33,17 +34,10 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
     uint64_t nv = n32 ? (uint64_t)*n32 : (uint64_t)*n64;
     if (nv > cap) nv = cap;
     const uint32_t n = (uint32_t)nv;
-    const uint32_t lane = lane_id();
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
-        const uint32_t i = base + lane;
-        const bool valid = i < n;
-        const uint32_t k = valid ? keys[i] : 0u;
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? ((k >> (8 * p)) & 255u) : 256u;
-            const uint32_t peers = match_digit(d);
-            if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
-        }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_BINS; i += blockDim.x) {
@@ -55,7 +49,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__
 // One digit pass.  n comes from n32 (if non-null) or n64, clamped to cap.
 // Per tile of RS_TILE keys (warp w owns a contiguous run of 32 * RS_ITEMS):
 //  1. each warp ranks its keys: peers with the same digit come from
-//     match_any; the run leader's shared atomicAdd on the warp's digit
+//     the match instruction (last pass) or per-bit ballots; the run leader's shared atomicAdd on the warp's digit
 //     counter returns the count of earlier keys, shuffled to the peers;
 //  2. the tile's digit counts are published to the look-back words at once,
 //     so later tiles rarely wait for this one;
@@ -123,8 +117,9 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_radix_pass(const uint32_t* __
         for (int it = 0; it < RS_ITEMS; ++it) {
             const uint32_t idx = base + it * 32;
             const uint32_t d = idx < n ? ((key[it] >> shift) & 255u) : 256u;
-            // tile ids (few distinct digits per warp): the match instruction; depth
-            // keys (many distinct low digits): one ballot per digit bit, faster there
+            // the last pass (the top byte: few distinct digits per warp) by the match
+            // instruction; the lower bytes (many distinct digits) by one ballot per
+            // digit bit, faster there (depth keys and tile ids alike)
             const uint32_t peers = HW_MATCH ? __match_any_sync(0xFFFFFFFFu, d) : match_digit(d);
             const int leader = __ffs(peers) - 1;
             uint32_t before = 0;

@@ -915,7 +915,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
         launch_radix_pass(kin, vin, p == 3 ? nullptr : v->sortK[p & 1], v->sortV[p & 1], &v->ctr->n_front, nullptr,
                           v->cap_vis, 8 * p,
                           v->ctr->depth_hist[p], v->status + v->st_depth + p * v->st_depth_stride,
-                          &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s);
+                          &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s, p == 3 ? 1 : 0);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
     if (!side) {
@@ -934,7 +934,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
         launch_radix_pass(v->pairK[p & 1], v->pairV[p & 1], v->pairK[(p + 1) & 1], v->pairV[(p + 1) & 1], nullptr,
                           &v->ctr->n_cand, v->cap_pairs, 8 * p, v->ctr->tile_hist[p],
                           v->status + v->st_tile + p * v->st_tile_stride, &v->ctr->tickets[TK_SORT0 + 4 + p],
-                          v->fp_dev, v->ctr, v->grid_scan, s, 1, last ? v->ranges : nullptr, n_tiles);
+                          v->fp_dev, v->ctr, v->grid_scan, s, last ? 1 : 0, last ? v->ranges : nullptr, n_tiles);
     }
     v->last_tile_buf = tile_passes & 1;
     mark(VGR_STAGE_RANGES);

@@ -57,7 +57,8 @@ cudaError_t sort_pairs_enqueue(const uint32_t* keys_in, const uint32_t* vals_in,
         uint32_t* ko = to_out ? keys_out : tmp_keys;
         uint32_t* vo = to_out ? vals_out : tmp_vals;
         launch_radix_pass(kin, vin, ko, vo, nullptr, &ctr->n_pairs, n, 8 * p, ctr->depth_hist[p],
-                          status + (size_t)p * stride, &ctr->tickets[TK_SORT0 + p], fp, ctr, grid, s);
+                          status + (size_t)p * stride, &ctr->tickets[TK_SORT0 + p], fp, ctr, grid, s,
+                          p == passes - 1 ? 1 : 0);
         kin = ko;
         vin = vo;
     }
