@@ -39,22 +39,15 @@ namespace vgr {
 // a Gaussian with u + Bx < 0.5 or u - Bx > T tiles_x - 0.5 (or likewise in
 // v) has no candidate tile in preprocess and can be left out here.  The
 // canonical mode's 3-sigma box is bounded the same way.
-// Set bit n of bm in the lanes where pred holds, one atomic per run of lanes
-// that hit the same word (callers pass ascending n across the lanes, so a
-// word's lanes are contiguous): a segmented OR by shuffles gives each run's
-// first lane the run's bits.  All 32 lanes call it.
+// Set bit n of bm in the lanes where pred holds, one atomic per word: the
+// lanes that hit the same word (the match instruction; a warp's nodes are
+// few words) OR their bits together and the lowest of them stores them.
+// All 32 lanes call it.
 __device__ __forceinline__ void warp_bitmap_set(uint32_t* bm, uint32_t n, bool pred) {
-    const uint32_t lane = lane_id();
     const uint32_t w = pred ? n >> 5 : 0xFFFFFFFFu;
-    uint32_t bits = pred ? 1u << (n & 31u) : 0u;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t ob = __shfl_down_sync(0xFFFFFFFFu, bits, d);
-        const uint32_t ow = __shfl_down_sync(0xFFFFFFFFu, w, d);
-        if (lane + d < 32u && ow == w) bits |= ob;
-    }
-    const uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, w, 1);
-    if (pred && (lane == 0u || wprev != w)) atomicOr(&bm[w], bits);
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, w);
+    const uint32_t bits = __reduce_or_sync(peers, pred ? 1u << (n & 31u) : 0u);
+    if (pred && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicOr(&bm[w], bits);
 }
 
 // With weight interpolation the rendered Gaussian of a cut node n is not n's
