@@ -175,9 +175,10 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
     return dict(
         lod=16 * E + 4 * C + 4 * C + 2 * N / 8,      # node tests, parent ids, prev cut read, two bitmaps set
         compact=2 * (N / 8 * 2) + 4 * C + 4 * F,     # two bitmaps read + cleared, cut and in-front ids written
-        preprocess=(4 + 16 + 32 + 52) * F,           # ids, centre, covariance + opacity, records out
+        # ids, centre, covariance + opacity, records out; SH in and rgb out (visible)
+        preprocess=(4 + 16 + 32 + 52) * F + (shb + 16) * V,
         depth_sort=4 * 2 * 8 * F + 4 * F,            # 4 passes x (key+value) read+write, histogram read
-        color=4 * F + (4 + 16 + shb) * V + 16 * V,   # culled flags, node, centre, SH; rgb out
+        color=0,                                     # evaluated in preprocess
         emit=(4 + 4 + 8 + 32) * V + 8 * P0,          # order, count, rect, record halves; slots
         tile_sort=tile_passes * 2 * 8 * P0,
         ranges=4 * P + 8 * (W // 16 + 1) * (H // 16 + 1),
@@ -447,7 +448,7 @@ def run_ours(args) -> dict:
         st_ms, n_st = np.zeros(2), min(args.steps, 50)
         for i in range(args.warmup, args.warmup + n_st):
             r_i = vit.render(cams[i], tau)
-            st_ms += np.array([r_i.stats["stage_ms"][k] for k in ("preprocess", "color")])
+            st_ms += np.array([r_i.stats["stage_ms"][k] for k in ("lod", "preprocess")])
         st_ms /= n_st
         i1 = args.warmup + n_st - 1
         vd.render(cams[i1 - 1], tau)
@@ -458,7 +459,7 @@ def run_ours(args) -> dict:
                              ms_per_step=round(msi / args.steps, 4),
                              front=round(float(np.mean([x["front_count"] for x in sti])), 1),
                              visible=round(float(np.mean([x["visible_count"] for x in sti])), 1),
-                             stage_ms=dict(preprocess=round(st_ms[0], 4), color=round(st_ms[1], 4)),
+                             stage_ms=dict(lod=round(st_ms[0], 4), preprocess=round(st_ms[1], 4)),
                              psnr_vs_plain_db=round(10 * math.log10(1.0 / mse), 2) if mse > 0 else None)
         vit.close()
         vd.close()
@@ -512,8 +513,8 @@ def run_ours(args) -> dict:
     hbm_stages = {s: fb[s] / (shares[s] * 1e-3) / 1e9 for s in vgr.STAGES if shares[s] > 0}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     roof_blend = blend_roofline(mean, shares["blend"], sms, peaks, fb["blend"], hbm_stages.get("blend", 0.0))
-    roof_color = hbm_roofline("color", "k_color", "k_preprocess.cu", fb["color"], shares["color"], peaks,
-                              mean["visible_count"])
+    roof_pre = hbm_roofline("preprocess", "k_preprocess", "k_preprocess.cu", fb["preprocess"], shares["preprocess"],
+                            peaks, mean["front_count"])
     out = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=ws, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms / args.steps, 4), higher_is_better=True,
                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
@@ -523,7 +524,7 @@ def run_ours(args) -> dict:
                gpu_launches=int(kernels),
                launch_mode="cuda-graph replay per frame" if not args.no_graph else "plain launch loop",
                value_plain_loop=round(value_loop, 2),
-               roofline=roof_blend, roofline_blend=roof_blend, roofline_color=roof_color, clocks=clocks,
+               roofline=roof_blend, roofline_blend=roof_blend, roofline_preprocess=roof_pre, clocks=clocks,
                frame_latency_ms=dict(p50=round(1e3 * float(np.percentile(lat, 50)), 4),
                                      p99=round(1e3 * float(np.percentile(lat, 99)), 4)),
                stage_ms={k: round(v, 4) for k, v in shares.items()},

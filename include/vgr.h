@@ -114,12 +114,11 @@ typedef struct {
     uint32_t timing;         /* 1: record per-stage device times into vgr_frame_stats */
     uint32_t use_graph;      /* 1: replay each frame as one captured CUDA graph (captured on first use per
                                 cut mode and buffer parity; re-captured after a buffer grows or the image
-                                size changes; inside it the colour pass runs on a second stream the view
-                                owns, beside the sorts); ignored while timing is set.  Default 0. */
+                                size changes); ignored while timing is set.  Default 0. */
     uint64_t cut_capacity;   /* initial capacities; 0 = automatic.  Grown on demand. */
     uint64_t pair_capacity;
     uint32_t lod_budget;     /* max nodes one thread explores when expanding a cut node (0 = 4096) */
-    uint32_t grid_wide;      /* CTAs of the grid-stride kernels (LoD, preprocess, colour, ranges);
+    uint32_t grid_wide;      /* CTAs of the grid-stride kernels (LoD, preprocess with colour, ranges);
                                 0 = 8 per SM.  Launch geometry only: results do not depend on it. */
     uint32_t grid_scan;      /* CTAs of the ticketed look-back kernels (compaction, radix passes,
                                 emission); 0 = 4 per SM.  Launch geometry only. */
@@ -143,6 +142,9 @@ enum { VGR_HOOK_WITHHOLD_LOOKBACK = 1,
        VGR_HOOK_FULL_STRIP_WALK = 2  /* the blend walks every record of a strip at every pixel instead of only
                                         the records whose footprint box covers the pixel (same image) */ };
 
+/* Stages of stage_ms.  The colour (SH -> RGB) is evaluated by the preprocess
+ * kernel, so VGR_STAGE_PREPROCESS includes it and VGR_STAGE_COLOR stays
+ * empty (kept so that the indices of the later stages do not move). */
 enum { VGR_STAGE_LOD = 0, VGR_STAGE_COMPACT, VGR_STAGE_PREPROCESS, VGR_STAGE_DEPTH_SORT, VGR_STAGE_COLOR,
        VGR_STAGE_EMIT, VGR_STAGE_TILE_SORT, VGR_STAGE_RANGES, VGR_STAGE_BLEND, VGR_N_STAGES };
 

@@ -17,9 +17,13 @@
 // are those whose pixel-centre rectangle meets the box.  A Gaussian is kept
 // when it has at least one candidate tile; the tile-level test (Eq. 4 over
 // each candidate tile) runs in the emission, where the work is balanced over
-// candidate slots.  Colour (real SH up to degree 3, +0.5, clamped at 0) is a
-// separate dense kernel over the in-front list (visible entries only), so
-// the 192-byte SH reads run at full occupancy, in ascending node order.
+// candidate slots.  Colour (real SH up to degree 3, +0.5, clamped at 0) is
+// evaluated here too, for the visible entries: the SH row (192 bytes in FP32
+// at degree 3) is requested together with the centre and the covariance, so
+// the projection arithmetic runs while it arrives, and the kernel streams
+// all of a node's bytes in one pass (two 256-thread CTAs per SM, registers
+// for the whole row in flight).  As a separate pass the colour could not
+// overlap the latency-bound sorts, which hold every SM slot they can get.
 #include <cuda_fp16.h>
 
 #include "vgr_internal.cuh"
@@ -120,12 +124,14 @@ struct Store<VGR_STORE_HALF> {
     }
 };
 
-template <int STORE, bool INTERP>
-__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
+template <int DEG, int STORE, bool INTERP>
+__global__ void __launch_bounds__(PRE_THREADS, 2) k_preprocess(SceneDev sc, const uint32_t* __restrict__ front,
                                                             const uint32_t* __restrict__ n_front_p, uint32_t cap,
                                                             const FrameParams* __restrict__ fp, VisBuffers vis,
                                                             Counters* __restrict__ ctr) {
     pdl_wait();
+    constexpr int K = (DEG + 1) * (DEG + 1);  // SH coefficients per channel
+    constexpr int NSH = ((3 * K + 7) / 8) * 8;
     __shared__ uint32_t s_hist[4][256];  // digit histograms of the depth keys (the sort's passes)
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     __syncthreads();
@@ -155,6 +161,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
         int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
         if (v) {
             float4 m = sc.cr[node];
+            float shc[NSH];
+            Store<STORE>::template sh<K>(sc, node, shc);  // in flight with the centre and covariance
             float S[6], lnth = 0.f;
             Store<STORE>::cov(sc, node, S, theta, lnth);  // in flight together with the centre
             if constexpr (INTERP) {
@@ -244,7 +252,30 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
                              ((uint32_t)__half_as_ushort(__float2half_ru(bx)) << 16);
                 }
             }
-            if (v) zbits = __float_as_uint(z);
+            if (v) {
+                // colour: rgb = sum_lm c_lm Y_lm(d) + 0.5, clamped at 0, d = (mu - C)/|mu - C|
+                // (with interpolation the coefficients and the mean move towards the parent's)
+                if constexpr (INTERP) {
+                    if (lw > 0.f) {
+                        float shp[NSH];
+                        Store<STORE>::template sh<K>(sc, sc.parent[node], shp);
+#pragma unroll
+                        for (int j = 0; j < 3 * K; ++j) shc[j] = fmaf(lw, shp[j] - shc[j], shc[j]);
+                    }
+                }
+                float Y[K];
+                const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                sh_basis<DEG>(dx * inv, dy * inv, dz * inv, Y);
+                float cr = 0.5f, cg = 0.5f, cbl = 0.5f;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    cr = fmaf(shc[3 * kk + 0], Y[kk], cr);
+                    cg = fmaf(shc[3 * kk + 1], Y[kk], cg);
+                    cbl = fmaf(shc[3 * kk + 2], Y[kk], cbl);
+                }
+                vis.rgb[i] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cbl, 0.f), 0.f);
+                zbits = __float_as_uint(z);
+            }
         }
         n_visible += __popc(__ballot_sync(0xFFFFFFFFu, v));
         // one shared-memory atomic per digit: equal digits within the warp (the
@@ -272,60 +303,6 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess(SceneDev sc, cons
     }
 }
 
-// Colour of the visible Gaussians (dense, no barriers), in visible order,
-// i.e. ascending node id, so consecutive threads read neighbouring SH rows:
-// rgb = sum_lm c_lm Y_lm(d) + 0.5, clamped at 0, d = (mu - C)/|mu - C|.
-template <int DEG, int STORE, bool INTERP>
-__global__ void __launch_bounds__(256) k_color(SceneDev sc, const uint32_t* __restrict__ vis_node,
-                                               const uint32_t* __restrict__ vis_ntile,
-                                               const float* __restrict__ vis_lw, uint32_t cap,
-                                               const FrameParams* __restrict__ fp, const Counters* __restrict__ ctr,
-                                               float4* __restrict__ rgb_out) {
-    pdl_wait();
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    const uint32_t n = min(ctr->n_front, cap);
-    const float Cx = fp->pos[0], Cy = fp->pos[1], Cz = fp->pos[2];
-    const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    // the next entry's node id and tile count are loaded one round ahead
-    uint32_t node_next = r < n ? vis_node[r] : 0u, nt_next = r < n ? vis_ntile[r] : 0u;
-    for (; r < n; r += stride) {
-        const uint32_t node = node_next, nt = nt_next;
-        node_next = r + stride < n ? vis_node[r + stride] : 0u;
-        nt_next = r + stride < n ? vis_ntile[r + stride] : 0u;
-        if (nt == 0u) continue;  // culled
-        float shc[((3 * K + 7) / 8) * 8];
-        Store<STORE>::template sh<K>(sc, node, shc);
-        float4 m = sc.cr[node];
-        if constexpr (INTERP) {  // coefficients and mean towards the parent's (weight from preprocess)
-            const float lw = vis_lw[r];
-            if (lw > 0.f) {
-                const uint32_t p = sc.parent[node];
-                float shp[((3 * K + 7) / 8) * 8];
-                Store<STORE>::template sh<K>(sc, p, shp);
-                const float4 mp = sc.cr[p];
-#pragma unroll
-                for (int j = 0; j < 3 * K; ++j) shc[j] = fmaf(lw, shp[j] - shc[j], shc[j]);
-                m.x = lod_lerp_rn(m.x, mp.x, lw);
-                m.y = lod_lerp_rn(m.y, mp.y, lw);
-                m.z = lod_lerp_rn(m.z, mp.z, lw);
-            }
-        }
-        const float dx = m.x - Cx, dy = m.y - Cy, dz = m.z - Cz;
-        float Y[K];
-        const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        sh_basis<DEG>(dx * inv, dy * inv, dz * inv, Y);
-        float cr = 0.5f, cg = 0.5f, cbl = 0.5f;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            cr = fmaf(shc[3 * kk + 0], Y[kk], cr);
-            cg = fmaf(shc[3 * kk + 1], Y[kk], cg);
-            cbl = fmaf(shc[3 * kk + 2], Y[kk], cbl);
-        }
-        rgb_out[r] = make_float4(fmaxf(cr, 0.f), fmaxf(cg, 0.f), fmaxf(cbl, 0.f), 0.f);
-    }
-}
-
 // ln(opacity) next to the opacity (Eq. 4 needs ln theta per Gaussian)
 __global__ void k_prepare(float4* covB, uint32_t n, int half) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -346,40 +323,27 @@ void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s) {
 void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
                        const FrameParams* fp, VisBuffers vis, Counters* ctr, bool interp, int grid, cudaStream_t s) {
     const bool half = sc.storage == VGR_STORE_HALF;
-    if (interp) {
-        if (half) launch_k(k_preprocess<VGR_STORE_HALF, true>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
-        else launch_k(k_preprocess<VGR_STORE_FP32, true>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
-    } else {
-        if (half) launch_k(k_preprocess<VGR_STORE_HALF, false>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
-        else launch_k(k_preprocess<VGR_STORE_FP32, false>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr);
-    }
-}
-
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, const float* vis_lw,
-                  uint32_t cap, const FrameParams* fp, const Counters* ctr, float4* rgb, bool interp, int grid,
-                  cudaStream_t s) {
-    const bool half = sc.storage == VGR_STORE_HALF;
-#define VGR_COLOR_LAUNCH(D, ST, IN) \
-    launch_k(k_color<D, ST, IN>, grid, 256, s, sc, vis_node, vis_ntile, vis_lw, cap, fp, ctr, rgb)
-#define VGR_COLOR_CASE(D)                                            \
-    case D:                                                          \
-        if (interp) {                                                \
-            if (half) VGR_COLOR_LAUNCH(D, VGR_STORE_HALF, true);     \
-            else VGR_COLOR_LAUNCH(D, VGR_STORE_FP32, true);          \
-        } else {                                                     \
-            if (half) VGR_COLOR_LAUNCH(D, VGR_STORE_HALF, false);    \
-            else VGR_COLOR_LAUNCH(D, VGR_STORE_FP32, false);         \
-        }                                                            \
+#define VGR_PRE_LAUNCH(D, ST, IN) \
+    launch_k(k_preprocess<D, ST, IN>, grid, PRE_THREADS, s, sc, front, n_front, cap, fp, vis, ctr)
+#define VGR_PRE_CASE(D)                                            \
+    case D:                                                        \
+        if (interp) {                                              \
+            if (half) VGR_PRE_LAUNCH(D, VGR_STORE_HALF, true);     \
+            else VGR_PRE_LAUNCH(D, VGR_STORE_FP32, true);          \
+        } else {                                                   \
+            if (half) VGR_PRE_LAUNCH(D, VGR_STORE_HALF, false);    \
+            else VGR_PRE_LAUNCH(D, VGR_STORE_FP32, false);         \
+        }                                                          \
         break;
     switch (sc.sh_degree) {
-        VGR_COLOR_CASE(0)
-        VGR_COLOR_CASE(1)
-        VGR_COLOR_CASE(2)
-        VGR_COLOR_CASE(3)
+        VGR_PRE_CASE(0)
+        VGR_PRE_CASE(1)
+        VGR_PRE_CASE(2)
+        VGR_PRE_CASE(3)
         default: break;
     }
-#undef VGR_COLOR_CASE
-#undef VGR_COLOR_LAUNCH
+#undef VGR_PRE_CASE
+#undef VGR_PRE_LAUNCH
 }
 
 uint32_t preprocess_tile() { return PRE_THREADS; }

@@ -1,11 +1,9 @@
 // vgr_capi.cu -- the C ABI (include/vgr.h): hierarchy upload and validation,
 // per-view buffers, and the per-frame launch sequence
 //   LoD (temporal update or top-down levels) -> cut compaction ->
-//   preprocess -> depth sort -> colour -> emission -> tile sort (its last
+//   preprocess (with colour) -> depth sort -> emission -> tile sort (its last
 //   pass records the tile ranges) -> blend order -> blend
-// all enqueued on the view's stream (or replayed as one captured graph, in
-// which the colour pass runs on a second stream beside the depth sort, the
-// emission and the tile sort).
+// all enqueued on the view's stream (or replayed as one captured graph).
 // Counts stay on the device (every kernel reads its element count from
 // device memory), so a frame needs no host round trip until its end, where
 // a 56-byte status block and the cut sizes are read back: buffer overflows
@@ -188,9 +186,6 @@ struct vgr_view {
     PendingFrame pend;
     cudaEvent_t done_ev = nullptr;
     cudaEvent_t join_ev = nullptr;  // end of this view's branch in a captured batch
-    // the colour pass runs beside the sorts and the emission on a second stream
-    cudaStream_t side = nullptr;
-    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     uint64_t uid = 0;               // unique per view ever created (batch graph keys)
     uint64_t gen = 0;               // bumped whenever the view's buffers change (graphs invalid)
     uint64_t vis_bytes = 0, pair_bytes = 0, img_bytes = 0, fixed_bytes = 0, status_bytes = 0, cut_bytes = 0;
@@ -637,9 +632,6 @@ void destroy_view(vgr_view* v) {
         if (e) cudaEventDestroy(e);
     if (v->done_ev) cudaEventDestroy(v->done_ev);
     if (v->join_ev) cudaEventDestroy(v->join_ev);
-    if (v->side_fork) cudaEventDestroy(v->side_fork);
-    if (v->side_join) cudaEventDestroy(v->side_join);
-    if (v->side) cudaStreamDestroy(v->side);
     forget_batches(v->uid);
     if (v->own_stream && v->stream) cudaStreamDestroy(v->stream);
     delete v;
@@ -739,9 +731,6 @@ vgr_status vgr_create_view(vgr_hierarchy* h, const vgr_view_opts* opts, vgr_view
     {
         cudaError_t ce = cudaEventCreateWithFlags(&v->done_ev, cudaEventDisableTiming);
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->join_ev, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->side_fork, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&v->side_join, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking);
         if (ce != cudaSuccess) { destroy_view(v); return fail(VGR_E_CUDA, "event: %s", cudaGetErrorString(ce)); }
         static std::atomic<uint64_t> next_uid{1};
         v->uid = next_uid.fetch_add(1);
@@ -846,7 +835,7 @@ constexpr int EMIT_GRID_NUM = 6;
 
 uint32_t frame_kernels(const vgr_view* v, bool scratch, int tile_passes) {
     const uint32_t lod = scratch ? v->h->max_depth + 1u : 1u;
-    return lod + 1u /*compact*/ + 1u /*preprocess*/ + 4u /*depth passes*/ + 1u /*color*/ +
+    return lod + 1u /*compact*/ + 1u /*preprocess, with colour*/ + 4u /*depth passes*/ +
            2u /*slot scan, emit*/ + (uint32_t)tile_passes + 1u /*tile order (finishes the ranges)*/ + 1u /*blend*/;
 }
 
@@ -856,17 +845,14 @@ void frame_readback(vgr_view* v, cudaStream_t s) {
     cudaMemcpyAsync(v->vstate_host, v->vstate, sizeof(ViewState), cudaMemcpyDeviceToHost, s);
 }
 
-// Enqueue one frame.  'scratch' selects the top-down cut; 'captured': the
-// frame is being captured into a graph, where the colour pass runs on the
-// side stream (launched one by one, the extra stream calls cost more host
-// time than the overlap saves).  'own_blend' false: the frame stops before
-// the blend, which a batch runs over all its views (frame_readback then
-// follows that blend).  Returns the number of kernels launched.
-uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured, bool own_blend = true) {
+// Enqueue one frame.  'scratch' selects the top-down cut.  'own_blend' false:
+// the frame stops before the blend, which a batch runs over all its views
+// (frame_readback then follows that blend).  Returns the number of kernels
+// launched.
+uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool own_blend = true) {
     const SceneDev& sc = v->h->dev;
     cudaStream_t s = v->stream;
     const bool timing = v->opts.timing != 0;
-    const bool side = captured && !timing;
     auto mark = [&](int i) { if (timing) cudaEventRecord(v->ev[i], s); };
     const FrameParams& fh = *v->fp_host;
     const uint32_t n_tiles = fh.tiles_x * fh.tiles_y;
@@ -894,17 +880,6 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
     mark(VGR_STAGE_PREPROCESS);
     launch_preprocess(sc, v->front_list, &v->ctr->n_front, v->cap_cut, v->fp_dev, v->vis, v->ctr, fh.lod_interp != 0,
                       v->grid_wide, s);
-    if (side) {
-        // colour (bandwidth-bound) on the side stream, beside the depth sort,
-        // emission and tile sort (latency-bound); joined before the blend
-        cudaEventRecord(v->side_fork, s);
-        cudaStreamWaitEvent(v->side, v->side_fork, 0);
-        pdl_state().plain_next = true;
-        launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb,
-                     fh.lod_interp != 0, v->grid_wide, v->side);
-        cudaEventRecord(v->side_join, v->side);
-        pdl_state().plain_next = true;  // the depth sort follows an event record on s
-    }
     mark(VGR_STAGE_DEPTH_SORT);
     // every potentially visible entry is sorted; culled ones carry the key
     // 0xFFFFFFFF and land last (the digit histograms come from preprocess)
@@ -918,11 +893,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
                           &v->ctr->tickets[TK_SORT0 + p], v->fp_dev, v->ctr, v->grid_scan, s, p == 3 ? 1 : 0);
     }
     const uint32_t* order = v->sortV[1];  // after 4 passes
-    if (!side) {
-        mark(VGR_STAGE_COLOR);
-        launch_color(sc, v->vis.node, v->vis.ntile, v->vis.lw, v->cap_vis, v->fp_dev, v->ctr, v->vis.rgb,
-                     fh.lod_interp != 0, v->grid_wide, s);
-    }
+    mark(VGR_STAGE_COLOR);  // (evaluated in preprocess: the stage is empty)
     mark(VGR_STAGE_EMIT);
     const uint32_t sentinel = (uint32_t)((1ull << (8 * tile_passes)) - 1ull);
     launch_emit(order, v->cap_vis, v->vis, v->slot_off, v->pairK[0], v->pairV[0], v->cap_pairs, tile_passes, sentinel,
@@ -939,10 +910,6 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
     v->last_tile_buf = tile_passes & 1;
     mark(VGR_STAGE_RANGES);
     launch_tile_order(v->ranges, n_tiles, v->tile_order, v->ctr, s);
-    if (side) {
-        cudaStreamWaitEvent(s, v->side_join, 0);  // the colour pass is done
-        pdl_state().plain_next = true;
-    }
     if (!own_blend) return frame_kernels(v, scratch, tile_passes) - 1u;  // a batch blend follows
     mark(VGR_STAGE_BLEND);
     launch_blend(v->fp_dev, nullptr, v->tile_order, n_tiles, &v->ctr->blend_next,
@@ -958,7 +925,7 @@ uint32_t enqueue_frame(vgr_view* v, bool scratch, int tile_passes, bool captured
 // (top-down?, parity) pair, captured on first use.
 vgr_status run_frame(vgr_view* v, bool scratch, int tile_passes, uint32_t n_tiles, uint32_t* kernels) {
     if (!v->opts.use_graph || v->opts.timing) {
-        *kernels += enqueue_frame(v, scratch, tile_passes, false);
+        *kernels += enqueue_frame(v, scratch, tile_passes);
         VGR_CK(cudaGetLastError());
         return VGR_OK;
     }
@@ -969,7 +936,7 @@ vgr_status run_frame(vgr_view* v, bool scratch, int tile_passes, uint32_t n_tile
     cudaGraphExec_t& ge = v->graph[scratch ? 1 : 0][v->parity];
     if (!ge) {
         VGR_CK(cudaStreamBeginCapture(v->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_frame(v, scratch, tile_passes, true);
+        enqueue_frame(v, scratch, tile_passes);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(v->stream, &g);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1247,7 +1214,7 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
             vgr_view* v = views[i];
             e = cudaStreamWaitEvent(v->stream, bs.fork, 0);
             if (e != cudaSuccess) break;
-            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, true, !shared[i]);
+            enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, !shared[i]);
             e = cudaEventRecord(v->join_ev, v->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
         }

@@ -86,9 +86,6 @@ struct VisBuffers {
 void launch_preprocess(const SceneDev& sc, const uint32_t* front, const uint32_t* n_front, uint32_t cap,
                        const FrameParams* fp, VisBuffers vis, Counters* ctr, bool interp, int grid, cudaStream_t s);
 uint32_t preprocess_tile();
-void launch_color(const SceneDev& sc, const uint32_t* vis_node, const uint32_t* vis_ntile, const float* vis_lw,
-                  uint32_t cap, const FrameParams* fp, const Counters* ctr, float4* rgb, bool interp, int grid,
-                  cudaStream_t s);
 void prepare_scene(float4* covB, uint32_t n, cudaStream_t s);
 void prepare_scene_half(float4* covB, uint32_t n, cudaStream_t s);
 
