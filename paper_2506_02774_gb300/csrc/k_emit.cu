@@ -4,7 +4,7 @@
 //
 // Two kernels.  k_slot_scan gives every visible Gaussian, in depth order (the
 // output of the depth sort), the first of its pair slots: an exclusive scan of
-// the candidate-tile counts by decoupled look-back over tiles of 2048, whose
+// the candidate-tile counts by decoupled look-back over tiles of 4096, whose
 // per-tile work is light, so the chain of tiles moves fast.  k_emit then takes
 // 512 Gaussians per CTA tile with no ticket and no look-back (their slot range
 // is known): it gathers their records, and walks the tile's slots with all 256
@@ -38,7 +38,7 @@ static_assert(EM_TILE == 512, "the owner search takes two ballots over 32 x 16 G
 uint32_t emit_tile() { return EM_TILE; }
 
 constexpr int SS_THREADS = 256;
-constexpr int SS_ITEMS = 8;
+constexpr int SS_ITEMS = 16;
 constexpr int SS_TILE = SS_THREADS * SS_ITEMS;  // Gaussians per look-back tile of the slot scan
 
 uint32_t slot_scan_tile() { return SS_TILE; }
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(SS_THREADS) k_slot_scan(const uint32_t* __rest
     }
 }
 
-__global__ void __launch_bounds__(EM_THREADS, 6) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
+__global__ void __launch_bounds__(EM_THREADS, 4) k_emit(const uint32_t* __restrict__ order, uint32_t cap_vis,
                                                      VisBuffers vis, const uint32_t* __restrict__ slot_off,
                                                      uint32_t* __restrict__ pair_key,
                                                      uint32_t* __restrict__ pair_val, uint64_t cap, int tile_passes,
