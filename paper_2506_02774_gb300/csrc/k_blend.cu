@@ -50,7 +50,7 @@ namespace vgr {
 constexpr int BL_THREADS = 256;          // 8 warps: a warp shades one strip of 32 pixels at a time
 constexpr int BL_WARPS = BL_THREADS / 32;
 constexpr int BL_SCAN = 128;   // pair values scanned per batch (4 per lane, loaded one batch ahead)
-constexpr int BL_MIN_CTAS = 5; // resident CTAs per SM the register budget is set for (48 registers)
+constexpr int BL_MIN_CTAS = 4; // resident CTAs per SM the register budget is set for (up to 64 registers)
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t WORK_TILE_BITS = 20;  // work item = view << 20 | tile
 constexpr uint32_t WORK_TILE_MASK = (1u << WORK_TILE_BITS) - 1u;
