@@ -485,6 +485,41 @@ def run_ours(args) -> dict:
         except vgr.VgrError as e:
             exp_lut = dict(error=str(e))
 
+    # ---- without the preemptive filter (Sec. 4.2): 3-sigma square footprints,
+    # every tile of the box kept, alpha computed before the alpha* test at every
+    # pixel of every pair; the same walk, timed like the headline, and the image
+    # difference from the filtered render of the same frame
+    canonical = None
+    if not args.no_canonical:
+        vc = vgr.View(h, stream=stream.cuda_stream, use_graph=not args.no_graph, filter=vgr.FILTER_CANONICAL)
+        msc, _, stc, _ = timed(vc)
+        vc.close()
+        vct = vgr.View(h, stream=stream.cuda_stream, timing=True, filter=vgr.FILTER_CANONICAL)
+        vd = vgr.View(h, stream=stream.cuda_stream)
+        for i in range(args.warmup):
+            vct.render(cams[i], tau)
+        st_ms, n_st = np.zeros(3), min(args.steps, 50)
+        for i in range(args.warmup, args.warmup + n_st):
+            r_c = vct.render(cams[i], tau)
+            st_ms += np.array([r_c.stats["stage_ms"][k] for k in ("emit", "tile_sort", "blend")])
+        st_ms /= n_st
+        i1 = args.warmup + n_st - 1  # the last frame above, filtered
+        vd.render(cams[i1 - 1], tau)
+        r_d = vd.render(cams[i1], tau)
+        img_c, img_d = r_c.image().double(), r_d.image().double()
+        mse = float(((img_c - img_d) ** 2).mean())
+        value_c = frames / (msc / 1e3)
+        canonical = dict(value=round(value_c, 2), unit="frames/s", ms_per_step=round(msc / args.steps, 4),
+                         filter_speedup=round(value / value_c, 3),
+                         pairs=round(float(np.mean([x["pair_count"] for x in stc])), 1),
+                         pixel_pair_evals=round(float(np.mean([x["pixel_pair_evals"] for x in stc])), 1),
+                         stage_ms=dict(emit=round(st_ms[0], 4), tile_sort=round(st_ms[1], 4),
+                                       blend=round(st_ms[2], 4)),
+                         psnr_vs_filtered_db=round(10 * math.log10(1.0 / mse), 2) if mse > 0 else None,
+                         max_abs_vs_filtered=round(float((img_c - img_d).abs().max()), 6))
+        vct.close()
+        vd.close()
+
     # ---- end to end through the host-buffer entry point
     host_img = torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
     hp = host_img.data_ptr()
@@ -536,6 +571,7 @@ def run_ours(args) -> dict:
                frustum_lod=frustum_lod,
                weight_interp=weight_interp,
                exp_lut=exp_lut,
+               canonical_filter=canonical,
                setup_s=dict(generate=round(t_gen, 1), upload=round(t_up, 1)))
     view.close()
     if args.config == "city" and not args.leaves and not args.no_served:
@@ -775,6 +811,8 @@ def main():
     ap.add_argument("--no-frustum", action="store_true", help="skip the frustum-aware LoD run of the walk")
     ap.add_argument("--no-interp", action="store_true", help="skip the weight-interpolation run of the walk")
     ap.add_argument("--no-lut", action="store_true", help="skip the Eq. 5 lookup-table run of the walk")
+    ap.add_argument("--no-canonical", action="store_true",
+                    help="skip the run of the walk without the preemptive filter (3-sigma binning)")
     ap.add_argument("--no-served", action="store_true", help="skip the serving leg")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)
