@@ -19,7 +19,7 @@ import os
 
 from . import View
 
-GRID_WIDE_PER_SM = (2, 4, 8, 16)   # grid-stride kernels: LoD, preprocess, colour, ranges
+GRID_WIDE_PER_SM = (2, 4, 8, 16)   # grid-stride kernels: LoD, preprocess (with colour), ranges
 GRID_SCAN_PER_SM = (2, 3, 4, 6)    # ticketed look-back kernels: compaction, radix passes, emission
 BLEND_DEPTHS = (16, 32, 48)        # Gaussians a blend warp stages per chunk
 TILE_SIZES = (8, 16, 32)           # tile side in pixels
