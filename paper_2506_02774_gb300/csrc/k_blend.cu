@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
     __shared__ float s_lut[MODE == 2 ? 260 : 1];
     __shared__ WarpItem s_item[BL_WARPS];
     __shared__ uint32_t s_pm[BL_WARPS][DEPTH];   // staged records' pixel masks
+    __shared__ __align__(16) float s_px[BL_WARPS][96];  // a finished strip's pixels, RGB
     __shared__ uint32_t s_claim;                 // next (slot, strip) item of this CTA
     __shared__ uint32_t s_slot_tile[4], s_slot_tag[4], s_slot_read[4];
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -501,13 +502,33 @@ __global__ void __launch_bounds__(BL_THREADS, BL_MIN_CTAS) k_blend(const FramePa
         }
         cp_async_wait<0>();  // the chunk staged ahead, if the strip stopped early
         const uint32_t cx = lane % T, cy = lane / T;
-        if (cx < it.nx && cy < it.ny) {
+        float* const host_image = it.host_image;
+        // a whole strip whose rows start 16-byte aligned (image width a multiple of
+        // 4): its 32 pixels staged in shared memory and stored as float4, SR rows
+        // of 3T/4 float4 each (long aligned bursts over the host link)
+        const bool whole = it.nx == (uint32_t)T && it.ny == (uint32_t)SR && (it.width & 3u) == 0u &&
+                           ((reinterpret_cast<uintptr_t>(host_image) & 15u) == 0u);
+        if (whole) {
+            float* s = s_px[warp];
+            s[3 * lane + 0] = p.cr;
+            s[3 * lane + 1] = p.cg;
+            s[3 * lane + 2] = p.cb;
+            __syncwarp();
+            constexpr int F4_ROW = 3 * T / 4;
+            if (lane < 24) {  // 96 floats = 24 float4
+                const uint32_t r = lane / F4_ROW, c4 = lane % F4_ROW;
+                const float4 val = reinterpret_cast<const float4*>(s)[lane];
+                const size_t at4 = ((size_t)it.at + (size_t)r * it.width) * 3 + 4u * c4;
+                *reinterpret_cast<float4*>(it.image + at4) = val;
+                if (host_image) *reinterpret_cast<float4*>(host_image + at4) = val;  // pinned host buffer
+            }
+            __syncwarp();
+        } else if (cx < it.nx && cy < it.ny) {
             const size_t at = ((size_t)it.at + (size_t)cy * it.width + cx) * 3;
             float* o = it.image + at;
             o[0] = p.cr;
             o[1] = p.cg;
             o[2] = p.cb;
-            float* const host_image = it.host_image;
             if (host_image) {  // the caller's pinned host buffer, over the host link
                 float* q = host_image + at;
                 q[0] = p.cr;
