@@ -272,6 +272,26 @@ vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, 
                                  vgr_frame* out);
 
 /*
+ * Pipelined host images, for a loop of frames whose images go to host
+ * memory: as vgr_render_frame_host, except that the copy of the image into
+ * host_rgb (caller-owned, height x width x 3 floats; pinned memory lets the
+ * copy engine do it without the host) is enqueued on the view's copy stream
+ * once the frame's status has been read, and overlaps the view's next frame,
+ * which writes the view's other device image.  Returns when the frame's
+ * kernels have finished (replays included) without waiting for the copy; out
+ * is filled as by vgr_render_frame, out->image being the frame's device image
+ * (valid until the next frame).  Copies land in the order of the frames.
+ * vgr_wait_host_images waits until every copy enqueued this way has landed;
+ * until then host_rgb must stay valid and does not yet hold the image.  A
+ * frame that would overwrite a device image still being copied waits for
+ * that copy (on the device).  The second device image is allocated by the
+ * view's first pipelined frame.
+ */
+vgr_status vgr_render_frame_pipelined(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb,
+                                      vgr_frame* out);
+vgr_status vgr_wait_host_images(vgr_view* v);
+
+/*
  * Asynchronous form of vgr_render_frame, for keeping several views' frames
  * on the GPU at once (a view created with stream 0 owns its own stream).
  * vgr_submit_frame validates the arguments as vgr_render_frame does and

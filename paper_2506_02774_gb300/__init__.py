@@ -193,6 +193,7 @@ class View:
         _abi.check(lib.vgr_create_view(hier.handle, ctypes.byref(o), ctypes.byref(v)))
         self.handle = v
         self.hier = hier
+        self._pipelined_hosts = []  # host arrays of copies not yet waited for
 
     def render(self, cam: dict, tau: float) -> FrameResult:
         fr = _abi.Frame()
@@ -213,6 +214,30 @@ class View:
         """Lowest-overhead form of render_host (pre-built structs); returns the status."""
         return _abi.load().vgr_render_frame_host(self.handle, ctypes.byref(cam_struct), float(tau),
                                                  ctypes.c_void_p(host_ptr), ctypes.byref(fr))
+
+    def render_pipelined(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
+        """Render, with the copy of the image into the float32 H x W x 3 host
+        array ``out`` overlapping the next frame (``vgr_render_frame_pipelined``):
+        ``out`` holds the image once ``wait_host_images`` returns, and is kept
+        alive until then."""
+        _host_image_ok(out, cam, "out")
+        fr = _abi.Frame()
+        c = camera_struct(cam)
+        self._pipelined_hosts.append(out)
+        _abi.check(_abi.load().vgr_render_frame_pipelined(self.handle, ctypes.byref(c), float(tau),
+                                                          ctypes.c_void_p(out.ctypes.data), ctypes.byref(fr)))
+        return FrameResult(fr)
+
+    def render_pipelined_ptr(self, cam_struct: _abi.Camera, tau: float, host_ptr: int, fr: _abi.Frame) -> int:
+        """Lowest-overhead form of render_pipelined (pre-built structs, the
+        caller keeps the host buffer alive); returns the status."""
+        return _abi.load().vgr_render_frame_pipelined(self.handle, ctypes.byref(cam_struct), float(tau),
+                                                      ctypes.c_void_p(host_ptr), ctypes.byref(fr))
+
+    def wait_host_images(self) -> None:
+        """Wait until every pipelined image copy of this view has landed."""
+        _abi.check(_abi.load().vgr_wait_host_images(self.handle))
+        self._pipelined_hosts = []
 
     def submit(self, cam: dict, tau: float, host_out: np.ndarray | None = None):
         """Enqueue a frame without waiting (``vgr_submit_frame``); ``host_out``
@@ -335,6 +360,12 @@ class Renderer:
 
     def render_host(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
         return self.view.render_host(cam, tau, out)
+
+    def render_pipelined(self, cam: dict, tau: float, out: np.ndarray) -> FrameResult:
+        return self.view.render_pipelined(cam, tau, out)
+
+    def wait_host_images(self) -> None:
+        self.view.wait_host_images()
 
     def reset(self):
         self.view.reset()

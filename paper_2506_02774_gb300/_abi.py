@@ -86,6 +86,8 @@ _PROTOS = {
     "vgr_view_device_bytes": (c_i32, [c_vp, ctypes.POINTER(c_u64)]),
     "vgr_render_frame": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, ctypes.POINTER(Frame)]),
     "vgr_render_frame_host": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp, ctypes.POINTER(Frame)]),
+    "vgr_render_frame_pipelined": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp, ctypes.POINTER(Frame)]),
+    "vgr_wait_host_images": (c_i32, [c_vp]),
     "vgr_view_debug": (c_i32, [c_vp, ctypes.POINTER(DebugBuffers)]),
     "vgr_sort_pairs": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_sort_pairs_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),

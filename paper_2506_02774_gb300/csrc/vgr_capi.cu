@@ -123,6 +123,8 @@ struct PendingFrame {
     uint32_t kernels = 0;
     float* host = nullptr;
     float* host_dev = nullptr;  // device address of host when the blend can write it directly
+    bool pipe = false;          // host copy on the copy stream after the status check, not awaited
+    int img = 0;                // device image written (0: image, 1: image_alt)
 };
 
 struct vgr_view {
@@ -151,6 +153,15 @@ struct vgr_view {
     uint2* ranges = nullptr;
     uint32_t* tile_order = nullptr;  // blend order, heaviest tiles first
     float* image = nullptr;
+    // pipelined host images: the second device image, the frame being
+    // written, the copy stream and, per device image, the event its last copy
+    // into host memory recorded
+    float* image_alt = nullptr;
+    float* cur_image = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[2] = {nullptr, nullptr};
+    bool copy_pending[2] = {false, false};
+    int img_sel = 0;  // device image the next pipelined frame writes
     float* lut = nullptr;
     unsigned long long* status = nullptr;
     size_t st_compact = 0, st_front = 0, st_emit = 0, st_depth = 0, st_tile = 0, st_depth_stride = 0,
@@ -594,19 +605,39 @@ vgr_status alloc_status(vgr_view* v) {
 uint32_t tile_of(const vgr_view* v) { return v->opts.tile_size ? v->opts.tile_size : TILE_DEFAULT; }
 uint32_t tiles_for(uint32_t W, uint32_t H, uint32_t T) { return ((W + T - 1) / T) * ((H + T - 1) / T); }
 
+// Wait for every pipelined image copy of the view.
+vgr_status wait_copies(vgr_view* v) {
+    if (!v->copy_stream) return VGR_OK;
+    v->copy_pending[0] = v->copy_pending[1] = false;
+    VGR_CK(cudaStreamSynchronize(v->copy_stream));
+    return VGR_OK;
+}
+
+// The second device image, the copy stream and its events, made on a view's
+// first pipelined frame.
+vgr_status ensure_pipeline(vgr_view* v) {
+    if (!v->copy_stream) VGR_CK(cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking));
+    for (auto& e : v->copy_ev)
+        if (!e) VGR_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!v->image_alt) return dalloc(&v->image_alt, (size_t)v->cap_pixels * 3, &v->img_bytes);
+    return VGR_OK;
+}
+
 vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
     const uint32_t T = tile_of(v);
     const uint32_t TW = (W + T - 1) / T, TH = (H + T - 1) / T;
     const uint64_t px = (uint64_t)W * H, tiles = (uint64_t)TW * TH;
     if (px <= v->cap_pixels && tiles <= v->cap_tiles) return VGR_OK;
+    vgr_status s = wait_copies(v);  // copies into host memory still read the old images
+    if (s != VGR_OK) return s;
     drop_graphs(v);
     dfree(v->image);
+    dfree(v->image_alt);
     dfree(v->ranges);
     dfree(v->tile_order);
     v->img_bytes = 0;
     const uint32_t cp = (uint32_t)std::max<uint64_t>(px, v->cap_pixels);
     const uint32_t ct = (uint32_t)std::max<uint64_t>(tiles, v->cap_tiles);
-    vgr_status s;
     if ((s = dalloc(&v->image, (size_t)cp * 3, &v->img_bytes)) || (s = dalloc(&v->ranges, ct, &v->img_bytes)) ||
         (s = dalloc(&v->tile_order, ct, &v->img_bytes))) {
         v->cap_pixels = v->cap_tiles = 0;
@@ -619,6 +650,13 @@ vgr_status ensure_image(vgr_view* v, uint32_t W, uint32_t H) {
 
 void destroy_view(vgr_view* v) {
     drop_graphs(v);
+    if (v->copy_stream) {
+        cudaStreamSynchronize(v->copy_stream);
+        cudaStreamDestroy(v->copy_stream);
+    }
+    for (auto& e : v->copy_ev)
+        if (e) cudaEventDestroy(e);
+    dfree(v->image_alt);
     free_vis(v);
     free_pairs(v);
     free_cut(v);
@@ -1051,7 +1089,7 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* ho
     p.bl_recB = v->vis.recB;
     p.bl_rgb = v->vis.rgb;
     p.bl_lut = v->lut;
-    p.bl_image = v->image;
+    p.bl_image = v->cur_image;
     p.bl_ctr = v->ctr;
 }
 
@@ -1059,7 +1097,7 @@ void fill_params(vgr_view* v, const vgr_camera* cam, float t, float k, float* ho
 // view's completion event; nothing waits.
 // Validate a frame and set up its parameters (pinned fp_host) without
 // launching anything.
-vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, bool pipe = false) {
     if (!v) return fail(VGR_E_INVALID, "null view");
     if (v->pending) return fail(VGR_E_INVALID, "a frame of this view is already in flight");
     if (v->broken) return fail(VGR_E_NOMEM, "a buffer of this view could not be grown; destroy the view");
@@ -1071,9 +1109,24 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
     if (T == 8 && (W > 8192 || H > 8192))
         return fail(VGR_E_INVALID, "8-pixel tiles need an image of at most 8192 x 8192");
     if ((s = ensure_image(v, W, H)) != VGR_OK) return s;
+    if (pipe && (s = ensure_pipeline(v)) != VGR_OK) return s;
     const uint32_t TW = (W + T - 1) / T, TH = (H + T - 1) / T;
     PendingFrame& q = v->pend;
     q = PendingFrame{};
+    q.pipe = pipe;
+    q.img = pipe ? v->img_sel : 0;
+    if (v->copy_pending[q.img]) {
+        // the image this frame overwrites is still being copied out: a
+        // pipelined frame waits for it on the device, any other frame (which
+        // may run on a batch stream) on the host
+        if (pipe) {
+            VGR_CK(cudaStreamWaitEvent(v->stream, v->copy_ev[q.img], 0));
+        } else {
+            VGR_CK(cudaEventSynchronize(v->copy_ev[q.img]));
+            v->copy_pending[q.img] = false;
+        }
+    }
+    v->cur_image = q.img ? v->image_alt : v->image;
     q.cam = *cam;
     q.tau = tau;
     q.host = host_rgb;
@@ -1085,7 +1138,7 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
     q.t = t;
     q.k = k;
     q.scratch = !v->has_prev || !v->opts.temporal || tau != v->prev_tau || q.f != v->prev_f;
-    q.host_dev = mapped_host(v, host_rgb);
+    q.host_dev = pipe ? nullptr : mapped_host(v, host_rgb);
     fill_params(v, cam, q.t, q.k, q.host_dev, q.tile_passes);
     return VGR_OK;
 }
@@ -1094,8 +1147,8 @@ vgr_status prepare_frame(vgr_view* v, const vgr_camera* cam, float tau, float* h
 // not write the host buffer itself, and the completion event.
 vgr_status close_frame(vgr_view* v, cudaStream_t s) {
     PendingFrame& q = v->pend;
-    if (q.host && !q.host_dev)
-        VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)q.cam.width * q.cam.height * 3 * sizeof(float),
+    if (q.host && !q.host_dev && !q.pipe)
+        VGR_CK(cudaMemcpyAsync(q.host, v->cur_image, (size_t)q.cam.width * q.cam.height * 3 * sizeof(float),
                                cudaMemcpyDeviceToHost, s));
     VGR_CK(cudaEventRecord(v->done_ev, s));
     v->pending = true;
@@ -1108,9 +1161,9 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
-vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
+vgr_status submit_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, bool pipe = false) {
     NvtxRange r("vgr submit frame");
-    vgr_status s = prepare_frame(v, cam, tau, host_rgb);
+    vgr_status s = prepare_frame(v, cam, tau, host_rgb, pipe);
     if (s != VGR_OK) return s;
     PendingFrame& q = v->pend;
     if ((s = run_frame(v, q.scratch, q.tile_passes, tiles_for(q.cam.width, q.cam.height, tile_of(v)), &q.kernels)) !=
@@ -1325,10 +1378,20 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
         ++replays;
         fill_params(v, &q.cam, q.t, q.k, q.host_dev, q.tile_passes);
         if ((s = run_frame(v, q.scratch, q.tile_passes, TW * TH, &q.kernels)) != VGR_OK) return s;
-        if (q.host && !q.host_dev)
-            VGR_CK(cudaMemcpyAsync(q.host, v->image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+        if (q.host && !q.host_dev && !q.pipe)
+            VGR_CK(cudaMemcpyAsync(q.host, v->cur_image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
                                    v->stream));
         VGR_CK(cudaStreamSynchronize(v->stream));
+    }
+    if (q.pipe) {
+        // the frame has finished (done_ev, or the replay's synchronize): its
+        // image goes out on the copy stream while the next frame runs
+        VGR_CK(cudaStreamWaitEvent(v->copy_stream, v->done_ev, 0));
+        VGR_CK(cudaMemcpyAsync(q.host, v->cur_image, (size_t)W * H * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                               v->copy_stream));
+        VGR_CK(cudaEventRecord(v->copy_ev[q.img], v->copy_stream));
+        v->copy_pending[q.img] = true;
+        v->img_sel ^= 1;
     }
     const int cur = v->parity ^ 1;
     v->parity = cur;
@@ -1342,7 +1405,7 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
     v->last_n_pairs = ch->n_pairs;
     if (out) {
         memset(out, 0, sizeof(*out));
-        out->image = v->image;
+        out->image = v->cur_image;
         out->cut = v->cut[cur];
         out->cut_count = v->last_n_cut;
         out->width = W;
@@ -1367,8 +1430,9 @@ vgr_status finish_impl(vgr_view* v, vgr_frame* out) {
     return VGR_OK;
 }
 
-vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
-    vgr_status s = submit_impl(v, cam, tau, host_rgb);
+vgr_status render_impl(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out,
+                       bool pipe = false) {
+    vgr_status s = submit_impl(v, cam, tau, host_rgb, pipe);
     if (s != VGR_OK) return s;
     return finish_impl(v, out);
 }
@@ -1384,6 +1448,18 @@ vgr_status vgr_render_frame(vgr_view* v, const vgr_camera* cam, float tau, vgr_f
 vgr_status vgr_render_frame_host(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb, vgr_frame* out) {
     if (!host_rgb) return fail(VGR_E_INVALID, "null host image");
     return render_impl(v, cam, tau, host_rgb, out);
+}
+
+vgr_status vgr_render_frame_pipelined(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb,
+                                      vgr_frame* out) {
+    if (!host_rgb) return fail(VGR_E_INVALID, "null host image");
+    return render_impl(v, cam, tau, host_rgb, out, true);
+}
+
+vgr_status vgr_wait_host_images(vgr_view* v) {
+    if (!v) return fail(VGR_E_INVALID, "null view");
+    VGR_CK(cudaSetDevice(v->h->device));
+    return wait_copies(v);
 }
 
 vgr_status vgr_submit_frame(vgr_view* v, const vgr_camera* cam, float tau, float* host_rgb) {
