@@ -325,6 +325,18 @@ vgr_status vgr_finish_frame(vgr_view* v, vgr_frame* out);
 vgr_status vgr_render_batch(vgr_view* const* views, const vgr_camera* cams, const float* taus,
                             float* const* host_rgb, uint32_t n, vgr_frame* outs);
 
+/*
+ * How many views of a captured batch run at once (process-wide; a tuning
+ * knob, results do not depend on it): with chains = c > 0 the views form c
+ * parallel chains, assigned largest image first each to the chain with the
+ * fewest pixels so far, a view starting when the previous view of its chain
+ * has finished up to its tile order; 0 (the default) runs every view as its
+ * own branch.  Large views' frames keep their sort and pair buffers in L2
+ * only while few of them run at once; small views gain from running many at
+ * once.  The batch's single blend launch follows every chain.
+ */
+vgr_status vgr_set_batch_chains(uint32_t chains);
+
 vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* out);
 
 /*

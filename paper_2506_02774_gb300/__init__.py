@@ -382,6 +382,13 @@ class Renderer:
         return False
 
 
+def set_batch_chains(chains: int) -> None:
+    """How many views of a captured batch run at once (``vgr_set_batch_chains``):
+    ``chains`` parallel chains, largest image first to the least-loaded chain;
+    0 runs every view as its own branch.  Results do not depend on it."""
+    _abi.check(_abi.load().vgr_set_batch_chains(int(chains)))
+
+
 def view_bytes_estimate(hier: Hierarchy, width: int, height: int, **view_kw) -> int:
     """Device bytes a view with these options holds after its first frame at
     width x height (``vgr_view_bytes_estimate``)."""

@@ -89,6 +89,7 @@ _PROTOS = {
     "vgr_render_frame_pipelined": (c_i32, [c_vp, ctypes.POINTER(Camera), c_f32, c_vp, ctypes.POINTER(Frame)]),
     "vgr_wait_host_images": (c_i32, [c_vp]),
     "vgr_view_debug": (c_i32, [c_vp, ctypes.POINTER(DebugBuffers)]),
+    "vgr_set_batch_chains": (c_i32, [c_u32]),
     "vgr_sort_pairs": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_sort_pairs_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_u64, c_u32, c_vp]),
     "vgr_last_error": (ctypes.c_char_p, []),

@@ -9,8 +9,8 @@ graph, timed with CUDA events on the view's stream after warm-up frames),
 keeps the fastest, then tries every (tile, depth) at that geometry.  None of
 the knobs changes the cut or the image (binning is exact at any tile size),
 only how the work is cut up and spread over the SMs, so any cached choice is
-safe to reuse.  ``tune_batch`` picks the (tile, depth) of a batch's single
-blend launch on the batch itself.
+safe to reuse.  ``tune_batch`` picks, on the batch itself, how many of a
+batch's views run at once and the (tile, depth) of its single blend launch.
 """
 from __future__ import annotations
 
@@ -22,6 +22,7 @@ from . import View
 GRID_WIDE_PER_SM = (2, 4, 8, 16)   # grid-stride kernels: LoD, preprocess (with colour), ranges
 GRID_SCAN_PER_SM = (2, 3, 4, 6)    # ticketed look-back kernels: compaction, radix passes, emission
 BLEND_DEPTHS = (16, 32, 48)        # Gaussians a blend warp stages per chunk
+BATCH_CHAINS = (0, 1, 2, 3, 4, 8)  # views of a batch running at once (0: all)
 TILE_SIZES = (8, 16, 32)           # tile side in pixels
 
 
@@ -115,20 +116,24 @@ def tune(hier, cams, tau: float, *, cache_path: str | None = None, warmup: int =
     return entry
 
 
-def tune_batch(views, steps, taus, *, depths=BLEND_DEPTHS, tiles=TILE_SIZES, warmup: int = 2) -> dict:
-    """The tile size and staging depth of a batch (``vgr_render_batch`` runs
-    the blend of every view it can in one launch, at one tile size and
-    depth): every candidate is set on all views and timed on the batch walk
-    ``steps`` (a list of per-step camera lists; the first ``warmup`` steps
-    untimed), wall clock per batch.  The fastest is left set on the views.
-    Returns {"tile_size", "blend_depth", "ms_per_batch", "candidates"}."""
+def tune_batch(views, steps, taus, *, depths=BLEND_DEPTHS, tiles=TILE_SIZES, chains=BATCH_CHAINS,
+               warmup: int = 2) -> dict:
+    """The concurrency, tile size and staging depth of a batch
+    (``vgr_render_batch`` runs the views' frames in parallel chains, then the
+    blend of every view it can in one launch, at one tile size and depth):
+    every number of chains is timed at 16-pixel tiles and depth 32, then every
+    (tile, depth) at the best number, each set on all views and timed on the
+    batch walk ``steps`` (a list of per-step camera lists; the first
+    ``warmup`` steps untimed), wall clock per batch.  The fastest is left set.
+    Returns {"chains", "tile_size", "blend_depth", "ms_per_batch", "candidates"}."""
     import time
 
     import torch
 
-    from . import render_batch
-    results = []
-    for t, d in _pairs(tiles, depths):
+    from . import render_batch, set_batch_chains
+
+    def run(c, t, d):
+        set_batch_chains(c)
         for v in views:
             v.set_tuning(blend_depth=d, tile_size=t)
             v.reset()
@@ -139,11 +144,26 @@ def tune_batch(views, steps, taus, *, depths=BLEND_DEPTHS, tiles=TILE_SIZES, war
         for cams in steps[warmup:]:
             render_batch(views, cams, taus)
         torch.cuda.synchronize()
-        results.append(((time.perf_counter() - t0) * 1e3 / max(1, len(steps) - warmup), t, d))
+        return (time.perf_counter() - t0) * 1e3 / max(1, len(steps) - warmup), c, t, d
+
+    n = len(views)
+    seen, results = set(), []
+    for c in chains:
+        eff = n if c == 0 else min(n, c)  # chains beyond the view count run like 0
+        if eff not in seen:
+            seen.add(eff)
+            results.append(run(c, 16, 32))
     results.sort()
-    best_ms, t, d = results[0]
+    c = results[0][1]
+    for t, d in _pairs(tiles, depths):
+        if (t, d) != (16, 32):
+            results.append(run(c, t, d))
+    results.sort()
+    best_ms, c, t, d = results[0]
+    set_batch_chains(c)
     for v in views:
         v.set_tuning(blend_depth=d, tile_size=t)
         v.reset()
-    return dict(tile_size=t, blend_depth=d, ms_per_batch=round(best_ms, 3),
-                candidates=[dict(tile_size=z, blend_depth=q, ms_per_batch=round(ms_, 3)) for ms_, z, q in results])
+    return dict(chains=c, tile_size=t, blend_depth=d, ms_per_batch=round(best_ms, 3),
+                candidates=[dict(chains=x, tile_size=z, blend_depth=q, ms_per_batch=round(ms_, 3))
+                            for ms_, x, z, q in results])

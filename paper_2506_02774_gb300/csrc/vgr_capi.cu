@@ -492,6 +492,7 @@ std::mutex g_batch_mu;
 std::vector<BatchGraph> g_batches;
 uint64_t g_batch_clock = 0;
 constexpr size_t BATCH_GRAPHS_KEPT = 8;
+std::atomic<uint32_t> g_batch_chains{0};  // parallel chains of a captured batch (0: one per view)
 
 void forget_batches(uint64_t uid) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -1212,8 +1213,27 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
         VGR_CK(cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking));
         VGR_CK(cudaEventCreateWithFlags(&bs.fork, cudaEventDisableTiming));
     }
+    // the views' chains: largest image first, each to the chain with the
+    // fewest pixels so far; a view follows the previous view of its chain
+    const uint32_t k = g_batch_chains.load() == 0 ? n : std::min(n, g_batch_chains.load());
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; ++i) order[i] = i;
+    auto pixels = [&](uint32_t i) { return (uint64_t)views[i]->pend.cam.width * views[i]->pend.cam.height; };
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return pixels(a) > pixels(b); });
+    std::vector<uint64_t> load(k, 0);
+    std::vector<int> chain_last(k, -1), prev(n, -1);
+    std::vector<char> tail(n, 0);
+    for (uint32_t i : order) {
+        const uint32_t c = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+        prev[i] = chain_last[c];
+        chain_last[c] = (int)i;
+        load[c] += pixels(i);
+    }
+    for (int i : chain_last)
+        if (i >= 0) tail[i] = 1;
     std::vector<uint64_t> key;
-    key.reserve((size_t)n * 6);
+    key.reserve((size_t)n * 6 + 1);
+    key.push_back(k);
     for (uint32_t i = 0; i < n; ++i) {
         const vgr_view* v = views[i];
         const PendingFrame& q = v->pend;
@@ -1264,13 +1284,14 @@ vgr_status launch_batch_graph(vgr_view* const* views, uint32_t n) {
         }
         VGR_CK(cudaStreamBeginCapture(bs.s, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaEventRecord(bs.fork, bs.s);
-        for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        for (uint32_t i : order) {  // a view's predecessor in its chain is captured before it
+            if (e != cudaSuccess) break;
             vgr_view* v = views[i];
-            e = cudaStreamWaitEvent(v->stream, bs.fork, 0);
+            e = cudaStreamWaitEvent(v->stream, prev[i] < 0 ? bs.fork : views[prev[i]]->join_ev, 0);
             if (e != cudaSuccess) break;
             enqueue_frame(v, v->pend.scratch, v->pend.tile_passes, !shared[i]);
             e = cudaEventRecord(v->join_ev, v->stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
+            if (e == cudaSuccess && tail[i]) e = cudaStreamWaitEvent(bs.s, v->join_ev, 0);
         }
         if (e == cudaSuccess && ns) {
             PdlScope pdl(true);  // the first kernel follows the joins in plain stream order
@@ -1536,6 +1557,11 @@ vgr_status vgr_render_batch(vgr_view* const* views, const vgr_camera* cams, cons
     }
     if (first != VGR_OK) g_err = first_msg;
     return first;
+}
+
+vgr_status vgr_set_batch_chains(uint32_t chains) {
+    g_batch_chains.store(chains);
+    return VGR_OK;
 }
 
 vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {

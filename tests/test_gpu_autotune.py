@@ -79,8 +79,9 @@ def test_tune_batch(small_sh3_scene):
     steps = [[scenegen.camera((2.0 + 0.05 * k + i, 15.0, 3.0), 0.2, W, H, 160.0) for i, (W, H) in enumerate(sizes)]
              for k in range(4)]
     r = autotune.tune_batch(views, steps, [3.0] * 3)
-    assert r["blend_depth"] in (16, 32, 48) and r["tile_size"] in (8, 16, 32) and len(r["candidates"]) == 8
-    assert r["ms_per_batch"] == min(c["ms_per_batch"] for c in r["candidates"])
+    assert r["blend_depth"] in (16, 32, 48) and r["tile_size"] in (8, 16, 32)
+    assert len(r["candidates"]) == 3 + 7  # chains 0 (= 3), 1, 2; then the other (tile, depth) pairs
+    assert r["chains"] in (0, 1, 2) and r["ms_per_batch"] == min(c["ms_per_batch"] for c in r["candidates"])
     res = vgr.render_batch(views, steps[-1], [3.0] * 3)
     for i, v in enumerate(views):
         alone = vgr.View(h)

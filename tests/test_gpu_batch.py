@@ -202,11 +202,21 @@ def test_server_without_release_waits_for_memory(h_small):
     sv.close()
 
 
-def test_whole_batch_graph_equals_individual(small_sh3_scene, h_small):
+@pytest.mark.parametrize("chains", [0, 1, 2, 3])
+def test_whole_batch_graph_equals_individual(small_sh3_scene, h_small, chains):
     """Every view replays captured frames on its own stream: the batch runs
     as one captured graph (re-captured when a view's buffers grow, reused
     when the combination repeats) and each frame equals the view rendered
-    alone, over several frames and both buffer parities."""
+    alone, over several frames and both buffer parities, with the views in
+    one branch each (chains 0) or in 1, 2 or 3 chains."""
+    vgr.set_batch_chains(chains)
+    try:
+        _whole_batch_equals_individual(h_small)
+    finally:
+        vgr.set_batch_chains(0)
+
+
+def _whole_batch_equals_individual(h_small):
     n = len(SIZES)
     batch = [vgr.View(h_small, use_graph=True, pair_capacity=(16 if i == 1 else 0)) for i in range(n)]
     solo = [vgr.View(h_small) for _ in range(n)]
