@@ -17,7 +17,10 @@
 //    (a child expands only if its parent does), which the nested radii
 //    guarantee; a violation raises F_NONMONOTONE.  A thread that would
 //    explore more than the budget sets F_LOD_FALLBACK and the host redoes
-//    the frame top-down.
+//    the frame top-down.  The parent's (mean, radius^2) is stored a second
+//    time beside each node's (one 16-byte entry per node, built at load),
+//    so a thread reads both in one round instead of waiting for the parent's
+//    id first; the id itself is read only when the node collapses.
 //  * k_lod_level: one level of the from-scratch, top-down traversal (frame 0,
 //    tau change, reset, fallback); frontiers are appended with one atomic per
 //    warp after a warp scan of the child counts.
@@ -186,16 +189,20 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
     uint32_t evals = 0, flags = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     // one previous-cut node: stay, collapse or expand
-    // (a staying node is only reported: its bits are set warp-aggregated below)
+    // (a staying node is only reported: its bits are set warp-aggregated below).
+    // cp is the parent's entry (w = +inf at the root); the parent's id p is
+    // loaded with it by the frustum and interpolation variants (which test its
+    // box or read its extent), else only when n collapses
+    constexpr bool WITH_P = FR || IP;
     auto visit = [&](uint32_t n, float4 cn, uint32_t p, float4 cp) -> bool {
         const bool en = expand(n, cn);
         bool ep = true;
         ++evals;
-        if (p != NONE) { ep = expand(p, cp); ++evals; }
+        if (cp.w != INFINITY) { ep = expand(p, cp); ++evals; }
         if (!ep) {
             if (en) flags |= F_NONMONOTONE;
             // collapse: climb while the parent of a does not expand
-            uint32_t a = p;
+            uint32_t a = WITH_P ? p : sc.parent[n];
             float4 ca = cp;
             for (uint32_t steps = 0;; ++steps) {
                 const uint32_t pa = sc.parent[a];
@@ -263,11 +270,10 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {
             cc[u] = sc.cr[nn[u]];
-            pp[u] = sc.parent[nn[u]];
+            qq[u] = sc.pcr[nn[u]];  // the parent's entry, in the same round
             ll[u] = sc.lmax[nn[u]];
+            pp[u] = WITH_P ? sc.parent[nn[u]] : NONE;
         }
-#pragma unroll
-        for (int u = 0; u < LOD_UNROLL; ++u) qq[u] = pp[u] != NONE ? sc.cr[pp[u]] : cc[u];
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {
             const bool stay = ok[u] && visit(nn[u], cc[u], pp[u], qq[u]);
