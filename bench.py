@@ -716,18 +716,18 @@ def _serve_once(h, n_clients, inflight, pick, trace):
 
 
 def run_served(sc, h, n_clients: int, rate: float, seconds: float, sweep, sweep_seconds: float,
-               p99_bound_ms: float, seed: int = 5) -> dict:
+               p99_bound_ms: float, seed: int = 5, modes=(("continuous", 2), ("one_at_a_time", 1))) -> dict:
     """Serving: n_clients clients with Poisson arrivals (rate req/s each) for
     `seconds`, image sizes uniform over 720p/1080p/1440p, each client on its
     own street walk (one frame step per request), images copied to pinned
-    host memory.  Latency = completion - arrival.  Continuous batching (every
-    client's frame may be in flight) against one frame at a time; then a
+    host memory.  Latency = completion - arrival.  Continuous batching (up
+    to two clients' frames in flight, the server's default) against one
+    frame at a time; then a
     sweep of the offered load, reporting for each mode the highest
     throughput whose p99 stays within p99_bound_ms."""
     rng = np.random.default_rng(seed)
     names = ["720p", "1080p", "1440p"]
     pick = [names[i] for i in rng.integers(0, 3, n_clients)]
-    modes = (("continuous", 0), ("one_at_a_time", 1))
     trace = _serve_trace(n_clients, rate, seconds, seed, pick, 2)
     out = {m: _serve_once(h, n_clients, inf, pick, trace) for m, inf in modes}
     pts = {m: [] for m, _ in modes}
@@ -740,7 +740,8 @@ def run_served(sc, h, n_clients: int, rate: float, seconds: float, sweep, sweep_
     best = {m: max([p["frames_per_s"] for p in pts[m] if p["p99_ms"] <= p99_bound_ms] or [0.0]) for m, _ in modes}
     saturated = {m: pts[m][-1]["frames_per_s"] if pts[m] else None for m, _ in modes}
     return dict(clients=n_clients, rate_per_client=rate, seconds=seconds, requests=len(trace),
-                sizes={n: pick.count(n) for n in names}, host_images=True, **out,
+                sizes={n: pick.count(n) for n in names}, host_images=True,
+                max_inflight={m: inf for m, inf in modes}, **out,
                 sweep=dict(seconds=sweep_seconds, p99_bound_ms=p99_bound_ms, points=pts,
                            max_frames_per_s_within_bound=best, frames_per_s_at_highest_load=saturated))
 

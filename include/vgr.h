@@ -367,7 +367,9 @@ typedef struct vgr_server vgr_server;
 
 typedef struct {
     uint32_t n_clients;      /* clients 0 .. n_clients-1 (1..65536) */
-    uint32_t max_inflight;   /* frames in flight at once; 1 = one frame at a time; 0 = n_clients */
+    uint32_t max_inflight;   /* frames in flight at once (default 2); 1 = one frame at a time;
+                                0 = n_clients.  A large frame's sort and pair buffers stay in
+                                L2 only while few such frames run at once. */
     uint32_t host_images;    /* 1: every image is copied to the client's pinned host buffer */
     uint64_t hbm_reserve;    /* free device bytes admission keeps (default 1 GiB) */
     vgr_view_opts view;      /* options of every client's view; stream and timing are ignored

@@ -405,12 +405,15 @@ def view_bytes_estimate(hier: Hierarchy, width: int, height: int, **view_kw) -> 
 class Server:
     """Continuous-batching frame server over one hierarchy (``vgr_create_server``)."""
 
-    def __init__(self, hier: Hierarchy, n_clients: int, *, max_inflight: int = 0, host_images: bool = False,
-                 hbm_reserve: int | None = None, use_graph: bool = True, evict_idle: bool = True, **view_kw):
+    def __init__(self, hier: Hierarchy, n_clients: int, *, max_inflight: int | None = None,
+                 host_images: bool = False, hbm_reserve: int | None = None, use_graph: bool = True,
+                 evict_idle: bool = True, **view_kw):
         lib = _abi.load()
         o = _abi.ServeOpts()
         lib.vgr_default_serve_opts(ctypes.byref(o))
-        o.n_clients, o.max_inflight, o.host_images = int(n_clients), int(max_inflight), int(host_images)
+        o.n_clients, o.host_images = int(n_clients), int(host_images)
+        if max_inflight is not None:  # else the library's default (2)
+            o.max_inflight = int(max_inflight)
         o.evict_idle = int(bool(evict_idle))
         if hbm_reserve is not None:
             o.hbm_reserve = int(hbm_reserve)

@@ -118,7 +118,7 @@ void vgr_default_serve_opts(vgr_serve_opts* o) {
     if (!o) return;
     *o = vgr_serve_opts{};
     o->n_clients = 1;
-    o->max_inflight = 0;
+    o->max_inflight = 2;  // more large frames at once push each other's sort buffers out of L2
     o->host_images = 0;
     o->hbm_reserve = 1ull << 30;
     vgr_default_view_opts(&o->view);

@@ -121,12 +121,23 @@ def _overlapping_clients(res):
             and res["start_s"][j] < res["finish_s"][i]]
 
 
-@pytest.mark.parametrize("max_inflight", [0, 1])
+def _max_concurrent(res) -> int:
+    """Most frames in flight at one instant ([start, finish) intervals)."""
+    ev = sorted([(s, 1) for s in res["start_s"]] + [(f, -1) for f in res["finish_s"]], key=lambda e: (e[0], e[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+@pytest.mark.parametrize("max_inflight", [0, 1, 2, None])
 def test_server_trace_equals_solo(h_small, max_inflight):
-    """Continuous batching (max_inflight 0) keeps frames of different clients
-    in flight together; one frame at a time (1) never does.  Either way every
-    served frame -- not only each client's last -- equals the same client's
-    walk rendered alone, bit for bit, through per-request host images."""
+    """Continuous batching (max_inflight 0: every client; 2, also the
+    default) keeps frames of different clients in flight together, never more
+    than the cap; one frame at a time (1) never does.  Either way every served
+    frame -- not only each client's last -- equals the same client's walk
+    rendered alone, bit for bit, through per-request host images."""
     C, K = 4, 6
     reqs = _trace(C, K, 200.0, 5)
     sv = vgr.Server(h_small, C, max_inflight=max_inflight, host_images=True)
@@ -144,9 +155,11 @@ def test_server_trace_equals_solo(h_small, max_inflight):
         assert not overlap
         order = np.argsort(res["start_s"])
         assert (res["start_s"][order][1:] >= res["finish_s"][order][:-1]).all()
-    else:
+    elif max_inflight == 0:
         # the t = 0 burst: all four first frames are submitted before any completes
         assert len(overlap) >= C - 1, overlap
+    else:
+        assert overlap and _max_concurrent(res) <= 2, (overlap, _max_concurrent(res))
     solo = _solo_walks(h_small, C, K)
     for i, r in enumerate(reqs):
         simg, scounts = solo[r["client"]]
