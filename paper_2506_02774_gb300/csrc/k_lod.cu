@@ -17,10 +17,10 @@
 //    (a child expands only if its parent does), which the nested radii
 //    guarantee; a violation raises F_NONMONOTONE.  A thread that would
 //    explore more than the budget sets F_LOD_FALLBACK and the host redoes
-//    the frame top-down.  The parent's (mean, radius^2) is stored a second
-//    time beside each node's (one 16-byte entry per node, built at load),
-//    so a thread reads both in one round instead of waiting for the parent's
-//    id first; the id itself is read only when the node collapses.
+//    the frame top-down.  The node's (mean, radius^2) and its parent's are
+//    stored together in one 32-byte record per node (built at load), so a
+//    cut node costs one sector and one round instead of waiting for the
+//    parent's id first; the id itself is read only when the node collapses.
 //  * k_lod_level: one level of the from-scratch, top-down traversal (frame 0,
 //    tau change, reset, fallback); frontiers are appended with one atomic per
 //    warp after a warp scan of the child counts.
@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(256) k_lod_update(const uint32_t* __restrict__
         }
 #pragma unroll
         for (int u = 0; u < LOD_UNROLL; ++u) {
-            cc[u] = sc.cr[nn[u]];
-            qq[u] = sc.pcr[nn[u]];  // the parent's entry, in the same round
+            cc[u] = sc.lodr[2 * (size_t)nn[u]];
+            qq[u] = sc.lodr[2 * (size_t)nn[u] + 1];  // the parent's entry, same sector
             ll[u] = sc.lmax[nn[u]];
             pp[u] = WITH_P ? sc.parent[nn[u]] : NONE;
         }

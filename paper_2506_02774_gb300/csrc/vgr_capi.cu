@@ -101,7 +101,7 @@ vgr::PdlState& vgr::pdl_state() {
 struct vgr_hierarchy {
     SceneDev dev{};
     float4* cr = nullptr;
-    float4* pcr = nullptr;  // the parent's cr entry per node (root: w = +inf)
+    float4* lodr = nullptr;  // per node its cr entry and its parent's (root: w = +inf), 32 bytes
     uint32_t* parent = nullptr;
     uint32_t* child = nullptr;
     float4* covA = nullptr;
@@ -309,7 +309,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     const bool half = d->storage == VGR_STORE_HALF;
     const uint32_t stride = half ? (K3 + 7u) / 8u * 8u : (K3 + 3u) / 4u * 4u;
     vgr_status st = VGR_OK;
-    auto cleanup = [&]() { dfree(h->cr); dfree(h->pcr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
+    auto cleanup = [&]() { dfree(h->cr); dfree(h->lodr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB); dfree(h->lmax);
                            dfree(h->box); if (h->sh) cudaFree(h->sh); delete h; };
 #define VGR_TRY(x)                 \
     do {                           \
@@ -320,7 +320,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
         }                          \
     } while (0)
     VGR_TRY(dalloc(&h->cr, N, &h->bytes));
-    VGR_TRY(dalloc(&h->pcr, N, &h->bytes));
+    VGR_TRY(dalloc(&h->lodr, 2 * (size_t)N, &h->bytes));
     VGR_TRY(dalloc(&h->parent, N, &h->bytes));
     VGR_TRY(dalloc(&h->child, N, &h->bytes));
     VGR_TRY(dalloc(&h->covA, N, &h->bytes));
@@ -363,18 +363,21 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
             f4[i] = make_float4(m[0], m[1], m[2], d->n_child[n] ? d->radius2[n] : -d->radius2[n]);
         }
         ce = cudaMemcpy(h->cr + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
-        // the parent's entry beside each node's, so the temporal update reads
-        // both in one round; the root's has w = +inf (radius2 is finite)
-        for (uint32_t i = 0; i < cnt; ++i) {
+        // the temporal update's record: the node's entry and its parent's in
+        // one 32-byte sector, so a cut node costs one sector and one round;
+        // the root's parent entry has w = +inf (radius2 is finite)
+        for (uint32_t i = cnt; i-- > 0;) {  // in place, from the end: entry i moves to 2i
             const uint32_t n = b + i, p = d->parent[n];
+            f4[2 * i] = f4[i];
             if (p == NONE) {
-                f4[i] = make_float4(0.f, 0.f, 0.f, INFINITY);
+                f4[2 * i + 1] = make_float4(0.f, 0.f, 0.f, INFINITY);
             } else {
                 const float* m = d->mean + 3 * (size_t)p;
-                f4[i] = make_float4(m[0], m[1], m[2], d->radius2[p]);  // a parent is internal: w = radius2
+                f4[2 * i + 1] = make_float4(m[0], m[1], m[2], d->radius2[p]);  // a parent is internal
             }
         }
-        if (ce == cudaSuccess) ce = cudaMemcpy(h->pcr + b, f4, cnt * sizeof(float4), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(h->lodr + 2 * (size_t)b, f4, 2 * (size_t)cnt * sizeof(float4), cudaMemcpyHostToDevice);
         uint32_t* u = (uint32_t*)pin;
         for (uint32_t i = 0; i < cnt; ++i) {
             const uint32_t n = b + i;
@@ -449,7 +452,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
     if (ce != cudaSuccess) { cleanup(); return fail(VGR_E_CUDA, "prepare: %s", cudaGetErrorString(ce)); }
 #undef VGR_TRY
     h->dev.cr = h->cr;
-    h->dev.pcr = h->pcr;
+    h->dev.lodr = h->lodr;
     h->dev.parent = h->parent;
     h->dev.child = h->child;
     h->dev.covA = h->covA;
@@ -468,7 +471,7 @@ vgr_status vgr_load_hierarchy(const vgr_scene_desc* d, vgr_hierarchy** out) {
 vgr_status vgr_free_hierarchy(vgr_hierarchy* h) {
     if (!h) return fail(VGR_E_INVALID, "null hierarchy");
     cudaSetDevice(h->device);
-    dfree(h->cr); dfree(h->pcr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
+    dfree(h->cr); dfree(h->lodr); dfree(h->parent); dfree(h->child); dfree(h->covA); dfree(h->covB);
     dfree(h->lmax); dfree(h->box);
     if (h->sh) cudaFree(h->sh);
     delete h;

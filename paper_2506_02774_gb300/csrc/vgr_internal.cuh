@@ -107,7 +107,7 @@ struct ViewState {
 // Device view of the hierarchy.
 struct SceneDev {
     const float4* cr;          // mean xyz, w = radius2 (internal) or -radius2 (leaf: never expands)
-    const float4* pcr;         // cr of the node's parent (the root: w = +inf)
+    const float4* lodr;        // per node 2 float4: its cr entry, its parent's (the root's: w = +inf)
     const uint32_t* parent;
     const uint32_t* child;     // first_child | n_child << 28
     const float4* covA;        // xx xy xz yy
