@@ -173,7 +173,7 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
     P0 = st.get("candidate_pairs", P)
     F = st.get("front_count", V)
     return dict(
-        lod=16 * E + 4 * C + 4 * C + 2 * N / 8,      # node tests, parent ids, prev cut read, two bitmaps set
+        lod=16 * E + 4 * C + 4 * C + 2 * N / 8,      # node and parent tests, lmax, prev cut read, two bitmaps set
         compact=2 * (N / 8 * 2) + 4 * C + 4 * F,     # two bitmaps read + cleared, cut and in-front ids written
         # ids, centre, covariance + opacity, records out; SH in and rgb out (visible)
         preprocess=(4 + 16 + 32 + 52) * F + (shb + 16) * V,
