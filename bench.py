@@ -176,7 +176,7 @@ def _frame_bytes(sc: dict, st: dict, W: int, H: int, tile_passes: int) -> dict:
         lod=16 * E + 4 * C + 4 * C + 2 * N / 8,      # node and parent tests, lmax, prev cut read, two bitmaps set
         compact=2 * (N / 8 * 2) + 4 * C + 4 * F,     # two bitmaps read + cleared, cut and in-front ids written
         # ids, centre, covariance + opacity, records out; SH in and rgb out (visible)
-        preprocess=(4 + 16 + 32 + 52) * F + (shb + 16) * V,
+        preprocess=(4 + 16 + 32 + 48) * F + (shb + 16) * V,
         depth_sort=4 * 2 * 8 * F + 4 * F,            # 4 passes x (key+value) read+write, histogram read
         color=0,                                     # evaluated in preprocess
         emit=(4 + 4 + 8 + 32) * V + 8 * P0,          # order, count, rect, record halves; slots

@@ -286,7 +286,6 @@ __global__ void __launch_bounds__(PRE_THREADS, 2) k_preprocess(SceneDev sc, cons
             for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(zbits >> (8 * p)) & 255u], 1u);
         }
         if (i < n_front) {
-            vis.node[i] = node;
             vis.depth[i] = zbits;  // culled: all ones, sorted behind every visible key
             vis.ntile[i] = v ? (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1) : 0u;
             vis.rect[i] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));

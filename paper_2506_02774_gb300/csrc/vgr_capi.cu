@@ -536,7 +536,7 @@ void drop_graphs(vgr_view* v) {
 
 void free_vis(vgr_view* v) {
     drop_graphs(v);
-    dfree(v->vis.node); dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
+    dfree(v->vis.depth); dfree(v->vis.ntile); dfree(v->vis.rect);
     dfree(v->vis.recA); dfree(v->vis.recB); dfree(v->vis.rgb); dfree(v->vis.lw);
     for (int i = 0; i < 2; ++i) { dfree(v->sortK[i]); dfree(v->sortV[i]); }
     dfree(v->slot_off);
@@ -547,7 +547,7 @@ vgr_status alloc_vis(vgr_view* v, uint32_t cap) {
     free_vis(v);
     uint64_t b = 0;
     vgr_status s;
-    if ((s = dalloc(&v->vis.node, cap, &b)) || (s = dalloc(&v->vis.depth, cap, &b)) ||
+    if ((s = dalloc(&v->vis.depth, cap, &b)) ||
         (s = dalloc(&v->vis.ntile, cap, &b)) || (s = dalloc(&v->vis.rect, cap, &b)) ||
         (s = dalloc(&v->vis.recA, cap, &b)) || (s = dalloc(&v->vis.recB, cap, &b)) ||
         (s = dalloc(&v->vis.rgb, cap, &b)) || (s = dalloc(&v->vis.lw, cap, &b)) ||
@@ -1594,7 +1594,7 @@ vgr_status vgr_view_debug(vgr_view* v, vgr_debug_buffers* o) {
     o->tiles_x = v->last_tw;
     o->tiles_y = v->last_th;
     o->cut = v->cut[v->parity];
-    o->vis_node = v->vis.node;
+    o->vis_node = v->front_list;  // entry i's node id
     o->vis_depth = v->vis.depth;
     o->vis_ntile = v->vis.ntile;
     o->vis_rect = reinterpret_cast<const uint32_t*>(v->vis.rect);

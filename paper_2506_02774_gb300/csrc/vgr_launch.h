@@ -73,8 +73,8 @@ uint32_t cut_compact_tiles(uint32_t n_words);
 uint32_t cut_compact_tile_words();
 
 // k_preprocess.cu
+// Per in-front entry i (the entry's node id is the in-front list's entry i)
 struct VisBuffers {
-    uint32_t* node;
     uint32_t* depth;
     uint32_t* ntile;
     uint2* rect;
