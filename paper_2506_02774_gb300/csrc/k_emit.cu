@@ -251,17 +251,26 @@ void launch_emit(const uint32_t* order, uint32_t cap_vis, VisBuffers vis, uint32
 // tile-sort pass recorded as (start, ~end) by atomic minima from all ones:
 // each becomes [start, end), or [0, 0) for a tile without pairs.  The class
 // counts go to the frame's counters, for a batch's order over all its views.
+// The few classes are counted and claimed once per run of equal classes in a
+// warp (match instruction), not once per tile.
 __global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges, uint32_t n_tiles,
                                                      uint32_t* __restrict__ order, Counters* __restrict__ ctr) {
     pdl_wait();
     __shared__ uint32_t s_cnt[33], s_start[33];
+    const uint32_t lane = lane_id();
     if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        uint2 r = ranges[t];
-        r = r.x == 0xFFFFFFFFu ? make_uint2(0u, 0u) : make_uint2(r.x, ~r.y);
-        ranges[t] = r;  // read back below by this same thread
-        atomicAdd(&s_cnt[32 - __clz(r.y - r.x + 1u)], 1u);
+    for (uint32_t t0 = threadIdx.x & ~31u; t0 < n_tiles; t0 += blockDim.x) {  // warp-uniform trips
+        const uint32_t t = t0 + lane;
+        uint32_t cls = 64u;  // past the end: no class
+        if (t < n_tiles) {
+            uint2 r = ranges[t];
+            r = r.x == 0xFFFFFFFFu ? make_uint2(0u, 0u) : make_uint2(r.x, ~r.y);
+            ranges[t] = r;  // read back below by this same thread
+            cls = 32 - __clz(r.y - r.x + 1u);
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cls);
+        if (cls < 33u && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_cnt[cls], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x < 33) ctr->tile_buckets[threadIdx.x] = s_cnt[threadIdx.x];
@@ -270,9 +279,19 @@ __global__ void __launch_bounds__(1024) k_tile_order(uint2* __restrict__ ranges,
         for (int b = 32; b >= 0; --b) { s_start[b] = run; run += s_cnt[b]; }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        order[atomicAdd(&s_start[32 - __clz(r.y - r.x + 1u)], 1u)] = t;
+    for (uint32_t t0 = threadIdx.x & ~31u; t0 < n_tiles; t0 += blockDim.x) {
+        const uint32_t t = t0 + lane;
+        uint32_t cls = 64u;
+        if (t < n_tiles) {
+            const uint2 r = ranges[t];
+            cls = 32 - __clz(r.y - r.x + 1u);
+        }
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cls);
+        const int leader = __ffs(peers) - 1;
+        uint32_t at = 0;
+        if (cls < 33u && (int)lane == leader) at = atomicAdd(&s_start[cls], (uint32_t)__popc(peers));
+        at = __shfl_sync(0xFFFFFFFFu, at, leader);
+        if (cls < 33u) order[at + __popc(peers & lanemask_lt())] = t;
     }
 }
 
